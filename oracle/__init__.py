@@ -1,0 +1,383 @@
+"""CPU oracle for the iterative-refinement solver -- TEST INFRASTRUCTURE ONLY.
+
+A plain, slow, obviously-correct implementation of the paper's method
+(Kelley, "Using MultiPrecisionArrays.jl: Iterative Refinement in Julia"):
+
+* ``ir_solve``      -- Algorithm IR (Sec. 1) with low-precision solves and the
+                       residual scaling of eqs. (vdlow)/(promotevd) (Sec. 5.3),
+                       the termination rules of Sec. 5.1 and the residual in
+                       TR = binary64 (Sec. 2.2.2, eq. xferrule).
+* ``cast``/``getrf_tf``/``getrs_f32``/``residual`` -- the steps, in C
+                       (``ir_oracle.c``), unblocked and in the paper's order.
+* ``reference_solution`` -- the binary64 solution x_ref every result is
+                       compared with: binary64 LU solve refined with
+                       extended-precision residuals until the corrections stop
+                       shrinking.
+* ``term_decide``   -- the termination test of Sec. 5.1, a pure function that
+                       the tests replay the paper's printed histories through.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA library and never imports it.
+
+Readings of the paper taken here (each also listed in the design notes):
+* u_W in the termination tests is Julia's ``eps(TW)`` (2^-52, 2^-23), the value
+  the paper's printed histories agree with.
+* The small-residual test (eq. residterm) is applied as ``||r|| <= C_r u_W ||b||``:
+  the toy IR listing of Sec. 2.1.1 loops while ``rnorm > tol*norm(b)``, and the
+  Float16 history of Sec. 2.2.1 stops at a residual equal to eps.
+* The stagnation test (eq. stag) is ``||r_new|| >= R_max ||r_old||``; when
+  TR is wider than TW only the correction test (eq. wilkterm)
+  ``||d_new|| >= R_max ||d_old||`` is applied (Sec. 5.1; the histories of
+  Sec. 2.2.2 and 2.3 continue past residual ratios >= R_max).
+* Norms are infinity norms; the solve scales r by ||r||_inf (eq. vdlow).
+* An iteration is one residual computation (Sec. 5.1.2); litmax bounds them.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import platform
+import subprocess
+import sys
+from dataclasses import dataclass, field
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liboracle.so")
+_SRC = os.path.join(_HERE, "ir_oracle.c")
+
+F64, F32, TF32, BF16, F16 = 0, 1, 2, 3, 4
+DTYPE_NAMES = {F64: "f64", F32: "f32", TF32: "tf32", BF16: "bf16", F16: "f16"}
+# Julia eps(T): the spacing of T at 1.0 (Sec. 5.4.1 uses it as u)
+EPS = {F64: 2.0 ** -52, F32: 2.0 ** -23, TF32: 2.0 ** -10, BF16: 2.0 ** -7, F16: 2.0 ** -10}
+# unit roundoff (half the spacing), for the rounding-error bounds of Sec. 5.4
+UNIT_ROUNDOFF = {k: v / 2 for k, v in EPS.items()}
+
+CONVERGED, STAGNATED, MAXIT, DIVERGED, FAILED = 0, 1, 2, 3, 4
+STATUS_NAMES = {CONVERGED: "converged", STAGNATED: "stagnated", MAXIT: "maxit",
+                DIVERGED: "diverged", FAILED: "failed"}
+
+
+def build(force: bool = False) -> str:
+    """Compile ir_oracle.c into a shared library (gcc, OpenMP, no contraction)."""
+    if not force and os.path.exists(_SO) and os.path.getmtime(_SO) >= os.path.getmtime(_SRC):
+        return _SO
+    os.makedirs(_BUILD, exist_ok=True)
+    flags = ["-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared"]
+    if platform.machine() in ("x86_64", "AMD64"):
+        flags.append("-mfma")  # hardware fma; results equal the libm fma exactly
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", *flags, _SRC, "-o", tmp, "-lm"])
+    os.replace(tmp, _SO)
+    return _SO
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        i64, i32, dbl, vp = ctypes.c_int64, ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+        sig = {
+            "orc_round_tf": (ctypes.c_float, [ctypes.c_float, i32]),
+            "orc_round_tf_array": (None, [i64, vp, vp, i32]),
+            "orc_cast": (None, [i64, i32, vp, i64, dbl, i32, vp, i64]),
+            "orc_maxabs": (dbl, [i64, i32, vp, i64]),
+            "orc_getrf_f64": (i64, [i64, vp, i64, vp]),
+            "orc_getrf_tf": (i64, [i64, vp, i64, vp, i32, i64, vp, vp]),
+            "orc_getrs_f32": (None, [i64, vp, i64, vp, vp]),
+            "orc_getrs_f64": (None, [i64, vp, i64, vp, vp]),
+            "orc_residual": (None, [i64, i32, vp, i64, vp, vp, vp]),
+            "orc_residual_ext": (None, [i64, i32, vp, i64, vp, vp, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _tw_of(A: np.ndarray) -> int:
+    if A.dtype == np.float64:
+        return F64
+    if A.dtype == np.float32:
+        return F32
+    raise TypeError(f"working precision must be float64 or float32, got {A.dtype}")
+
+
+# --------------------------------------------------------------------------
+# steps
+# --------------------------------------------------------------------------
+
+def round_tf(x: np.ndarray, tf: int) -> np.ndarray:
+    """Round binary32 values to TF (TF32: ties away; bf16/fp16: ties to even)."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    y = np.empty_like(x)
+    lib().orc_round_tf_array(x.size, _p(x), _p(y), tf)
+    return y
+
+
+def maxabs(A: np.ndarray) -> float:
+    A = np.asfortranarray(A)
+    n = A.shape[0]
+    return float(lib().orc_maxabs(n, _tw_of(A), _p(A), max(n, 1)))
+
+
+def fp16_scale(A: np.ndarray) -> float:
+    """s = 2^10 / max|a_ij|, the scaling that moves A into the binary16 range."""
+    m = maxabs(A)
+    return 1.0 if m == 0.0 or not np.isfinite(m) else 1024.0 / m
+
+
+def cast(A: np.ndarray, tf: int, s: float = 1.0) -> np.ndarray:
+    """A_F = round_TF(fl32(s A)) as a column-major binary32 array (Sec. 1)."""
+    A = np.asfortranarray(A)
+    n = A.shape[0]
+    AF = np.empty((n, n), dtype=np.float32, order="F")
+    lib().orc_cast(n, _tw_of(A), _p(A), max(n, 1), s, tf, _p(AF), max(n, 1))
+    return AF
+
+
+def getrf_f64(A: np.ndarray):
+    """Unblocked binary64 LU with partial pivoting -> (LU, ipiv, info)."""
+    LU = np.array(A, dtype=np.float64, order="F", copy=True)
+    n = LU.shape[0]
+    ipiv = np.zeros(n, dtype=np.int32)
+    info = lib().orc_getrf_f64(n, _p(LU), max(n, 1), _p(ipiv))
+    return LU, ipiv, int(info)
+
+
+def getrf_tf(AF: np.ndarray, tf: int, nb: int = 0, force_piv: Optional[np.ndarray] = None,
+             want_gap: bool = False):
+    """LU of the binary32 factorization copy (see ir_oracle.c) -> (LU, ipiv, info[, gap])."""
+    LU = np.array(AF, dtype=np.float32, order="F", copy=True)
+    n = LU.shape[0]
+    ipiv = np.zeros(n, dtype=np.int32)
+    fp = None
+    if force_piv is not None:
+        fp = np.ascontiguousarray(force_piv, dtype=np.int32)
+    gap = np.zeros(3 * n, dtype=np.float32) if want_gap else None
+    info = lib().orc_getrf_tf(n, _p(LU), max(n, 1), _p(ipiv), tf, nb,
+                              _p(fp) if fp is not None else None,
+                              _p(gap) if gap is not None else None)
+    if want_gap:
+        return LU, ipiv, int(info), gap.reshape(n, 3)
+    return LU, ipiv, int(info)
+
+
+def getrs_f32(LU: np.ndarray, ipiv: np.ndarray, v: np.ndarray) -> np.ndarray:
+    v = np.array(v, dtype=np.float32, copy=True)
+    n = v.shape[0]
+    LU = np.asfortranarray(LU, dtype=np.float32)
+    lib().orc_getrs_f32(n, _p(LU), max(n, 1), _p(np.ascontiguousarray(ipiv, dtype=np.int32)), _p(v))
+    return v
+
+
+def getrs_f64(LU: np.ndarray, ipiv: np.ndarray, v: np.ndarray) -> np.ndarray:
+    v = np.array(v, dtype=np.float64, copy=True)
+    n = v.shape[0]
+    LU = np.asfortranarray(LU, dtype=np.float64)
+    lib().orc_getrs_f64(n, _p(LU), max(n, 1), _p(np.ascontiguousarray(ipiv, dtype=np.int32)), _p(v))
+    return v
+
+
+def residual(A: np.ndarray, b: np.ndarray, x: np.ndarray, extended: bool = False) -> np.ndarray:
+    """r = b - A x in binary64 (or the host's long double when extended)."""
+    A = np.asfortranarray(A)
+    n = A.shape[0]
+    b64 = np.ascontiguousarray(b, dtype=np.float64)
+    x64 = np.ascontiguousarray(x, dtype=np.float64)
+    r = np.empty(n, dtype=np.float64)
+    f = lib().orc_residual_ext if extended else lib().orc_residual
+    f(n, _tw_of(A), _p(A), max(n, 1), _p(b64), _p(x64), _p(r))
+    return r
+
+
+def apply_pivots(ipiv: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """P v: the interchanges ipiv applied in order (LAPACK laswp semantics)."""
+    v = np.array(v, copy=True)
+    for k, p in enumerate(ipiv):
+        if p != k:
+            v[[k, p]] = v[[p, k]]
+    return v
+
+
+def perm_from_ipiv(ipiv: np.ndarray) -> np.ndarray:
+    """perm with (P A)[i] = A[perm[i]]."""
+    return apply_pivots(ipiv, np.arange(len(ipiv)))
+
+
+# --------------------------------------------------------------------------
+# Algorithm IR
+# --------------------------------------------------------------------------
+
+@dataclass
+class Term:
+    """Termination parameters (the TERM structure of Sec. 5.1.3)."""
+    Cr: float = 1.0
+    Ce: float = 1.0
+    Rmax: float = 0.5
+    litmax: int = 10
+    abs_rel_tol: float = 0.0  # > 0: converged iff ||r|| <= abs_rel_tol ||b||
+
+
+@dataclass
+class IRResult:
+    x: np.ndarray                   # the binary64 accumulator (TR)
+    sol: np.ndarray                 # x rounded to TW
+    rhist: list = field(default_factory=list)
+    dhist: list = field(default_factory=list)
+    status: int = CONVERGED
+    info: int = 0
+    ipiv: Optional[np.ndarray] = None
+    LU: Optional[np.ndarray] = None
+    scale: float = 1.0
+
+    @property
+    def iters(self) -> int:
+        return len(self.rhist) - 1
+
+
+def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: bool):
+    """Termination test of Sec. 5.1, applied after each residual computation.
+
+    rhist = [||r_0||, ..., ||r_k||] (r_0 = b), dhist = [||d_0||, ..., ||d_{k-1}||].
+    Returns a status code, or None to continue.
+    """
+    k = len(rhist) - 1
+    rn = rhist[-1]
+    if not np.isfinite(rn):
+        return DIVERGED
+    if tr_wider:
+        # eq. (wilkterm): corrections stagnate
+        if len(dhist) >= 2 and dhist[-1] >= term.Rmax * dhist[-2]:
+            return STAGNATED
+    else:
+        tol = term.abs_rel_tol if term.abs_rel_tol > 0 else term.Cr * eps_w
+        if rn <= tol * bnorm:             # eq. (residterm)
+            return CONVERGED
+        if k >= 1 and rn >= term.Rmax * rhist[-2]:   # eq. (stag)
+            return STAGNATED
+    if k >= term.litmax:
+        return MAXIT
+    return None
+
+
+def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
+             nb: int = 0, fp16_scaling: bool = True, tr_wider: Optional[bool] = None) -> IRResult:
+    """Algorithm IR (Sec. 1) with TR = binary64 and solves in binary32.
+
+    1. A_F = round_TF(s A) (s = 2^10/max|a| for TF = binary16, else 1);
+       factor A_F = P^T L U (getrf_tf).
+    2. x = 0, r = b, rhist = [||b||].
+    3. repeat: rho = ||r||; v = fl32(P r / rho); v = U^{-1} L^{-1} v in binary32
+       (eq. vdlow); d = (rho s) fl64(v) (eq. promotevd); x += d;
+       r = b - A x in binary64; test termination.
+    The solution is returned both as the binary64 accumulator and rounded to TW.
+    """
+    term = term or Term()
+    A = np.asfortranarray(A)
+    tw = _tw_of(A)
+    n = A.shape[0]
+    if tr_wider is None:
+        tr_wider = tw == F32   # TR = binary64 is wider than TW = binary32
+    b64 = np.ascontiguousarray(b, dtype=np.float64)
+    eps_w = EPS[tw]
+    s = fp16_scale(A) if (tf == F16 and fp16_scaling) else 1.0
+    AF = cast(A, tf, s)
+    LU, ipiv, info = getrf_tf(AF, tf, nb)
+    x = np.zeros(n)
+    res = IRResult(x=x, sol=x.astype(A.dtype), ipiv=ipiv, LU=LU, scale=s, info=info)
+    bnorm = float(np.max(np.abs(b64))) if n else 0.0
+    res.rhist.append(bnorm)
+    if info != 0:
+        res.status = FAILED
+        return res
+    if bnorm == 0.0:
+        res.status = CONVERGED
+        return res
+    r = b64.copy()
+    while True:
+        rho = float(np.max(np.abs(r)))
+        v = getrs_f32(LU, ipiv, (r / rho).astype(np.float32))
+        d = (rho * s) * v.astype(np.float64)
+        x += d
+        res.dhist.append(float(np.max(np.abs(d))))
+        r = residual(A, b64, x)
+        res.rhist.append(float(np.max(np.abs(r))))
+        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, term, tr_wider)
+        if st is not None:
+            res.status = st
+            break
+    res.x = x
+    res.sol = x.astype(A.dtype)
+    return res
+
+
+# --------------------------------------------------------------------------
+# reference solution and conditioning
+# --------------------------------------------------------------------------
+
+def reference_solution(A: np.ndarray, b: np.ndarray, maxit: int = 10) -> np.ndarray:
+    """x_ref ~ fl64(A^{-1} b): binary64 LU solve refined with extended residuals.
+
+    For binary32 A the problem solved is the promoted one (A and b promoted
+    exactly to binary64), as in Sec. 2.2.2.
+    """
+    A = np.asfortranarray(A)
+    b64 = np.ascontiguousarray(b, dtype=np.float64)
+    LU, ipiv, info = getrf_f64(A.astype(np.float64))
+    if info:
+        raise np.linalg.LinAlgError(f"singular matrix (zero pivot at {info})")
+    x = getrs_f64(LU, ipiv, b64)
+    dold = np.inf
+    for _ in range(maxit):
+        r = residual(A, b64, x, extended=True)
+        d = getrs_f64(LU, ipiv, r)
+        x = x + d
+        dn = float(np.max(np.abs(d)))
+        if dn == 0.0 or dn >= 0.5 * dold:
+            break
+        dold = dn
+    return x
+
+
+def inverse_f64(A: np.ndarray) -> np.ndarray:
+    A64 = np.asfortranarray(A, dtype=np.float64)
+    n = A64.shape[0]
+    LU, ipiv, info = getrf_f64(A64)
+    if info:
+        raise np.linalg.LinAlgError("singular")
+    inv = np.empty((n, n), order="F")
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        inv[:, j] = getrs_f64(LU, ipiv, e)
+    return inv
+
+
+def cond_inf(A: np.ndarray) -> float:
+    """kappa_inf(A) = ||A||_inf ||A^{-1}||_inf with the oracle's explicit inverse."""
+    A64 = np.asarray(A, dtype=np.float64)
+    return float(np.max(np.abs(A64).sum(axis=1)) * np.max(np.abs(inverse_f64(A64)).sum(axis=1)))
+
+
+def rel_err_inf(x: np.ndarray, xref: np.ndarray) -> float:
+    den = float(np.max(np.abs(xref)))
+    return float(np.max(np.abs(np.asarray(x, dtype=np.float64) - xref))) / (den if den else 1.0)
+
+
+def parity_tol(kappa: float, tw: int) -> float:
+    """max(1e-12, 10 kappa eps(TW)): the forward-error bar for converged IR."""
+    return max(1e-12, 10.0 * kappa * EPS[tw])
