@@ -1,0 +1,404 @@
+#!/usr/bin/env python3
+"""Benchmark: time to solution of mixed-precision iterative refinement on GB300.
+
+Workload (one system per step, inputs resident in HBM): the Green's-function
+system of the paper's Sec. 2 at N = 4096, A = I - 800 G (midpoint rule),
+x_true = sin(pi x), b = A x_true; TW = binary64, TF = binary32 (tensor-core
+TF32 trailing update reported beside it), TR = binary64.  A step is the whole
+hot path: rounded copy of A, blocked LU with partial pivoting, and the
+refinement loop (correction solves, x += d, binary64 residual) until the
+termination rule of Sec. 5.1 holds.
+
+Metric: milliseconds per solved system (lower is better).  With N GPUs
+(torchrun, one process per GPU) every rank solves its own copy of the system
+("replicas only": one system does not shard); the value is the slowest
+rank's step time divided by the number of systems solved per step.
+
+Besides the headline it reports: the plain binary64 LU solve (cuSOLVER via
+torch.linalg) on the same system, the LU rate in TFLOP/s, a roofline line for
+the kernel that takes the most time, an end-to-end number through the
+host-buffer entry point, and the CPU oracle timed on the host cores.
+
+`--impl reference` times the CPU oracle instead (the reference arm).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 4096
+ALPHA = 800.0
+L2_FLUSH_BYTES = 512 * 1024 * 1024
+
+# Algorithmic work per launcher call (for the roofline line).
+#   panel:     the N x nb rank-1 updates of a panel, 2 * sum_k (M - k)(nb - k) flops
+#   gemm_*:    2 m^2 nb flops (trailing update of an m x m block, K = nb)
+#   residual:  N^2 * sizeof(TW) bytes of A read once
+#   trsv_pair: N^2 * 4 bytes of factors read once (L and U)
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return {"hbm_gbs": p["hbm_gbs"], "bf16_tflops": p["bf16_tflops"],
+                "bf16_tflops_sustained": p.get("bf16_tflops_sustained"), "source": "measured"}
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "source": "fallback"}
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() in ("active", "1"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def dist_setup(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_inputs(n):
+    import irgen
+    A, b, xt = irgen.case_green_sine(n, ALPHA)
+    return A, b, xt
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# ---------------------------------------------------------------------------
+
+def oracle_sample_time(n_full, sample_n):
+    """Oracle IR (binary32 factorization, binary64 residual) on the host cores for
+    the same workload at N = sample_n; time scaled by (n_full / sample_n)^3 (the
+    LU's N^3 term dominates)."""
+    import oracle as O
+    A, b, _ = make_inputs(sample_n)
+    t0 = time.perf_counter()
+    res = O.ir_solve(A, b, O.F32, nb=64)
+    dt = time.perf_counter() - t0
+    scale = (n_full / sample_n) ** 3
+    return dt * scale * 1e3, res, dt
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def run_reference(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = cpu_cores()
+    os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+    sample_n = min(args.n, 2048)
+    times = []
+    for i in range(args.warmup + args.steps):
+        ms, _, _ = oracle_sample_time(args.n, sample_n)
+        if i >= args.warmup:
+            times.append(ms)
+    v = statistics.mean(times)
+    sample = (f"oracle IR (binary32 LU, binary64 residual) at N={sample_n} of the same workload, "
+              f"time x (N/{sample_n})^3")
+    out = {
+        "impl": "reference", "metric": "ir_solve_ms", "value": v, "unit": "ms", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": f"green_sine_N{args.n}_alpha800_TWf64_TFf32_TRf64", "n": args.n,
+                   "alpha": ALPHA},
+        "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    ws, rank, local = dist_setup(args)
+    import numpy as np
+    import torch
+
+    from paper_2311_14616_gb300 import ir
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = args.n
+    A, b, xt = make_inputs(n)
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()        # column-major
+    b_d = torch.from_numpy(b).to(dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    ctx = ir.Context(local)
+    stream = torch.cuda.current_stream(dev)
+
+    def timed_steps(step_fn, steps, warmup, profile=False):
+        for _ in range(warmup):
+            step_fn()
+        torch.cuda.synchronize()
+        barrier(ws)
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(steps)]
+        launches0 = ir.kernel_launches()
+        if profile:
+            ir.profile_start()
+        out = None
+        for e0, e1 in ev:
+            flush.fill_(1.0)                    # evict A from L2 between steps
+            e0.record(stream)
+            out = step_fn()
+            e1.record(stream)
+        torch.cuda.synchronize()
+        prof = ir.profile_stop() if profile else None
+        launches = ir.kernel_launches() - launches0
+        barrier(ws)
+        ms = [a.elapsed_time(z) for a, z in ev]
+        return ms, out, prof, launches
+
+    # --- headline: TF = binary32 (bit-exact FP32 LU), default termination
+    fact32 = ctx.factor(A_d, tf="f32")
+    x32 = torch.empty_like(b_d)
+    term = ir.default_term()
+
+    def step32():
+        fact32.refactor(A_d)
+        return fact32.solve(b_d, x32, term)[1]
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms32, rep32, prof32, launches = timed_steps(step32, args.steps, args.warmup, profile=True)
+    clk = clocks.stop()
+    # unprofiled repeat: the headline number carries no event overhead
+    ms32_plain, rep32, _, _ = timed_steps(step32, args.steps, 1)
+    t32 = max_over_ranks(statistics.mean(ms32_plain), ws)
+
+    # --- tensor-core arm: TF = TF32, litmax raised so IR reaches its limiting accuracy
+    fact_tc = ctx.factor(A_d, tf="tf32")
+    xtc = torch.empty_like(b_d)
+    term_tc = ir.default_term(litmax=30)
+
+    def step_tc():
+        fact_tc.refactor(A_d)
+        return fact_tc.solve(b_d, xtc, term_tc)[1]
+
+    ms_tc, rep_tc, prof_tc, _ = timed_steps(step_tc, max(3, args.steps // 2), 1, profile=True)
+    t_tc = max_over_ranks(statistics.mean(ms_tc), ws)
+
+    # --- binary64 LU solve (cuSOLVER through torch.linalg) on the same system
+    A_row = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
+
+    def step64():
+        LU, piv = torch.linalg.lu_factor(A_row)
+        return torch.linalg.lu_solve(LU, piv, b_d.unsqueeze(1))
+
+    ms64, x64, _, _ = timed_steps(step64, max(3, args.steps // 2), 1)
+    t64 = max_over_ranks(statistics.mean(ms64), ws)
+
+    # --- accuracy against the closed form and the binary64 LU solution
+    xg = x32.double().cpu().numpy()
+    x64h = x64.squeeze(1).cpu().numpy()
+    err_true = float(np.max(np.abs(xg - xt)) / np.max(np.abs(xt)))
+    err_vs_lu64 = float(np.max(np.abs(xg - x64h)) / np.max(np.abs(x64h)))
+    err_tc_true = float(np.max(np.abs(xtc.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
+
+    # --- roofline of the kernel kind with the largest share of the profiled step
+    peaks = load_peaks()
+    total_prof = sum(v[0] for v in prof32.values())
+    dom = max(prof32, key=lambda k: prof32[k][0])
+    nb = 64
+    dom_ms, dom_calls = prof32[dom]
+    avg_ms = dom_ms / dom_calls
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    fp32_peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12   # SMs x FP32 lanes x FMA x max clock
+    if dom == "panel":
+        flops = sum(2 * sum((n - j - k) * (min(nb, n - j) - k) for k in range(min(nb, n - j)))
+                    for j in range(0, n, nb)) / dom_calls
+        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "kernel": "k_panel"}
+    elif dom in ("gemm_simt", "gemm_tc"):
+        flops = sum(2 * (n - j - nb) ** 2 * nb for j in range(0, n - nb, nb)) / dom_calls
+        peak = fp32_peak_tflops if dom == "gemm_simt" else peaks["bf16_tflops"] * 1.1 / 2.25
+        roof = {"bound": "alu" if dom == "gemm_simt" else "tensor",
+                "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                "kernel": "k_" + dom}
+    elif dom == "residual":
+        roof = {"bound": "hbm", "achieved": n * n * 8 / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "kernel": "k_resid_partial+k_resid_final"}
+    else:
+        roof = {"bound": "hbm", "achieved": n * n * 4 / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "kernel": "k_" + dom}
+    roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+    roof["peak_source"] = peaks["source"] if roof["bound"] != "alu" else "unit counts x 2070 MHz"
+    roof["share_of_step"] = dom_ms / total_prof
+    roof["avg_launch_ms"] = avg_ms
+
+    # --- LU rate of the headline path (2 N^3 / 3 flops over factor time = cast + LU kernels)
+    lu_kinds = ("cast", "iota", "panel", "laswp", "trsm", "gemm_simt", "diag_inv")
+    lu_ms = sum(prof32[k][0] for k in lu_kinds if k in prof32) / args.steps
+    lu_tflops = (2.0 * n ** 3 / 3.0) / (lu_ms * 1e-3) / 1e12
+    lu_tc_ms = sum(prof_tc[k][0] for k in ("cast", "iota", "panel", "laswp", "trsm", "gemm_tc", "diag_inv")
+                   if k in prof_tc) / max(3, args.steps // 2)
+
+    # --- end to end through the host-buffer entry point (copies inside the timed region)
+    e2e = None
+    if not args.no_e2e:
+        A_h = torch.from_numpy(np.ascontiguousarray(A.T)).t().pin_memory()
+        b_h = torch.from_numpy(b).pin_memory()
+        for _ in range(2):
+            ctx.solve_host(A_h, b_h, tf="f32")
+        torch.cuda.synchronize()
+        barrier(ws)
+        t_e = []
+        for _ in range(max(3, args.steps // 2)):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.solve_host(A_h, b_h, tf="f32")
+            t_e.append((time.perf_counter() - t0) * 1e3)
+        e2e = {"value": max_over_ranks(statistics.mean(t_e), ws) / ws, "unit": "ms",
+               "h2d_bytes_per_step": int(n * n * 8 + n * 8), "d2h_bytes_per_step": int(n * 8),
+               "api": "ir_solve_host (pinned host A, b; allocation, copies, factor, refine, copy back)"}
+
+    # --- CPU oracle on the host cores (rank 0, one GPU only)
+    cpu = None
+    acc_oracle = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cores = cpu_cores()
+        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
+        sample_n = min(n, 2048)
+        ms_cpu, res, dt = oracle_sample_time(n, sample_n)
+        cpu = {"value": ms_cpu, "unit": "ms", "cores": cores, "kind": "oracle",
+               "sample": f"one oracle IR solve of the same workload at N={sample_n} "
+                         f"({dt:.2f} s), scaled by (N/{sample_n})^3"}
+
+    value = t32 / ws if ws > 1 else t32
+    out = {
+        "metric": "ir_solve_ms", "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": f"green_sine_N{n}_alpha800_TWf64_TFf32_TRf64", "n": n, "alpha": ALPHA,
+                   "TW": "f64", "TF": "f32", "TR": "f64", "rhs": "b = A sin(pi x)",
+                   "l2": "flushed by a 512 MiB write before every timed step",
+                   "parallelism": "replicas" if ws > 1 else "single"},
+        "iters": rep32.iters, "status": rep32.status,
+        "rel_err_vs_closed_form": err_true, "rel_err_vs_fp64_lu": err_vs_lu64,
+        "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": t64 / t32,
+        "lu_ms": lu_ms, "lu_tflops": lu_tflops,
+        "tf32_tensor_core": {"ms": t_tc, "iters": rep_tc.iters, "status": rep_tc.status,
+                             "lu_ms": lu_tc_ms, "rel_err_vs_closed_form": err_tc_true,
+                             "litmax": 30},
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof32.items())},
+        "roofline": roof,
+        "e2e": e2e,
+        "cpu_baseline": cpu,
+        "gpu_launches": launches,
+        "gpu_launches_per_step": launches / args.steps,
+        "clocks": clk,
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

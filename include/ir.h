@@ -1,0 +1,188 @@
+/*
+ * ir.h -- C ABI of the GB300 mixed-precision iterative-refinement solver.
+ *
+ * The library solves dense A x = b on one NVIDIA GB300 GPU by Algorithm IR of
+ * Kelley, "Using MultiPrecisionArrays.jl: Iterative Refinement in Julia"
+ * (Sec. 1): a copy of the working-precision matrix A (type TW) is rounded to
+ * the factorization precision TF and factored by LU with partial pivoting;
+ * the loop { d = U^{-1} L^{-1} r ; x += d ; r = b - A x in precision TR }
+ * runs until a termination rule on ||r|| holds (Sec. 5.1).
+ *
+ * Conventions shared by every entry point
+ *   - Matrices are column-major with a leading dimension lda >= n (LAPACK and
+ *     Julia layout).  Vectors are contiguous.
+ *   - Unless a name says "host", pointers are DEVICE pointers (cudaMalloc /
+ *     torch allocations) on the device the context was created for.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  All device work is enqueued on it.
+ *   - Pivots are 0-based: step k interchanged rows k and ipiv[k].
+ *   - Every call returns an ir_status and never aborts the process.  On an
+ *     error return nothing the call was to produce is valid.
+ *   - The library allocates its own device workspace (the factorization copy,
+ *     pivots, solve vectors) inside ir_factor; the caller owns A, b and x.
+ */
+#ifndef GB300_IR_H
+#define GB300_IR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Precisions (the TW / TF / TR types of Sec. 1).  IR_TF32 is the tensor-core
+ * format with 10 fraction bits; IR_BF16 / IR_F16 the 16-bit formats of Sec. 3. */
+typedef enum { IR_F64 = 0, IR_F32 = 1, IR_TF32 = 2, IR_BF16 = 3, IR_F16 = 4 } ir_dtype;
+
+typedef enum {
+    IR_OK = 0,
+    IR_EINVAL = 1,        /* bad argument (null pointer, n < 0, lda < n, unsupported dtype mix) */
+    IR_ENOMEM = 2,        /* device allocation failed */
+    IR_ECUDA = 3,         /* a CUDA runtime call failed */
+    IR_ESINGULAR = 4,     /* exact zero pivot in the TF factorization (report.info) */
+    IR_ENONFINITE = 5,    /* NaN/Inf in A or b, or overflow of the rounded copy */
+    IR_ETIMEOUT = 6,      /* a bounded device-side wait gave up */
+    IR_EUNSUPPORTED = 7   /* size or configuration outside what this build supports */
+} ir_status;
+
+/* Outcome of the refinement loop (numerical non-convergence is not an error). */
+typedef enum {
+    IR_CONVERGED = 0,     /* eq. (residterm) held */
+    IR_STAGNATED = 1,     /* eq. (stag), or eq. (wilkterm) when TR is wider than TW */
+    IR_MAXIT = 2,         /* litmax residual computations without termination */
+    IR_DIVERGED = 3,      /* the residual norm became non-finite */
+    IR_FAILED = 4         /* the factorization had a zero pivot; no iteration ran */
+} ir_solve_status;
+
+/* Termination parameters: the TERM structure of Sec. 5.1.3.
+ *   converged   if ||r|| <= Cr * eps(TW) * ||b||        (eq. residterm)
+ *               or, when abs_rel_tol > 0, ||r|| <= abs_rel_tol * ||b||
+ *   stagnated   if ||r_new|| >= Rmax ||r_old||           (eq. stag), TR == TW
+ *               if ||d_new|| >= Rmax ||d_old||           (eq. wilkterm), TR wider than TW
+ *   stop        after litmax residual computations.
+ * Norms are infinity norms; eps(T) is 2^-52 (FP64) or 2^-23 (FP32). */
+typedef struct {
+    double Cr;            /* default 1.0 */
+    double Ce;            /* default 1.0 (backward-error test, not used by this build) */
+    double Rmax;          /* default 0.5 */
+    int litmax;           /* default 10, at most IR_MAX_HIST - 1 */
+    int mode;             /* 0: residual test (the only mode of this build) */
+    double abs_rel_tol;   /* > 0 overrides Cr * eps(TW) */
+} ir_term;
+
+/* Factorization options (the keyword arguments TF and TR of mplu, Sec. 2.4).
+ *   TW: IR_F64 or IR_F32 (type of A and b).  TF: IR_F32, IR_TF32, IR_BF16 or
+ *   IR_F16.  TR: IR_F64.  fp16_scale = 1 multiplies A by s = 2^10 / max|a_ij|
+ *   before the binary16 cast (ignored for other TF).  nb = 0 picks the block
+ *   size. */
+typedef struct {
+    ir_dtype TW, TF, TR;
+    int fp16_scale;       /* default 1 */
+    int nb;               /* outer block size; 0 = default (64) */
+    int autotune;         /* reserved, 0 */
+} ir_opts;
+
+#define IR_MAX_HIST 32
+
+/* Iteration statistics (the `reporting = true` output of Sec. 2.2.1).
+ * rhist[0] = ||b||; rhist[k] = ||r|| after the k-th correction; dhist[k] =
+ * ||d_k||, one entry fewer than rhist. */
+typedef struct {
+    int iters;                    /* residual computations = entries of rhist - 1 */
+    ir_solve_status status;
+    double rhist[IR_MAX_HIST];
+    double dhist[IR_MAX_HIST];
+    int64_t info;                 /* first zero pivot (1-based) or 0 */
+    double scale;                 /* s used for the factorization copy */
+} ir_report;
+
+typedef struct ir_ctx ir_ctx;
+typedef struct ir_fact ir_fact;
+
+/* Fill the paper's defaults (TW = F64, TF = F32, TR = F64; Cr = Ce = 1,
+ * Rmax = 0.5, litmax = 10; Sec. 2.4 and 5.1.3). */
+void ir_default_opts(ir_opts *opts);
+void ir_default_term(ir_term *term);
+
+/* Create a context on CUDA device `device` (selects it for the calling
+ * thread).  *ctx receives a handle owned by the caller; free with ir_finalize. */
+ir_status ir_init(int device, ir_ctx **ctx);
+void ir_finalize(ir_ctx *ctx);
+
+/* mplu (Sec. 2.4): round A to TF (A_F = I_W^F(s A), Sec. 1) into a library-
+ * owned copy and factor it by LU with partial pivoting.
+ *   n >= 0, A: n x n in TW, column-major, lda >= max(1, n).
+ * The handle BORROWS A for the residuals of ir_solve: A must stay alive and
+ * unmodified until ir_fact_destroy or ir_refactor (the MPArray shares A's
+ * storage, Sec. 2.5).  Asynchronous; a zero pivot or a non-finite copy is
+ * reported by ir_solve or ir_fact_info. */
+ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda,
+                    const ir_opts *opts, void *stream, ir_fact **out);
+
+/* mplu!(MPF, B) (Sec. 2.5): factor another matrix of the same size and
+ * precisions into the same storage.  The handle then borrows B. */
+ir_status ir_refactor(ir_fact *fact, const void *B, int64_t ldb, void *stream);
+
+/* Backslash on the factorization (Algorithm IR, Sec. 1): solve A x = b.
+ *   b: n values in TW; x: n values in TW (the binary64 iterate rounded to TW).
+ *   term may be NULL (defaults).  rep may be NULL.
+ * Returns IR_ESINGULAR / IR_ENONFINITE when the factorization failed (rep
+ * then carries info), IR_ENONFINITE for a non-finite b, IR_ETIMEOUT when a
+ * device wait gave up.  The call synchronizes `stream` once per iteration. */
+ir_status ir_solve(ir_fact *fact, const void *b, void *x, const ir_term *term,
+                   void *stream, ir_report *rep);
+
+/* End-to-end solve from HOST memory: copies A and b to the device, factors,
+ * refines, copies x back and releases the device buffers.  A_host: n x n
+ * column-major in TW (lda); b_host, x_host: n values in TW.  Synchronous.
+ * Host buffers may be pageable; pinned buffers copy faster. */
+ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda,
+                        const void *b_host, void *x_host, const ir_opts *opts,
+                        const ir_term *term, void *stream, ir_report *rep);
+
+/* One correction solve d = U^{-1} L^{-1} P v in binary32 (eq. vdlow without
+ * the scaling): v, d are n binary32 device vectors (may alias). */
+ir_status ir_lu_solve(ir_fact *fact, const float *v, float *d, void *stream);
+
+/* Residual r = b - A x in binary64 (Algorithm IR, eq. xferrule: A and b in
+ * TW are promoted exactly) and rnorm[0] = ||r||_inf.  A: n x n column-major
+ * in TW (IR_F64 or IR_F32) with lda; b in TW; x, r, rnorm binary64; all
+ * device pointers.  Uses library workspace from ctx. */
+ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_t lda,
+                      const void *b, const double *x, double *r, double *rnorm,
+                      void *stream);
+
+/* Pivots of the factorization (0-based, n entries) copied to host memory. */
+ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);
+
+/* The factors L (unit lower, below the diagonal) and U (upper) of P A_F =
+ * L U, binary32, copied to host memory column-major with leading dimension
+ * ld >= n.  Synchronizes the device. */
+ir_status ir_fact_factors(const ir_fact *fact, float *LU_host, int64_t ld);
+
+/* Status of the factorization: 0-based-free info (first zero pivot, 1-based,
+ * or 0) and whether the rounded copy held a non-finite value.  Synchronizes. */
+ir_status ir_fact_info(const ir_fact *fact, int64_t *info, int *nonfinite);
+
+void ir_fact_destroy(ir_fact *fact);
+const char *ir_strerror(ir_status s);
+
+/* Text of the most recent CUDA failure seen by this thread (diagnostics). */
+const char *ir_last_error(void);
+
+/* Instrumentation (no counterpart in the paper; used by the benchmark).
+ * ir_kernel_launches: number of kernels this library has launched in the
+ * process.  ir_profile_start: from now on, every launcher call is bracketed by
+ * a pair of CUDA events on its stream.  ir_profile_stop: synchronizes the
+ * device, writes per-kind total milliseconds and call counts for kinds
+ * 0 .. max_kinds-1 (names from ir_profile_kind) and returns the number of
+ * kinds (0 if profiling was off, -1 on a CUDA error). */
+unsigned long long ir_kernel_launches(void);
+void ir_profile_start(void);
+int ir_profile_stop(double *ms, int *counts, int max_kinds);
+const char *ir_profile_kind(int k);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GB300_IR_H */

@@ -216,16 +216,27 @@ int64_t orc_getrf_tf(int64_t n, float *A, int64_t lda, int32_t *ipiv, int tf,
             for (int64_t k = j; k < je; ++k)
                 for (int64_t m = j; m < k; ++m)
                     A[k + c * lda] = fmaf(-A[k + m * lda], A[m + c * lda], A[k + c * lda]);
-        /* 3. A22 -= rTF(L21) rTF(U12) */
+        /* 3. A22 -= rTF(L21) rTF(U12): the operands are rounded once per block */
+        {
+            const int64_t m = n - je;
+            double *rl = (double *)malloc(sizeof(double) * (size_t)m * (size_t)jb);   /* rl[i][k] */
+            double *ru = (double *)malloc(sizeof(double) * (size_t)m * (size_t)jb);   /* ru[c][k] */
+            if (!rl || !ru) { free(rl); free(ru); return -1; }
+            for (int64_t i = 0; i < m; ++i)
+                for (int64_t k = 0; k < jb; ++k) {
+                    rl[i * jb + k] = (double)orc_round_tf(A[(je + i) + (j + k) * lda], tf);
+                    ru[i * jb + k] = (double)orc_round_tf(A[(j + k) + (je + i) * lda], tf);
+                }
 #pragma omp parallel for schedule(static)
-        for (int64_t c = je; c < n; ++c)
-            for (int64_t i = je; i < n; ++i) {
-                double acc = 0.0;
-                for (int64_t m = j; m < je; ++m)
-                    acc += (double)orc_round_tf(A[i + m * lda], tf) *
-                           (double)orc_round_tf(A[m + c * lda], tf);
-                A[i + c * lda] = A[i + c * lda] - (float)acc;
-            }
+            for (int64_t c = 0; c < m; ++c)
+                for (int64_t i = 0; i < m; ++i) {
+                    double acc = 0.0;
+                    for (int64_t k = 0; k < jb; ++k) acc += rl[i * jb + k] * ru[c * jb + k];
+                    A[(je + i) + (je + c) * lda] = A[(je + i) + (je + c) * lda] - (float)acc;
+                }
+            free(rl);
+            free(ru);
+        }
     }
     return info;
 }

@@ -1,0 +1,565 @@
+// C ABI of the iterative-refinement library: argument checking, workspace,
+// the blocked LU driver and the refinement loop (Algorithm IR, Sec. 1) with the
+// termination rules of Sec. 5.1.
+#include <climits>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <atomic>
+#include <new>
+#include <vector>
+
+#include "ir_internal.cuh"
+
+namespace ir {
+static std::atomic<unsigned long long> g_launch_count{0};
+void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches() { return g_launch_count.load(std::memory_order_relaxed); }
+}  // namespace ir
+
+using namespace ir;
+
+namespace {
+
+// Optional per-launcher timing: a pair of CUDA events around every launcher
+// call on the launching stream, summed per kind when profiling stops.
+enum Kind {
+    KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_N
+};
+const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
+                                "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x"};
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    std::vector<ProfRec> recs;
+    cudaEvent_t next() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+};
+Profiler g_prof;
+
+struct ProfScope {
+    ProfRec r{};
+    cudaStream_t s;
+    bool active;
+    ProfScope(int kind, cudaStream_t st) : s(st), active(g_prof.on) {
+        if (!active) return;
+        r.kind = kind;
+        r.a = g_prof.next();
+        r.b = g_prof.next();
+        active = r.a && r.b;
+        if (active) cudaEventRecord(r.a, s);
+    }
+    void done() {
+        if (!active) return;
+        cudaEventRecord(r.b, s);
+        g_prof.recs.push_back(r);
+    }
+};
+
+thread_local char g_last_error[256] = "";
+
+ir_status cuda_fail(cudaError_t e, const char *what) {
+    snprintf(g_last_error, sizeof g_last_error, "%s: %s", what, cudaGetErrorString(e));
+    return (e == cudaErrorMemoryAllocation) ? IR_ENOMEM : IR_ECUDA;
+}
+
+#define CK(call)                                                \
+    do {                                                        \
+        cudaError_t e_ = (call);                                \
+        if (e_ != cudaSuccess) return cuda_fail(e_, #call);     \
+    } while (0)
+
+// Launcher call with optional timing.
+#define RUN(kind, s, call)                \
+    do {                                  \
+        ProfScope ps_((kind), (s));       \
+        CK(call);                         \
+        ps_.done();                       \
+    } while (0)
+
+constexpr int kInfoNone = 0x7F7F7F7F;   // memset(0x7F) pattern: no zero pivot
+
+bool tw_ok(ir_dtype t) { return t == IR_F64 || t == IR_F32; }
+bool tf_ok(ir_dtype t) { return t == IR_F32 || t == IR_TF32 || t == IR_BF16 || t == IR_F16; }
+size_t op_elem(ir_dtype tf) { return tf == IR_TF32 ? 4 : 2; }
+double eps_of(ir_dtype tw) { return tw == IR_F64 ? std::ldexp(1.0, -52) : std::ldexp(1.0, -23); }
+
+double bits_to_double(unsigned long long b) {
+    double d;
+    std::memcpy(&d, &b, sizeof d);
+    return d;
+}
+
+ir_status ensure_partials(ir_ctx *ctx, int64_t n) {
+    const int64_t need = residual_partials_needed(n, ctx->sms);
+    if (need <= ctx->partials_cap) return IR_OK;
+    if (ctx->partials) cudaFree(ctx->partials);
+    ctx->partials = nullptr;
+    ctx->partials_cap = 0;
+    CK(cudaMalloc(&ctx->partials, need * sizeof(double)));
+    ctx->partials_cap = need;
+    return IR_OK;
+}
+
+void free_fact(ir_fact *f) {
+    if (!f) return;
+    cudaFree(f->AF);
+    cudaFree(f->ipiv);
+    cudaFree(f->perm);
+    cudaFree(f->swap_list);
+    cudaFree(f->Aop);
+    cudaFree(f->Bop);
+    cudaFree(f->Linv);
+    cudaFree(f->Uinv);
+    cudaFree(f->tags);
+    cudaFree(f->x);
+    cudaFree(f->r);
+    cudaFree(f->dev);
+    if (f->host_dev) cudaFreeHost(f->host_dev);
+    delete f;
+}
+
+ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
+    ir_fact *f = new (std::nothrow) ir_fact();
+    if (!f) return IR_ENOMEM;
+    f->ctx = ctx;
+    f->n = n;
+    f->TW = o->TW;
+    f->TF = o->TF;
+    f->TR = o->TR;
+    f->fp16_scale = o->fp16_scale;
+    f->nb = kPanelNB;
+    f->ldf = ((n > 0 ? n : 1) + 31) / 32 * 32;
+    const int64_t nn = n > 0 ? n : 1;
+    const int64_t nblk = (nn + kTrsvB - 1) / kTrsvB;
+    ir_status st = IR_OK;
+#define AL(ptr, bytes)                                                        \
+    do {                                                                      \
+        cudaError_t e_ = cudaMalloc((void **)&(ptr), (bytes));                \
+        if (e_ != cudaSuccess) { st = cuda_fail(e_, "cudaMalloc"); goto fail; } \
+    } while (0)
+    AL(f->AF, (size_t)nn * f->ldf * sizeof(float));
+    AL(f->ipiv, nn * sizeof(int32_t));
+    AL(f->perm, nn * sizeof(int32_t));
+    AL(f->swap_list, (1 + 4 * kPanelNB) * sizeof(int32_t));
+    if (o->TF != IR_F32) {
+        AL(f->Aop, (size_t)nn * kPanelNB * op_elem(o->TF));
+        AL(f->Bop, (size_t)nn * kPanelNB * op_elem(o->TF));
+    }
+    AL(f->Linv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
+    AL(f->Uinv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
+    AL(f->tags, (size_t)2 * nblk * kTrsvB * sizeof(unsigned long long));
+    AL(f->x, nn * sizeof(double));
+    AL(f->r, nn * sizeof(double));
+    AL(f->dev, sizeof(DevScalars));
+#undef AL
+    if (cudaMallocHost((void **)&f->host_dev, sizeof(DevScalars)) != cudaSuccess) {
+        st = IR_ENOMEM;
+        goto fail;
+    }
+    if (cudaMemset(f->AF, 0, (size_t)nn * f->ldf * sizeof(float)) != cudaSuccess ||
+        cudaMemset(f->tags, 0, (size_t)2 * nblk * kTrsvB * sizeof(unsigned long long)) != cudaSuccess) {
+        st = IR_ECUDA;
+        goto fail;
+    }
+    st = ensure_partials(ctx, nn);
+    if (st != IR_OK) goto fail;
+    f->epoch = 0;
+    *out = f;
+    return IR_OK;
+fail:
+    free_fact(f);
+    return st;
+}
+
+// Cast + blocked right-looking LU with partial pivoting + diagonal-block inverses.
+ir_status run_factor(ir_fact *f, cudaStream_t s) {
+    const int n = (int)f->n;
+    const int64_t ldf = f->ldf;
+    CK(cudaMemsetAsync(f->dev, 0, sizeof(DevScalars), s));
+    CK(cudaMemsetAsync(&f->dev->info, 0x7F, sizeof(int), s));
+    if (n == 0) return IR_OK;
+    const int use_scale = (f->TF == IR_F16 && f->fp16_scale) ? 1 : 0;
+    if (use_scale) RUN(KC_MAXABS, s, launch_maxabs(n, f->TW, f->A, f->lda, f->dev, f->ctx->sms, s));
+    RUN(KC_CAST, s, launch_cast(n, f->TW, f->A, f->lda, f->TF, use_scale, f->AF, ldf, f->dev, s));
+    RUN(KC_IOTA, s, launch_iota(n, f->perm, s));
+    const int NB = kPanelNB;
+    for (int j = 0; j < n; j += NB) {
+        const int nbp = (n - j < NB) ? n - j : NB;
+        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, f->swap_list, f->dev, f->TF,
+                        f->Aop, s));
+        RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, n, j, nbp, f->swap_list, s));
+        if (j + nbp < n) {
+            RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, n, j, NB, f->TF, f->Bop, s));
+            if (f->TF == IR_F32)
+                RUN(KC_GEMM_SIMT, s, launch_gemm_simt(f->AF, ldf, n, j, NB, s));
+            else
+                RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, f->TF, f->Aop, f->Bop, f->ctx->sms, f->dev, s));
+        }
+    }
+    RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, s));
+    return IR_OK;
+}
+
+ir_status read_dev(ir_fact *f, cudaStream_t s) {
+    CK(cudaMemcpyAsync(f->host_dev, f->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return IR_OK;
+}
+
+// Termination test of Sec. 5.1 after the k-th residual (rh[0..k], dh[0..k-1]).
+// Returns -1 to continue, else an ir_solve_status.
+int term_decide(const double *rh, const double *dh, int k, double bnorm, double eps_w,
+                const ir_term *t, bool tr_wider) {
+    const double rn = rh[k];
+    if (!std::isfinite(rn)) return IR_DIVERGED;
+    if (tr_wider) {
+        if (k >= 2 && dh[k - 1] >= t->Rmax * dh[k - 2]) return IR_STAGNATED;   // eq. (wilkterm)
+    } else {
+        const double tol = t->abs_rel_tol > 0 ? t->abs_rel_tol : t->Cr * eps_w;
+        if (rn <= tol * bnorm) return IR_CONVERGED;                           // eq. (residterm)
+        if (k >= 1 && rn >= t->Rmax * rh[k - 1]) return IR_STAGNATED;         // eq. (stag)
+    }
+    if (k >= t->litmax) return IR_MAXIT;
+    return -1;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ir_default_opts(ir_opts *o) {
+    if (!o) return;
+    o->TW = IR_F64;
+    o->TF = IR_F32;
+    o->TR = IR_F64;
+    o->fp16_scale = 1;
+    o->nb = 0;
+    o->autotune = 0;
+}
+
+void ir_default_term(ir_term *t) {
+    if (!t) return;
+    t->Cr = 1.0;
+    t->Ce = 1.0;
+    t->Rmax = 0.5;
+    t->litmax = 10;
+    t->mode = 0;
+    t->abs_rel_tol = 0.0;
+}
+
+const char *ir_last_error(void) { return g_last_error; }
+
+unsigned long long ir_kernel_launches(void) { return ir::launches(); }
+
+void ir_profile_start(void) {
+    g_prof.on = true;
+    g_prof.used = 0;
+    g_prof.recs.clear();
+}
+
+int ir_profile_stop(double *ms, int *counts, int max_kinds) {
+    const bool was_on = g_prof.on;
+    g_prof.on = false;
+    if (!was_on) return 0;
+    if (cudaDeviceSynchronize() != cudaSuccess) return -1;
+    for (int k = 0; k < max_kinds && k < KC_N; ++k) {
+        if (ms) ms[k] = 0.0;
+        if (counts) counts[k] = 0;
+    }
+    for (const ProfRec &r : g_prof.recs) {
+        float t = 0.f;
+        if (r.kind >= max_kinds || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess) continue;
+        if (ms) ms[r.kind] += t;
+        if (counts) counts[r.kind] += 1;
+    }
+    g_prof.recs.clear();
+    return KC_N;
+}
+
+const char *ir_profile_kind(int k) { return (k >= 0 && k < KC_N) ? kKindNames[k] : ""; }
+
+ir_status ir_init(int device, ir_ctx **out) {
+    if (!out) return IR_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    CK(cudaGetDeviceCount(&ndev));
+    if (device < 0 || device >= ndev) return IR_EINVAL;
+    CK(cudaSetDevice(device));
+    cudaDeviceProp p;
+    CK(cudaGetDeviceProperties(&p, device));
+    if (p.major != 10 || p.minor != 3) {
+        snprintf(g_last_error, sizeof g_last_error, "device %d is sm_%d%d; this library is built for sm_103a",
+                 device, p.major, p.minor);
+        return IR_EUNSUPPORTED;
+    }
+    ir_ctx *c = new (std::nothrow) ir_ctx();
+    if (!c) return IR_ENOMEM;
+    c->device = device;
+    c->sms = p.multiProcessorCount;
+    c->partials = nullptr;
+    c->partials_cap = 0;
+    if (cudaMalloc(&c->rnorm_tmp, sizeof(double)) != cudaSuccess) {
+        delete c;
+        return IR_ENOMEM;
+    }
+    *out = c;
+    return IR_OK;
+}
+
+void ir_finalize(ir_ctx *c) {
+    if (!c) return;
+    cudaFree(c->partials);
+    cudaFree(c->rnorm_tmp);
+    delete c;
+}
+
+ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda, const ir_opts *opts,
+                    void *stream, ir_fact **out) {
+    if (!ctx || !out || n < 0 || (n > 0 && !A) || lda < (n > 1 ? n : 1)) return IR_EINVAL;
+    *out = nullptr;
+    ir_opts o;
+    if (opts) o = *opts;
+    else ir_default_opts(&o);
+    if (!tw_ok(o.TW) || !tf_ok(o.TF) || o.TR != IR_F64) return IR_EINVAL;
+    if (o.nb != 0 && o.nb != kPanelNB) return IR_EUNSUPPORTED;
+    if (n > kMaxN) {
+        snprintf(g_last_error, sizeof g_last_error, "n = %lld exceeds the supported maximum %d",
+                 (long long)n, kMaxN);
+        return IR_EUNSUPPORTED;
+    }
+    CK(cudaSetDevice(ctx->device));
+    ir_fact *f = nullptr;
+    ir_status st = alloc_fact(ctx, n, &o, &f);
+    if (st != IR_OK) return st;
+    f->A = A;
+    f->lda = lda;
+    st = run_factor(f, (cudaStream_t)stream);
+    if (st != IR_OK) {
+        free_fact(f);
+        return st;
+    }
+    *out = f;
+    return IR_OK;
+}
+
+ir_status ir_refactor(ir_fact *f, const void *B, int64_t ldb, void *stream) {
+    if (!f || (f->n > 0 && !B) || ldb < (f->n > 1 ? f->n : 1)) return IR_EINVAL;
+    f->A = B;
+    f->lda = ldb;
+    return run_factor(f, (cudaStream_t)stream);
+}
+
+ir_status ir_fact_info(const ir_fact *fc, int64_t *info, int *nonfinite) {
+    if (!fc) return IR_EINVAL;
+    ir_fact *f = const_cast<ir_fact *>(fc);
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(f->host_dev, f->dev, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+    if (info) *info = f->host_dev->info == kInfoNone ? 0 : f->host_dev->info;
+    if (nonfinite) *nonfinite = f->host_dev->nonfinite;
+    return IR_OK;
+}
+
+ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void *stream,
+                   ir_report *rep) {
+    if (!f || (f->n > 0 && (!b || !x))) return IR_EINVAL;
+    ir_term t;
+    if (term) t = *term;
+    else ir_default_term(&t);
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = f->n;
+    ir_report R;
+    std::memset(&R, 0, sizeof R);
+    R.scale = 1.0;
+    if (n == 0) {
+        R.status = IR_CONVERGED;
+        if (rep) *rep = R;
+        return IR_OK;
+    }
+    CK(cudaSetDevice(f->ctx->device));
+    // factorization outcome
+    ir_status st = read_dev(f, s);
+    if (st != IR_OK) return st;
+    R.scale = f->host_dev->scale;
+    if (f->host_dev->nonfinite) {
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ENONFINITE;
+    }
+    if (f->host_dev->info != kInfoNone) {
+        R.info = f->host_dev->info;
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ESINGULAR;
+    }
+    // x = 0, r = b, rhist[0] = ||b||
+    CK(cudaMemsetAsync(&f->dev->bnorm_bits, 0, sizeof(unsigned long long), s));
+    RUN(KC_INIT, s, launch_init_rb(n, f->TW, b, f->r, f->x, f->dev, s));
+    CK(cudaMemcpyAsync(&f->dev->rnorm_bits, &f->dev->bnorm_bits, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToDevice, s));
+    st = read_dev(f, s);
+    if (st != IR_OK) return st;
+    if (f->host_dev->nonfinite) {
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ENONFINITE;
+    }
+    const double bnorm = bits_to_double(f->host_dev->bnorm_bits);
+    R.rhist[0] = bnorm;
+    const bool tr_wider = (f->TW == IR_F32);
+    const double eps_w = eps_of(f->TW);
+    int k = 0;
+    int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
+    while (status < 0) {
+        f->epoch += 1;
+        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, sizeof(unsigned long long), s));
+        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->perm, f->r, nullptr, nullptr,
+                            f->x, f->tags, f->epoch, f->dev, s));
+        RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
+                           f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
+        st = read_dev(f, s);
+        if (st != IR_OK) return st;
+        if (f->host_dev->timeout) {
+            snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the triangular solve timed out");
+            return IR_ETIMEOUT;
+        }
+        ++k;
+        R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
+        R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
+        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider);
+    }
+    RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
+    R.iters = k;
+    R.status = (ir_solve_status)status;
+    if (rep) {
+        CK(cudaStreamSynchronize(s));
+        *rep = R;
+    }
+    return IR_OK;
+}
+
+ir_status ir_lu_solve(ir_fact *f, const float *v, float *d, void *stream) {
+    if (!f || (f->n > 0 && (!v || !d))) return IR_EINVAL;
+    if (f->n == 0) return IR_OK;
+    CK(cudaSetDevice(f->ctx->device));
+    f->epoch += 1;
+    CK(launch_trsv_pair(f->AF, f->ldf, (int)f->n, f->Linv, f->Uinv, f->perm, nullptr, v, d, nullptr,
+                        f->tags, f->epoch, f->dev, (cudaStream_t)stream));
+    return IR_OK;
+}
+
+ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_t lda, const void *b,
+                      const double *x, double *r, double *rnorm, void *stream) {
+    if (!ctx || n < 0 || !tw_ok(TW) || lda < (n > 1 ? n : 1)) return IR_EINVAL;
+    if (n > 0 && (!A || !b || !x || !r || !rnorm)) return IR_EINVAL;
+    if (n == 0) {
+        if (rnorm) CK(cudaMemsetAsync(rnorm, 0, sizeof(double), (cudaStream_t)stream));
+        return IR_OK;
+    }
+    CK(cudaSetDevice(ctx->device));
+    ir_status st = ensure_partials(ctx, n);
+    if (st != IR_OK) return st;
+    CK(launch_residual(n, TW, A, lda, b, x, r, ctx->partials, ctx->partials_cap,
+                       reinterpret_cast<unsigned long long *>(rnorm), ctx->sms, (cudaStream_t)stream));
+    return IR_OK;
+}
+
+ir_status ir_fact_pivots(const ir_fact *f, int32_t *ipiv_host) {
+    if (!f || (f->n > 0 && !ipiv_host)) return IR_EINVAL;
+    if (f->n == 0) return IR_OK;
+    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpy(ipiv_host, f->ipiv, f->n * sizeof(int32_t), cudaMemcpyDeviceToHost));
+    return IR_OK;
+}
+
+ir_status ir_fact_factors(const ir_fact *f, float *LU_host, int64_t ld) {
+    if (!f || ld < (f->n > 1 ? f->n : 1) || (f->n > 0 && !LU_host)) return IR_EINVAL;
+    const int64_t n = f->n;
+    if (n == 0) return IR_OK;
+    float *tmp = (float *)std::malloc((size_t)n * f->ldf * sizeof(float));
+    if (!tmp) return IR_ENOMEM;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(tmp, f->AF, (size_t)n * f->ldf * sizeof(float), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+        std::free(tmp);
+        return cuda_fail(e, "ir_fact_factors");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        for (int64_t j = 0; j < n; ++j) LU_host[i + j * ld] = tmp[i * f->ldf + j];
+    std::free(tmp);
+    return IR_OK;
+}
+
+void ir_fact_destroy(ir_fact *f) { free_fact(f); }
+
+ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda, const void *b_host,
+                        void *x_host, const ir_opts *opts, const ir_term *term, void *stream,
+                        ir_report *rep) {
+    if (!ctx || n < 0 || lda < (n > 1 ? n : 1)) return IR_EINVAL;
+    if (n > 0 && (!A_host || !b_host || !x_host)) return IR_EINVAL;
+    ir_opts o;
+    if (opts) o = *opts;
+    else ir_default_opts(&o);
+    if (!tw_ok(o.TW)) return IR_EINVAL;
+    const size_t es = o.TW == IR_F64 ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(ctx->device));
+    void *dA = nullptr, *db = nullptr, *dx = nullptr;
+    ir_fact *f = nullptr;
+    ir_status st = IR_OK;
+    const int64_t nn = n > 0 ? n : 1;
+    cudaError_t e = cudaMalloc(&dA, (size_t)lda * nn * es);
+    if (e == cudaSuccess) e = cudaMalloc(&db, nn * es);
+    if (e == cudaSuccess) e = cudaMalloc(&dx, nn * es);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dA, A_host, (size_t)lda * n * es, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(db, b_host, n * es, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "ir_solve_host upload");
+        goto done;
+    }
+    st = ir_factor(ctx, n, dA, lda, &o, stream, &f);
+    if (st != IR_OK) goto done;
+    st = ir_solve(f, db, dx, term, stream, rep);
+    if (st != IR_OK) goto done;
+    if (n > 0) {
+        e = cudaMemcpyAsync(x_host, dx, n * es, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) st = cuda_fail(e, "ir_solve_host download");
+    }
+done:
+    if (f) ir_fact_destroy(f);
+    cudaFree(dA);
+    cudaFree(db);
+    cudaFree(dx);
+    return st;
+}
+
+const char *ir_strerror(ir_status s) {
+    switch (s) {
+    case IR_OK: return "ok";
+    case IR_EINVAL: return "invalid argument";
+    case IR_ENOMEM: return "device allocation failed";
+    case IR_ECUDA: return "CUDA runtime error";
+    case IR_ESINGULAR: return "zero pivot in the factorization";
+    case IR_ENONFINITE: return "non-finite value in A, b or the rounded copy";
+    case IR_ETIMEOUT: return "a bounded device wait timed out";
+    case IR_EUNSUPPORTED: return "unsupported size or configuration";
+    }
+    return "unknown status";
+}
+
+}  // extern "C"

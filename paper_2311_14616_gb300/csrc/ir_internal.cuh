@@ -1,0 +1,141 @@
+// Internal declarations of the GB300 iterative-refinement library.
+//
+// Data layout in HBM (per factorization handle):
+//   A      caller's working-precision matrix, column-major, borrowed (residual)
+//   AF     factorization copy, binary32, ROW-major with padded row stride ldf
+//          (row interchanges move contiguous rows; a panel row is contiguous)
+//   Aop    rTF(L21) of the current block step, row-major (K contiguous), TF dtype
+//   Bop    rTF(U12)^T of the current block step, row-major (K contiguous)
+//   Linv/Uinv  inverses of the 64x64 diagonal blocks of L and U (row-major)
+//   x      binary64 iterate (TR), r binary64 residual, y binary32 solve vector
+//   dev    small block of device scalars (norms as ordered bit patterns, flags)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ir.h"
+
+namespace ir {
+
+constexpr int kTrsvB = 64;        // row block of the triangular solves
+constexpr int kPanelNB = 64;      // panel width = outer block size
+constexpr int kPanelT = 512;      // threads per panel CTA (one row each)
+constexpr int kPanelMaxCluster = 16;
+constexpr int kMaxN = kPanelT * kPanelMaxCluster;  // 8192 rows per panel cluster
+
+// Device-side scalars.  Non-negative doubles are ordered like their bit
+// patterns, so maxima are kept with atomicMax on uint64 (deterministic).
+struct DevScalars {
+    unsigned long long rnorm_bits;   // ||r||_inf of the latest residual
+    unsigned long long dnorm_bits;   // ||d||_inf of the latest correction
+    unsigned long long bnorm_bits;   // ||b||_inf
+    unsigned long long amax_bits;    // max |a_ij| (binary16 scaling)
+    double scale;                    // s of the factorization copy
+    int info;                        // first zero pivot, 1-based (INT_MAX = none)
+    int nonfinite;                   // 1: NaN/Inf met in A, b or the rounded copy
+    int timeout;                     // 1: a bounded wait gave up
+    int pad;
+    unsigned int ticket[2];          // CTA ticket counters of the two solves
+};
+
+}  // namespace ir
+
+struct ir_ctx {
+    int device;
+    int sms;
+    double *partials;        // residual split-K partial sums
+    int64_t partials_cap;    // capacity in doubles
+    double *rnorm_tmp;       // scratch scalar for ir_residual
+};
+
+struct ir_fact {
+    ir_ctx *ctx;
+    int64_t n;
+    ir_dtype TW, TF, TR;
+    int fp16_scale;
+    int nb;
+    const void *A;
+    int64_t lda;
+    int64_t ldf;             // row stride of AF in floats (multiple of 32)
+    float *AF;
+    int32_t *ipiv;           // 0-based pivots
+    int32_t *perm;           // (P A)[i] = A[perm[i]]
+    int32_t *swap_list;      // 1 + 2*2*NB ints: count, then (dst, src) pairs of a panel
+    void *Aop, *Bop;         // tensor-core operands (NULL for TF = F32)
+    float *Linv, *Uinv;      // diagonal-block inverses, nblk x 64 x 64
+    unsigned long long *tags;  // 2 x nblk*64 tagged solve values (epoch << 32 | bits)
+    unsigned epoch;            // tag of the latest solve
+    double *x, *r;           // binary64 iterate and residual
+    ir::DevScalars *dev;
+    ir::DevScalars *host_dev;  // pinned mirror
+};
+
+namespace ir {
+
+// ---- launch accounting and optional per-launcher event timing --------------
+void count_launch();                       // one call per kernel launch
+unsigned long long launches();
+
+// ---- launchers (each returns the launch error) -----------------------------
+cudaError_t launch_maxabs(int64_t n, ir_dtype tw, const void *A, int64_t lda, DevScalars *dev,
+                          int sms, cudaStream_t s);
+cudaError_t launch_cast(int64_t n, ir_dtype tw, const void *A, int64_t lda, ir_dtype tf,
+                        int use_scale, float *AF, int64_t ldf, DevScalars *dev, cudaStream_t s);
+cudaError_t launch_init_rb(int64_t n, ir_dtype tw, const void *b, double *r, double *x,
+                           DevScalars *dev, cudaStream_t s);
+cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s);
+
+cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
+                         int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
+                         void *Aop, cudaStream_t s);
+cudaError_t launch_laswp(float *AF, int64_t ldf, int n, int j, int nbp, const int32_t *swap_list,
+                         cudaStream_t s);
+cudaError_t launch_trsm(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, void *Bop,
+                        cudaStream_t s);
+cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, cudaStream_t s);
+cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf,
+                           const void *Aop, const void *Bop, int sms, DevScalars *dev,
+                           cudaStream_t s);
+cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
+
+cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
+                            cudaStream_t s);
+cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *Linv,
+                             const float *Uinv, const int32_t *perm, const double *r,
+                             const float *vin, float *dout, double *x,
+                             unsigned long long *tags, unsigned epoch, DevScalars *dev,
+                             cudaStream_t s);
+cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *b,
+                            const double *x, double *r, double *partials, int64_t partials_cap,
+                            unsigned long long *rnorm_bits, int sms, cudaStream_t s);
+int64_t residual_partials_needed(int64_t n, int sms);
+
+// ---- device helpers --------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Bounded wait limit for inter-CTA flags (nanoseconds).
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(unsigned long long *p, double v) {
+    // |v| >= 0 (or NaN with the sign cleared): bit patterns order like values
+    atomicMax(p, static_cast<unsigned long long>(__double_as_longlong(fabs(v))));
+}
+
+}  // namespace ir

@@ -1,0 +1,183 @@
+// Elementwise kernels: the copy to the factorization precision (A_F = I_W^F(s A),
+// Sec. 1), the max |a_ij| pass of the binary16 scaling, and the setup/finish of
+// the refinement vectors (x = 0, r = b, Algorithm IR).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ir_internal.cuh"
+
+namespace ir {
+namespace {
+
+template <typename TW>
+__device__ __forceinline__ double ld_w(const TW *p) { return static_cast<double>(__ldg(p)); }
+
+// max |a_ij| over a column-major n x n matrix; NaN/Inf raise the non-finite flag.
+template <typename TW>
+__global__ void k_maxabs(int64_t n, const TW *A, int64_t lda, DevScalars *dev) {
+    double m = 0.0;
+    int bad = 0;
+    const int64_t total = n * n;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t j = e / n, i = e - j * n;
+        double a = ld_w(A + i + j * lda);
+        if (!isfinite(a)) bad = 1;
+        m = fmax(m, fabs(a));
+    }
+    // block reduction of the maximum
+    __shared__ double sm[32];
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            atomic_max_nonneg(&dev->amax_bits, m);
+            if (bad) atomicExch(&dev->nonfinite, 1);
+        }
+    }
+}
+
+// Round a binary32 value to TF, kept in binary32 (hardware conversions:
+// cvt.rna.tf32.f32 = nearest, ties away; bf16/fp16 = nearest, ties to even).
+__device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
+    switch (tf) {
+    case IR_TF32: {
+        uint32_t u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+        return __uint_as_float(u);
+    }
+    case IR_BF16: return __bfloat162float(__float2bfloat16_rn(v));
+    case IR_F16: return __half2float(__float2half_rn(v));
+    default: return v;
+    }
+}
+
+// A (column-major, TW) -> AF (row-major binary32 holding TF values):
+// AF[i][j] = rTF(fl32(s * a_ij)).  32 x 32 tiles through shared memory so that
+// both the column-major read and the row-major write are coalesced.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_cast(int64_t n, const TW *A, int64_t lda, ir_dtype tf,
+                                              int use_scale, float *AF, int64_t ldf,
+                                              DevScalars *dev) {
+    __shared__ float tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.x * 32, j0 = (int64_t)blockIdx.y * 32;
+    double s = 1.0;
+    if (use_scale) {
+        double m = __longlong_as_double((long long)dev->amax_bits);
+        s = (m > 0.0 && isfinite(m)) ? 1024.0 / m : 1.0;
+    }
+    if (blockIdx.x == 0 && blockIdx.y == 0 && threadIdx.x == 0 && threadIdx.y == 0) dev->scale = s;
+    int bad = 0;
+    // read: threadIdx.x runs down a column (i), coalesced in column-major A
+    for (int jj = threadIdx.y; jj < 32; jj += 8) {
+        int64_t i = i0 + threadIdx.x, j = j0 + jj;
+        float v = 0.f;
+        if (i < n && j < n) {
+            double a = ld_w(A + i + j * lda);
+            v = round_tf(__double2float_rn(s * a), tf);
+            if (!isfinite(v)) bad = 1;
+        }
+        tile[jj][threadIdx.x] = v;
+    }
+    __syncthreads();
+    // write: threadIdx.x runs along a row (j), coalesced in row-major AF
+    for (int ii = threadIdx.y; ii < 32; ii += 8) {
+        int64_t i = i0 + ii, j = j0 + threadIdx.x;
+        if (i < n && j < n) AF[i * ldf + j] = tile[threadIdx.x][ii];
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && threadIdx.y == 0) atomicExch(&dev->nonfinite, 1);
+}
+
+// x = 0, r = b promoted to binary64, ||b||_inf.
+template <typename TW>
+__global__ void k_init_rb(int64_t n, const TW *b, double *r, double *x, DevScalars *dev) {
+    double m = 0.0;
+    int bad = 0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double v = static_cast<double>(b[i]);
+        if (!isfinite(v)) bad = 1;
+        r[i] = v;
+        x[i] = 0.0;
+        m = fmax(m, fabs(v));
+    }
+    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ double sm[32];
+    if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = m;
+    bad = __syncthreads_or(bad);
+    if (threadIdx.x < 32) {
+        m = threadIdx.x < (blockDim.x >> 5) ? sm[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+        if (threadIdx.x == 0) {
+            atomic_max_nonneg(&dev->bnorm_bits, m);
+            if (bad) atomicExch(&dev->nonfinite, 1);
+        }
+    }
+}
+
+template <typename TW>
+__global__ void k_store_x(int64_t n, const double *x, TW *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = static_cast<TW>(x[i]);
+}
+
+int grid_for(int64_t work, int threads, int cap) {
+    int64_t g = (work + threads - 1) / threads;
+    if (g < 1) g = 1;
+    return (int)(g < cap ? g : cap);
+}
+
+}  // namespace
+
+cudaError_t launch_maxabs(int64_t n, ir_dtype tw, const void *A, int64_t lda, DevScalars *dev,
+                          int sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int g = grid_for(n * n, 512, sms * 8);
+    count_launch();
+    if (tw == IR_F64)
+        k_maxabs<double><<<g, 512, 0, s>>>(n, (const double *)A, lda, dev);
+    else
+        k_maxabs<float><<<g, 512, 0, s>>>(n, (const float *)A, lda, dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cast(int64_t n, ir_dtype tw, const void *A, int64_t lda, ir_dtype tf,
+                        int use_scale, float *AF, int64_t ldf, DevScalars *dev, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    dim3 grid((unsigned)((n + 31) / 32), (unsigned)((n + 31) / 32)), block(32, 8);
+    count_launch();
+    if (tw == IR_F64)
+        k_cast<double><<<grid, block, 0, s>>>(n, (const double *)A, lda, tf, use_scale, AF, ldf, dev);
+    else
+        k_cast<float><<<grid, block, 0, s>>>(n, (const float *)A, lda, tf, use_scale, AF, ldf, dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_init_rb(int64_t n, ir_dtype tw, const void *b, double *r, double *x,
+                           DevScalars *dev, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int g = grid_for(n, 256, 1024);
+    count_launch();
+    if (tw == IR_F64)
+        k_init_rb<double><<<g, 256, 0, s>>>(n, (const double *)b, r, x, dev);
+    else
+        k_init_rb<float><<<g, 256, 0, s>>>(n, (const float *)b, r, x, dev);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    int g = grid_for(n, 256, 1024);
+    count_launch();
+    if (tw == IR_F64)
+        k_store_x<double><<<g, 256, 0, s>>>(n, x, (double *)out);
+    else
+        k_store_x<float><<<g, 256, 0, s>>>(n, x, (float *)out);
+    return cudaGetLastError();
+}
+
+}  // namespace ir

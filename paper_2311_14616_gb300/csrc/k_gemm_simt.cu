@@ -1,0 +1,95 @@
+// binary32 trailing update of the blocked LU: A22 <- A22 - L21 U12 with every
+// element updated by the fmaf chain acc = fmaf(-l_im, u_mc, acc), m ascending
+// from the stored value -- the same operations as the unblocked right-looking
+// algorithm, so the binary32 factors are bitwise those of the plain LU.
+#include "ir_internal.cuh"
+
+namespace ir {
+namespace {
+
+constexpr int BM = 128, BN = 128, BK = 32, NB = kPanelNB;
+
+__global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n, int j) {
+    __shared__ __align__(16) float As[BK][BM + 4];   // As[k][i] = L21[i][k]
+    __shared__ __align__(16) float Bs[BK][BN + 4];   // Bs[k][c] = U12[k][c]
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int i0 = j + NB + blockIdx.y * BM;
+    const int c0 = j + NB + blockIdx.x * BN;
+
+    // C micro-tile: rows i0 + {ty*4 + r, 64 + ty*4 + r}, cols c0 + {tx*4 + q, 64 + tx*4 + q}
+    float acc[8][8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c0 + h * 64 + tx * 4;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n && c < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c);
+            acc[r][h * 4 + 0] = v.x; acc[r][h * 4 + 1] = v.y;
+            acc[r][h * 4 + 2] = v.z; acc[r][h * 4 + 3] = v.w;
+        }
+    }
+    for (int kb = 0; kb < NB; kb += BK) {
+        // A tile: 128 rows x 32 k (each row 128 contiguous bytes), stored transposed
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = t + q * 256;
+            const int row = idx >> 3, kq = (idx & 7) * 4;
+            const int i = i0 + row;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (i < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + kb + kq);
+            As[kq + 0][row] = v.x; As[kq + 1][row] = v.y; As[kq + 2][row] = v.z; As[kq + 3][row] = v.w;
+        }
+        // B tile: 32 k x 128 cols (rows of U12 are contiguous)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int idx = t + q * 256;
+            const int m = idx >> 5, cq = (idx & 31) * 4;
+            const int c = c0 + cq;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (c < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + kb + m) * ldf + c);
+            *reinterpret_cast<float4 *>(&Bs[m][cq]) = v;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int m = 0; m < BK; ++m) {
+            const float4 a0 = *reinterpret_cast<const float4 *>(&As[m][ty * 4]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&As[m][64 + ty * 4]);
+            const float4 b0 = *reinterpret_cast<const float4 *>(&Bs[m][tx * 4]);
+            const float4 b1 = *reinterpret_cast<const float4 *>(&Bs[m][64 + tx * 4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+            const float bv[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+#pragma unroll
+            for (int r = 0; r < 8; ++r)
+#pragma unroll
+                for (int q = 0; q < 8; ++q) acc[r][q] = fmaf(-av[r], bv[q], acc[r][q]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+        const int i = i0 + (r < 4 ? ty * 4 + r : 64 + ty * 4 + (r - 4));
+        if (i >= n) continue;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int c = c0 + h * 64 + tx * 4;
+            if (c < n)
+                *reinterpret_cast<float4 *>(AF + (int64_t)i * ldf + c) =
+                    make_float4(acc[r][h * 4 + 0], acc[r][h * 4 + 1], acc[r][h * 4 + 2], acc[r][h * 4 + 3]);
+        }
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, cudaStream_t s) {
+    const int m = n - (j + nb);
+    if (m <= 0) return cudaSuccess;
+    dim3 grid((m + BN - 1) / BN, (m + BM - 1) / BM);
+    count_launch();
+    k_gemm_simt<<<grid, 256, 0, s>>>(AF, ldf, n, j);
+    return cudaGetLastError();
+}
+
+}  // namespace ir

@@ -1,0 +1,397 @@
+// Tensor-core trailing update of the mixed-precision blocked LU:
+//     A22 <- A22 - rTF(L21) rTF(U12)
+// with the TF-rounded operands (TF32, bf16 or fp16, written by the panel and
+// U12 kernels) multiplied by tcgen05.mma with binary32 accumulation in tensor
+// memory (TMEM), then subtracted from the binary32 matrix in the epilogue.
+//
+// Persistent, warp-specialised kernel, one CTA per SM:
+//   warp 0      TMA producer: both operand tiles of a 128x128 output tile
+//               (K = 64) into a 2-stage shared-memory ring (128-byte swizzle)
+//   warp 1      allocates TMEM (2 accumulators x 128 columns) and issues the
+//               MMAs from one thread; tcgen05.commit frees the stage and
+//               signals the accumulator
+//   warps 2-9   epilogue: tcgen05.ld the accumulator, C -= D in global memory
+// Every mbarrier wait is bounded (globaltimer); on timeout the CTA records
+// the error, waits (bounded) for its own copies in flight, frees TMEM and
+// returns.
+#include <cuda.h>
+
+#include "ir_internal.cuh"
+
+namespace ir {
+namespace {
+
+constexpr int BM = 128, BN = 128, K = kPanelNB;
+constexpr int kStages = 2;
+constexpr int kAtomBytes = BM * 128;      // one 128-row x 128-byte swizzle tile = 16 KB
+constexpr int kThreads = 320;             // 10 warps
+constexpr int kEpiThreads = 256;
+constexpr unsigned kTmemCols = 2 * BN;    // double-buffered accumulator
+
+struct TcParams {
+    float *C;
+    int64_t ldc;
+    int M, N;
+    int tiles_n, num_tiles;
+    unsigned idesc;
+    int *timeout;
+};
+
+__device__ __forceinline__ void mbar_init(unsigned addr, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned addr, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// Bounded wait; returns false (and raises the flags) after the time limit or
+// when another role already aborted.
+__device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volatile int *abort_flag,
+                                          int *timeout) {
+    if (mbar_try_wait(addr, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(addr, parity)) {
+        if (*abort_flag) return false;
+        if (globaltimer() - t0 > kWaitLimitNs) {
+            *abort_flag = 1;
+            atomicExch(timeout, 1);
+            return false;
+        }
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive(unsigned addr) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(addr)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned addr, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map, int c0, int c1,
+                                            unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor, K-major operand with 128-byte swizzle:
+// start address >> 4 (bits 0-13), leading byte offset 16 B (unused for this
+// layout), stride byte offset 1024 B between 8-row groups (bits 32-45),
+// descriptor version 1 (bits 46-47), swizzle mode 2 = 128B (bits 61-63).
+__device__ __forceinline__ uint64_t make_desc(unsigned saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16u >> 4) << 16;
+    d |= (uint64_t)(1024u >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(unsigned dtmem, uint64_t a, uint64_t b, unsigned idesc, int acc) {
+    if (TF32)
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+    else
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+            "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+            "l"(a), "l"(b), "r"(idesc), "r"(acc)
+            : "memory");
+}
+__device__ __forceinline__ void mma_commit(unsigned mbar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr)
+        : "memory");
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+}
+
+template <int KATOMS>   // 128-byte K atoms per operand row: 2 for TF32, 1 for 16-bit types
+__global__ void __launch_bounds__(kThreads, 1)
+    k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+              TcParams p) {
+    constexpr bool kTF32 = (KATOMS == 2);
+    constexpr int kAtomElems = kTF32 ? 32 : 64;          // elements per 128-byte K atom
+    constexpr int kKSteps = 128 / 32;                    // MMAs per atom (32-byte K per MMA)
+    constexpr unsigned kStageBytes = 2u * KATOMS * kAtomBytes;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned operand area
+    const unsigned sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    const unsigned sA = sbase;                                   // stages x KATOMS x 16 KB
+    const unsigned sB = sbase + kStages * KATOMS * kAtomBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + 2 * kStages * KATOMS * kAtomBytes);
+    const unsigned bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
+    const unsigned drain_bar = bar0 + 8u * (2 * kStages + 4);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * kStages + 5);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), kEpiThreads);
+        }
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0;
+            unsigned ph = 0;
+            unsigned last_ph[kStages];  // parity of the latest fill of each stage
+            bool issued[kStages];
+            for (int q = 0; q < kStages; ++q) issued[q] = false;
+            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+                const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+                if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.timeout)) break;
+                mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+#pragma unroll
+                for (int q = 0; q < KATOMS; ++q) {
+                    tma_load_2d(sA + (s * KATOMS + q) * kAtomBytes, &tmA, q * kAtomElems, tm * BM, full_bar(s));
+                    tma_load_2d(sB + (s * KATOMS + q) * kAtomBytes, &tmB, q * kAtomElems, tn * BN, full_bar(s));
+                }
+                last_ph[s] = ph;
+                issued[s] = true;
+                if (++s == kStages) { s = 0; ph ^= 1u; }
+            }
+            if (*abort_flag) {
+                // drain: wait (bounded) until the copies this thread issued have landed
+                int dummy = 0;
+                volatile int no_abort = 0;
+                for (int q = 0; q < kStages; ++q)
+                    if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, &dummy);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            unsigned ph = 0;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+                const int ab = it & 1;
+                const unsigned aph = (unsigned)(it >> 1) & 1u;
+                if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, p.timeout)) break;
+                tc_fence_after();
+                if (!mbar_wait(full_bar(s), ph, abort_flag, p.timeout)) break;
+                tc_fence_after();
+                const unsigned dt = tmem_base + (unsigned)(ab * BN);
+#pragma unroll
+                for (int q = 0; q < KATOMS; ++q)
+#pragma unroll
+                    for (int kk = 0; kk < kKSteps; ++kk) {
+                        const uint64_t ad = make_desc(sA + (s * KATOMS + q) * kAtomBytes + kk * 32);
+                        const uint64_t bd = make_desc(sB + (s * KATOMS + q) * kAtomBytes + kk * 32);
+                        mma<kTF32>(dt, ad, bd, p.idesc, (q | kk) != 0);
+                    }
+                mma_commit(empty_bar(s));
+                mma_commit(accf_bar(ab));
+                if (++s == kStages) { s = 0; ph ^= 1u; }
+            }
+            if (*abort_flag) {
+                // wait (bounded) until the tensor core has finished everything issued
+                int dummy = 0;
+                volatile int no_abort = 0;
+                mma_commit(drain_bar);
+                mbar_wait(drain_bar, 0u, &no_abort, &dummy);
+            }
+        }
+    } else {
+        // epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+        const int quarter = warp & 3;
+        const int half = (warp - 2) >> 2;
+        int it = 0;
+        for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+            const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
+            const int ab = it & 1;
+            const unsigned aph = (unsigned)(it >> 1) & 1u;
+            if (!mbar_wait(accf_bar(ab), aph, abort_flag, p.timeout)) break;
+            tc_fence_after();
+            const int row = tm * BM + quarter * 32 + lane;
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                const int chunk = half * 2 + cc;
+                float v[32];
+                tmem_ld32(tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * BN + chunk * 32), v);
+                const int col0 = tn * BN + chunk * 32;
+                if (row < p.M) {
+                    float *crow = p.C + (int64_t)row * p.ldc + col0;
+                    float4 c[8];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (col0 + 4 * q < p.N) c[q] = reinterpret_cast<const float4 *>(crow)[q];
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (col0 + 4 * q < p.N) {
+                            c[q].x -= v[4 * q + 0];
+                            c[q].y -= v[4 * q + 1];
+                            c[q].z -= v[4 * q + 2];
+                            c[q].w -= v[4 * q + 3];
+                            reinterpret_cast<float4 *>(crow)[q] = c[q];
+                        }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acce_bar(ab));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kTmemCols)
+                     : "memory");
+    }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                  const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                  const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encoder() {
+    static EncodeTiledFn fn = nullptr;
+    if (!fn) {
+        void *ptr = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &ptr, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(ptr);
+    }
+    return fn;
+}
+
+// rows x K operand, row-major, K contiguous; box = one 128-byte K atom x 128 rows.
+bool make_map(CUtensorMap *m, const void *base, int rows, ir_dtype tf) {
+    EncodeTiledFn enc = get_encoder();
+    if (!enc) return false;
+    const int esz = (tf == IR_TF32) ? 4 : 2;
+    const CUtensorMapDataType dt = (tf == IR_TF32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                   : (tf == IR_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                                     : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)K * esz};
+    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Instruction descriptor for kind::tf32 / kind::f16: D = F32 (bits 4-5 = 1),
+// A/B format (bits 7-9 / 10-12: F16 0, BF16 1, TF32 2), both K-major,
+// N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+unsigned make_idesc(ir_dtype tf) {
+    const unsigned fmt = (tf == IR_TF32) ? 2u : (tf == IR_BF16) ? 1u : 0u;
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(BM >> 4) << 24);
+}
+
+// At least 116 KB, so that one CTA (one TMEM allocation of 256 columns) runs per SM.
+template <int KATOMS>
+size_t smem_bytes() {
+    const size_t need = 1024 + 2 * kStages * KATOMS * kAtomBytes + 8 * (2 * kStages + 5) + 16;
+    return need > 116 * 1024 ? need : 116 * 1024;
+}
+
+}  // namespace
+
+cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, const void *Aop,
+                           const void *Bop, int sms, DevScalars *dev, cudaStream_t s) {
+    const int m = n - (j + nb);
+    if (m <= 0) return cudaSuccess;
+    if (nb != K) return cudaErrorInvalidValue;
+    CUtensorMap ta, tb;
+    if (!make_map(&ta, Aop, m, tf) || !make_map(&tb, Bop, m, tf)) return cudaErrorInvalidValue;
+    TcParams p;
+    p.C = AF + (int64_t)(j + nb) * ldf + (j + nb);
+    p.ldc = ldf;
+    p.M = m;
+    p.N = m;
+    const int tiles_m = (m + BM - 1) / BM;
+    p.tiles_n = (m + BN - 1) / BN;
+    p.num_tiles = tiles_m * p.tiles_n;
+    p.idesc = make_idesc(tf);
+    p.timeout = &dev->timeout;
+    const int grid = p.num_tiles < sms ? p.num_tiles : sms;
+    if (tf == IR_TF32) {
+        static bool attr = false;
+        const size_t sm = smem_bytes<2>();
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        count_launch();
+        k_gemm_tc<2><<<grid, kThreads, sm, s>>>(ta, tb, p);
+    } else {
+        static bool attr = false;
+        const size_t sm = smem_bytes<1>();
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        count_launch();
+        k_gemm_tc<1><<<grid, kThreads, sm, s>>>(ta, tb, p);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ir

@@ -1,0 +1,385 @@
+// Panel factorization, row interchanges and the U12 triangular solve of the
+// blocked LU with partial pivoting ("Factor A = LU in precision TF",
+// Algorithm IR; lu! of Sec. 2.1.1).
+//
+// The binary32 operations are exactly those of the unblocked right-looking
+// algorithm: pivot = first row of maximal |a_ik|, l_ik = a_ik / a_kk (IEEE
+// division), a_ij = fmaf(-l_ik, u_kj, a_ij) with k ascending for every
+// element.  Blocking only regroups these chains, so the factors are bitwise
+// those of the unblocked algorithm whenever the trailing update is binary32.
+#include <climits>
+#include <cstddef>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "ir_internal.cuh"
+
+namespace ir {
+namespace {
+
+constexpr int NB = kPanelNB;
+constexpr int T = kPanelT;
+constexpr int NW = T / 32;
+
+// Every panel row carries the index of the row it started the panel in
+// ("origin"), so the panel's net permutation is known at the end without
+// replaying the interchanges.
+struct PanelSmem {
+    // row arrays first, each 16-byte aligned (they are accessed as float4)
+    alignas(16) float stage_row[NW][NB];     // per-warp candidate row
+    alignas(16) float slot_row[2][NB];       // this CTA's candidate, read by the cluster
+    alignas(16) float diag_row[2][NB];       // row k (owned by CTA 0), read by the winner's CTA
+    alignas(16) float urow[NB];              // pivot row, local copy
+    alignas(16) float drow[NB];              // old row k, local copy (winner's CTA)
+    float stage_val[NW];
+    int stage_pos[NW];
+    int stage_org[NW];
+    float slot_val[2];
+    int slot_pos[2];
+    int slot_org[2];
+    int diag_org[2];
+    int uorg, dorg;
+    int win_pos;
+};
+static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, slot_row) % 16 == 0 &&
+                  offsetof(PanelSmem, diag_row) % 16 == 0 && offsetof(PanelSmem, urow) % 16 == 0 &&
+                  offsetof(PanelSmem, drow) % 16 == 0,
+              "float4 rows of the panel's shared memory must be 16-byte aligned");
+
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ unsigned cluster_size() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                     : "memory");
+}
+__device__ __forceinline__ unsigned map_cta(unsigned local_addr, unsigned rank) {
+    unsigned r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ float ld_dsmem_f32(unsigned addr) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_dsmem_s32(unsigned addr) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
+    switch (tf) {
+    case IR_TF32: {
+        uint32_t u;
+        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
+        return __uint_as_float(u);
+    }
+    case IR_BF16: return __bfloat162float(__float2bfloat16_rn(v));
+    case IR_F16: return __half2float(__float2half_rn(v));
+    default: return v;
+    }
+}
+
+// Store one operand row (NB values, rounded to TF) into Aop/Bop.
+__device__ __forceinline__ void store_op_row(void *op, int64_t row, const float *v, ir_dtype tf) {
+    if (tf == IR_TF32) {
+        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(op) + row * NB);
+#pragma unroll
+        for (int c = 0; c < NB; c += 4)
+            dst[c / 4] = make_float4(round_tf(v[c], tf), round_tf(v[c + 1], tf), round_tf(v[c + 2], tf),
+                                     round_tf(v[c + 3], tf));
+    } else if (tf == IR_BF16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(op) + row * NB);
+#pragma unroll
+        for (int c = 0; c < NB; c += 8) {
+            __nv_bfloat162 p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p[q] = __floats2bfloat162_rn(v[c + 2 * q], v[c + 2 * q + 1]);
+            dst[c / 8] = *reinterpret_cast<uint4 *>(p);
+        }
+    } else if (tf == IR_F16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__half *>(op) + row * NB);
+#pragma unroll
+        for (int c = 0; c < NB; c += 8) {
+            __half2 p[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) p[q] = __floats2half2_rn(v[c + 2 * q], v[c + 2 * q + 1]);
+            dst[c / 8] = *reinterpret_cast<uint4 *>(p);
+        }
+    }
+}
+
+// One cluster factors the panel AF[j:n, j:j+nbp].  CTA c of the cluster owns
+// panel rows (positions) j + c*T + t, one per thread, held in registers.
+// Per column k: warp argmax (redux.sync) -> CTA candidate -> DSMEM exchange
+// across the cluster (one cluster barrier) -> winner row copied locally ->
+// interchange of positions k and p -> scale and rank-1 update in registers.
+// At the end the rows whose content moved are listed as (destination,
+// origin) pairs in swap_list (count in swap_list[0]) for the gather of the
+// other columns, and perm is composed with the panel's permutation.
+__global__ void __launch_bounds__(T, 1)
+    k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
+            int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
+    __shared__ __align__(16) PanelSmem sm;
+    const unsigned crank = cluster_rank();
+    const unsigned csize = cluster_size();
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int gi = j + (int)crank * T + t;           // this thread's row (position)
+    const bool valid = gi < n;
+
+    int org = gi;
+    if (crank == 0 && t == 0) swap_list[0] = 0;
+    float a[NB];
+    if (valid) {
+        const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)gi * ldf + j);
+#pragma unroll
+        for (int c = 0; c < NB; c += 4) {
+            float4 v = (c < nbp) ? src[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            a[c] = v.x; a[c + 1] = v.y; a[c + 2] = v.z; a[c + 3] = v.w;
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < NB; ++c) a[c] = 0.f;
+    }
+    cluster_sync_all();   // every CTA of the cluster is running
+
+    const unsigned slot_val_addr = smem_u32(&sm.slot_val[0]);
+    const unsigned slot_pos_addr = smem_u32(&sm.slot_pos[0]);
+    const unsigned slot_row_addr = smem_u32(&sm.slot_row[0][0]);
+    const unsigned diag_row_addr = smem_u32(&sm.diag_row[0][0]);
+    const unsigned slot_org_addr = smem_u32(&sm.slot_org[0]);
+    const unsigned diag_org_addr = smem_u32(&sm.diag_org[0]);
+
+#pragma unroll
+    for (int k = 0; k < NB; ++k) {
+        if (k < nbp) {
+            const int buf = k & 1;
+            const int pk = j + k;   // position being eliminated
+            // 1. local candidate: first maximal |a_ik| over rows i >= pk
+            const bool cand = valid && gi >= pk;
+            unsigned key = cand ? __float_as_uint(fabsf(a[k])) : 0u;
+            int pos = cand ? gi : INT_MAX;
+            unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+            int pmin = __reduce_min_sync(0xffffffffu, (key == kmax) ? pos : INT_MAX);
+            if (pos == pmin && pmin != INT_MAX) {
+#pragma unroll
+                for (int c = 0; c < NB; c += 4)
+                    *reinterpret_cast<float4 *>(&sm.stage_row[warp][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+                sm.stage_org[warp] = org;
+            }
+            if (lane == 0) { sm.stage_val[warp] = __uint_as_float(kmax); sm.stage_pos[warp] = pmin; }
+            // row k is published by its owner (always CTA 0: positions j..j+NB-1)
+            if (valid && gi == pk) {
+#pragma unroll
+                for (int c = 0; c < NB; c += 4)
+                    *reinterpret_cast<float4 *>(&sm.diag_row[buf][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+                sm.diag_org[buf] = org;
+            }
+            __syncthreads();
+            // 2. CTA candidate
+            if (warp == 0) {
+                unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
+                int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
+                unsigned bk = __reduce_max_sync(0xffffffffu, wk);
+                int bp = __reduce_min_sync(0xffffffffu, (wk == bk) ? wp : INT_MAX);
+                unsigned who = __ballot_sync(0xffffffffu, wp == bp && bp != INT_MAX);
+                int w = who ? __ffs(who) - 1 : 0;
+                for (int c = lane; c < NB; c += 32) sm.slot_row[buf][c] = sm.stage_row[w][c];
+                if (lane == 0) {
+                    sm.slot_val[buf] = __uint_as_float(bk);
+                    sm.slot_pos[buf] = bp;
+                    sm.slot_org[buf] = sm.stage_org[w];
+                }
+            }
+            // 3. exchange
+            cluster_sync_all();
+            // 4. cluster winner, pivot row and (for its owner) the old row k
+            if (warp == 0) {
+                unsigned ck = 0u;
+                int cp = INT_MAX;
+                if (lane < (int)csize) {
+                    ck = __float_as_uint(ld_dsmem_f32(map_cta(slot_val_addr + 4u * buf, lane)));
+                    cp = ld_dsmem_s32(map_cta(slot_pos_addr + 4u * buf, lane));
+                }
+                unsigned bk = __reduce_max_sync(0xffffffffu, ck);
+                int bp = __reduce_min_sync(0xffffffffu, (ck == bk) ? cp : INT_MAX);
+                unsigned who = __ballot_sync(0xffffffffu, cp == bp && bp != INT_MAX);
+                unsigned wc = who ? (unsigned)(__ffs(who) - 1) : 0u;
+                const unsigned rbase = map_cta(slot_row_addr + 4u * NB * buf, wc);
+                for (int c = lane; c < NB; c += 32) sm.urow[c] = ld_dsmem_f32(rbase + 4u * c);
+                if (lane == 0) sm.uorg = ld_dsmem_s32(map_cta(slot_org_addr + 4u * buf, wc));
+                const int p_off = bp - j;   // winner position relative to the panel
+                if (bp != pk && p_off >= (int)crank * T && p_off < ((int)crank + 1) * T) {
+                    const unsigned dbase = map_cta(diag_row_addr + 4u * NB * buf, 0u);
+                    for (int c = lane; c < NB; c += 32) sm.drow[c] = ld_dsmem_f32(dbase + 4u * c);
+                    if (lane == 0) sm.dorg = ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u));
+                }
+                if (lane == 0) sm.win_pos = bp;
+            }
+            __syncthreads();
+            const int p = sm.win_pos;
+            const float piv = sm.urow[k];
+            // 5. interchange of positions pk and p (whole panel rows)
+            if (valid && gi == pk) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) a[c] = sm.urow[c];
+                org = sm.uorg;
+            } else if (valid && gi == p) {
+#pragma unroll
+                for (int c = 0; c < NB; ++c) a[c] = sm.drow[c];
+                org = sm.dorg;
+            }
+            if (crank == 0 && t == 0) {
+                ipiv[pk] = p;
+                if (piv == 0.f) atomicMin(&dev->info, pk + 1);
+            }
+            // 6. scale column k and update the rest of the panel
+            if (valid && gi > pk) {
+                float l = a[k];
+                if (piv != 0.f) l = l / piv;
+                a[k] = l;
+#pragma unroll
+                for (int c = k + 1; c < NB; ++c) a[c] = fmaf(-l, sm.urow[c], a[c]);
+            }
+        }
+    }
+    // write the factored panel back, and rTF(L21) for the tensor-core update
+    if (valid) {
+        float4 *dst = reinterpret_cast<float4 *>(AF + (int64_t)gi * ldf + j);
+#pragma unroll
+        for (int c = 0; c < NB; c += 4)
+            if (c < nbp) dst[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+        if (has_trailing && Aop != nullptr && gi >= j + NB) store_op_row(Aop, gi - (j + NB), a, tf);
+    }
+    // net permutation of the panel: position gi now holds the row from org
+    int porg = 0;
+    const bool moved = valid && org != gi;
+    if (moved) {
+        int e = atomicAdd(&swap_list[0], 1);
+        swap_list[1 + 2 * e] = gi;
+        swap_list[2 + 2 * e] = org;
+        porg = perm[org];
+    }
+    cluster_sync_all();   // all reads of perm done; no CTA leaves while its smem may be read
+    if (moved) perm[gi] = porg;
+}
+
+// Apply the panel's row permutation to the columns outside the panel:
+// A[dst][c] = A[src][c] for the (dst, src) pairs the panel listed.  All
+// sources of a column are read before any destination is written.
+constexpr int kLaswpT = 64;   // 2*NB*kLaswpT floats of staging stay under 48 KB
+__global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int n, int j, int nbp,
+                                                  const int32_t *swap_list) {
+    __shared__ int sd[2 * NB], ss[2 * NB];
+    __shared__ float vals[2 * NB][kLaswpT];
+    const int cnt = swap_list[0];
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        sd[e] = swap_list[1 + 2 * e];
+        ss[e] = swap_list[2 + 2 * e];
+    }
+    __syncthreads();
+    int c = blockIdx.x * blockDim.x + threadIdx.x;
+    int ncols = n - nbp;
+    if (c >= ncols || cnt == 0) return;
+    if (c >= j) c += nbp;     // skip the panel's own columns
+    for (int e = 0; e < cnt; ++e) vals[e][threadIdx.x] = AF[(int64_t)ss[e] * ldf + c];
+    for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
+}
+
+// U12 = L11^{-1} A12 for the block row j..j+NB and columns j+NB..n.  One
+// thread per column, its NB values in registers, L11 in shared memory; each
+// u_kc is the fmaf chain over m < k in ascending order.  For tensor-core
+// updates the rounded values rTF(u_mc) are also written to Bop (row c).
+__global__ void __launch_bounds__(128) k_trsm(float *AF, int64_t ldf, int n, int j, ir_dtype tf,
+                                              void *Bop) {
+    __shared__ float L[NB][NB + 1];
+    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
+        int r = e / NB, m = e % NB;
+        L[r][m] = AF[(int64_t)(j + r) * ldf + j + m];
+    }
+    __syncthreads();
+    const int c = j + NB + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= n) return;
+    float u[NB];
+#pragma unroll
+    for (int m = 0; m < NB; ++m) u[m] = AF[(int64_t)(j + m) * ldf + c];
+#pragma unroll
+    for (int k = 1; k < NB; ++k)
+#pragma unroll
+        for (int m = 0; m < k; ++m) u[k] = fmaf(-L[k][m], u[m], u[k]);
+#pragma unroll
+    for (int m = 1; m < NB; ++m) AF[(int64_t)(j + m) * ldf + c] = u[m];
+    if (Bop != nullptr) store_op_row(Bop, c - (j + NB), u, tf);
+}
+
+__global__ void k_iota(int n, int32_t *perm) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = i;
+}
+
+}  // namespace
+
+cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
+                         int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
+                         void *Aop, cudaStream_t s) {
+    static bool attr_done = false;
+    if (!attr_done) {
+        cudaError_t e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e != cudaSuccess) return e;
+        attr_done = true;
+    }
+    int M = n - j;
+    int C = (M + T - 1) / T;
+    if (C > kPanelMaxCluster) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(T, 1, 1);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int has_trailing = (j + NB < n) ? 1 : 0;
+    count_launch();
+    return cudaLaunchKernelEx(&cfg, k_panel, AF, ldf, n, j, nbp, ipiv, perm, swap_list, dev, tf, Aop,
+                              has_trailing);
+}
+
+cudaError_t launch_laswp(float *AF, int64_t ldf, int n, int j, int nbp, const int32_t *swap_list,
+                         cudaStream_t s) {
+    int ncols = n - nbp;
+    if (ncols <= 0) return cudaSuccess;
+    count_launch();
+    k_laswp<<<(ncols + kLaswpT - 1) / kLaswpT, kLaswpT, 0, s>>>(AF, ldf, n, j, nbp, swap_list);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_trsm(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, void *Bop,
+                        cudaStream_t s) {
+    int ncols = n - (j + nb);
+    if (ncols <= 0) return cudaSuccess;
+    count_launch();
+    k_trsm<<<(ncols + 127) / 128, 128, 0, s>>>(AF, ldf, n, j, tf, tf == IR_F32 ? nullptr : Bop);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    count_launch();
+    k_iota<<<(n + 255) / 256, 256, 0, s>>>(n, perm);
+    return cudaGetLastError();
+}
+
+}  // namespace ir

@@ -1,0 +1,136 @@
+// Residual r = b - A x in binary64 (Algorithm IR, residual in TR; eq. xferrule:
+// A and b in TW are promoted exactly) and ||r||_inf.
+//
+// Pass 1: CTA (row block, column split) forms the partial sums of 256 rows over
+// a range of columns -- each thread two adjacent rows, loaded as one 16-byte
+// (binary64) or 8-byte (binary32) vector per column, so a warp reads 512 B of
+// a column-major A contiguously; x is staged in shared memory.
+// Pass 2: r_i = b_i - sum of the partials in split order (deterministic), and
+// the maximum |r_i| by an atomic maximum on ordered bit patterns.
+#include "ir_internal.cuh"
+
+namespace ir {
+namespace {
+
+constexpr int RT = 128;            // threads per CTA
+constexpr int RB = 2 * RT;         // rows per CTA
+constexpr int XCH = 512;           // x values staged per smem chunk
+
+template <typename TW>
+struct Vec2;
+template <>
+struct Vec2<double> { using T = double2; };
+template <>
+struct Vec2<float> { using T = float2; };
+
+template <typename TW>
+__global__ void __launch_bounds__(RT) k_resid_partial(int64_t n, const TW *A, int64_t lda,
+                                                      const double *x, int64_t cols_per_split,
+                                                      double *partials, int vec_ok) {
+    __shared__ double xs[XCH];
+    const int64_t i = (int64_t)blockIdx.x * RB + 2 * threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.y * cols_per_split;
+    int64_t c1 = c0 + cols_per_split;
+    if (c1 > n) c1 = n;
+    double s0 = 0.0, s1 = 0.0;
+    const bool both = (i + 1 < n);
+    for (int64_t cb = c0; cb < c1; cb += XCH) {
+        const int64_t ce = (cb + XCH < c1) ? cb + XCH : c1;
+        __syncthreads();
+        for (int64_t c = cb + threadIdx.x; c < ce; c += RT) xs[c - cb] = x[c];
+        __syncthreads();
+        if (i >= n) continue;
+        const TW *col = A + i + cb * lda;
+        const int cnt = (int)(ce - cb);
+        if (vec_ok && both) {
+            using V = typename Vec2<TW>::T;
+            int c = 0;
+            for (; c + 4 <= cnt; c += 4) {
+                const V a0 = __ldg(reinterpret_cast<const V *>(col + (int64_t)(c + 0) * lda));
+                const V a1 = __ldg(reinterpret_cast<const V *>(col + (int64_t)(c + 1) * lda));
+                const V a2 = __ldg(reinterpret_cast<const V *>(col + (int64_t)(c + 2) * lda));
+                const V a3 = __ldg(reinterpret_cast<const V *>(col + (int64_t)(c + 3) * lda));
+                s0 = fma((double)a0.x, xs[c + 0], s0); s1 = fma((double)a0.y, xs[c + 0], s1);
+                s0 = fma((double)a1.x, xs[c + 1], s0); s1 = fma((double)a1.y, xs[c + 1], s1);
+                s0 = fma((double)a2.x, xs[c + 2], s0); s1 = fma((double)a2.y, xs[c + 2], s1);
+                s0 = fma((double)a3.x, xs[c + 3], s0); s1 = fma((double)a3.y, xs[c + 3], s1);
+            }
+            for (; c < cnt; ++c) {
+                const V a = __ldg(reinterpret_cast<const V *>(col + (int64_t)c * lda));
+                s0 = fma((double)a.x, xs[c], s0);
+                s1 = fma((double)a.y, xs[c], s1);
+            }
+        } else {
+            for (int c = 0; c < cnt; ++c) {
+                s0 = fma((double)__ldg(col + (int64_t)c * lda), xs[c], s0);
+                if (both) s1 = fma((double)__ldg(col + (int64_t)c * lda + 1), xs[c], s1);
+            }
+        }
+    }
+    if (i < n) partials[blockIdx.y * n + i] = s0;
+    if (both) partials[blockIdx.y * n + i + 1] = s1;
+}
+
+template <typename TW>
+__global__ void k_resid_final(int64_t n, const TW *b, const double *partials, int nsplit,
+                              double *r, unsigned long long *rnorm_bits) {
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double s = partials[i];
+        for (int k = 1; k < nsplit; ++k) s += partials[(int64_t)k * n + i];
+        const double ri = (double)b[i] - s;
+        r[i] = ri;
+        m = fmax(m, fabs(ri));
+        if (ri != ri) m = ri;   // keep a NaN visible to the norm
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = (v != v || v > m) ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rnorm_bits, m);
+}
+
+int nsplit_for(int64_t n, int sms) {
+    const int64_t rowblocks = (n + RB - 1) / RB;
+    int64_t ns = (4 * (int64_t)sms + rowblocks - 1) / rowblocks;
+    int64_t maxs = (n + 63) / 64;           // at least 64 columns per split
+    if (ns > maxs) ns = maxs;
+    if (ns < 1) ns = 1;
+    return (int)ns;
+}
+
+}  // namespace
+
+int64_t residual_partials_needed(int64_t n, int sms) { return (int64_t)nsplit_for(n, sms) * n; }
+
+cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *b,
+                            const double *x, double *r, double *partials, int64_t partials_cap,
+                            unsigned long long *rnorm_bits, int sms, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const int ns = nsplit_for(n, sms);
+    if ((int64_t)ns * n > partials_cap) return cudaErrorInvalidValue;
+    const int64_t cps = (n + ns - 1) / ns;
+    const int64_t rowblocks = (n + RB - 1) / RB;
+    dim3 grid((unsigned)rowblocks, (unsigned)ns);
+    const size_t esz = (tw == IR_F64) ? 8 : 4;
+    const int vec_ok = ((lda % 2) == 0) && (((uintptr_t)A % (2 * esz)) == 0);
+    cudaError_t e = cudaMemsetAsync(rnorm_bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int fg = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
+    if (tw == IR_F64) {
+        count_launch();
+        k_resid_partial<double><<<grid, RT, 0, s>>>(n, (const double *)A, lda, x, cps, partials, vec_ok);
+        count_launch();
+        k_resid_final<double><<<fg, 256, 0, s>>>(n, (const double *)b, partials, ns, r, rnorm_bits);
+    } else {
+        count_launch();
+        k_resid_partial<float><<<grid, RT, 0, s>>>(n, (const float *)A, lda, x, cps, partials, vec_ok);
+        count_launch();
+        k_resid_final<float><<<fg, 256, 0, s>>>(n, (const float *)b, partials, ns, r, rnorm_bits);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace ir

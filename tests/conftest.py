@@ -28,3 +28,16 @@ def golden():
         with open(os.path.join(GOLDEN, name)) as f:
             return json.load(f)
     return load
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """One library context on cuda:0 (GPU tests only; the library must be built)."""
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_14616_gb300 import build, ir
+    build.build()
+    c = ir.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,153 @@
+"""Parity of the CUDA correction solve, residual and refinement loop with the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import irgen
+import oracle as O
+from gpu_util import dev_colmajor, dev_vec
+from paper_2311_14616_gb300 import ir
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("n", [1, 7, 64, 65, 130, 333, 1000])
+def test_lu_solve_matches_oracle_substitution(ctx, n):
+    """d = U^{-1} L^{-1} P v on the GPU's own factors vs the oracle's substitution."""
+    A, _ = irgen.case_random(n, 50 + n)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    LU, piv = f.factors(), f.pivots()
+    v = np.random.Generator(np.random.PCG64(n)).standard_normal(n).astype(np.float32)
+    d = f.lu_solve(dev_vec(v)).cpu().numpy()
+    do = O.getrs_f32(LU, piv, v)
+    # both are binary32 solves of the same triangular systems; their difference is
+    # bounded by the conditioning of the factors times the binary32 unit roundoff
+    L = np.tril(LU.astype(np.float64), -1) + np.eye(n)
+    U = np.triu(LU.astype(np.float64))
+    dx = np.linalg.solve(U, np.linalg.solve(L, O.apply_pivots(piv, v.astype(np.float64))))
+    cond = np.linalg.cond(L, np.inf) * np.linalg.cond(U, np.inf)
+    tol = 4 * n * 2.0 ** -24 * cond * np.max(np.abs(dx))
+    assert np.max(np.abs(d - dx)) <= tol
+    assert np.max(np.abs(do - dx)) <= tol
+
+
+@pytest.mark.parametrize("n", [1, 5, 255, 256, 257, 1023, 3000])
+@pytest.mark.parametrize("tw", [np.float64, np.float32])
+def test_residual_matches_oracle(ctx, n, tw):
+    A, b = irgen.case_gaussian(n, 70 + n)
+    A = np.asfortranarray(A.astype(tw))
+    b = b.astype(tw)
+    x = np.random.Generator(np.random.PCG64(n + 1)).standard_normal(n)
+    r, rn = ctx.residual(dev_colmajor(A), dev_vec(b), dev_vec(x))
+    r = r.cpu().numpy()
+    ro = O.residual(A, b, x)
+    g = 2 * n * 2.0 ** -53
+    bound = g * (np.abs(A).astype(np.float64) @ np.abs(x) + np.abs(b.astype(np.float64)))
+    assert np.all(np.abs(r - ro) <= bound + 1e-300)
+    assert float(rn.cpu()[0]) == np.max(np.abs(r))
+
+
+def _cfg_cases():
+    yield "green_a1_N256_f32", lambda: irgen.case_green(256, 1.0), O.F32, dict(abs_rel_tol=1e-13)
+    yield "green_sine_a800_N512_f32", lambda: irgen.case_green_sine(512)[:2], O.F32, {}
+    # TF32 factors of this kappa ~ 1e5 system contract slowly: allow 30 iterations
+    yield "green_sine_a800_N520_tf32", lambda: irgen.case_green_sine(520)[:2], O.TF32, dict(litmax=30)
+    yield "gauss_N700_f16", lambda: irgen.case_gaussian(700, 9), O.F16, {}
+    yield "gauss_N700_bf16", lambda: irgen.case_gaussian(700, 9), O.BF16, {}
+    yield "gauss_N300_tf32", lambda: irgen.case_gaussian(300, 4), O.TF32, {}
+    yield "random_N300_f32", lambda: irgen.case_random(300, 3), O.F32, {}
+
+
+@pytest.mark.parametrize("name,make,tf,term", list(_cfg_cases()), ids=[c[0] for c in _cfg_cases()])
+def test_ir_matches_oracle(ctx, name, make, tf, term):
+    A, b = make()
+    n = A.shape[0]
+    f = ctx.factor(dev_colmajor(A), tf=O.DTYPE_NAMES[tf])
+    x, rep = f.solve(dev_vec(b), term=ir.default_term(**term))
+    x = x.cpu().numpy()
+    ref = O.ir_solve(A, b, tf, O.Term(**term), nb=64)
+    xr = O.reference_solution(A, b)
+    kappa = O.cond_inf(A)
+    tol = O.parity_tol(kappa, O.F64)
+    assert rep.status == O.STATUS_NAMES[ref.status]
+    assert abs(rep.iters - ref.iters) <= 1
+    assert rep.rhist[0] == ref.rhist[0]
+    if ref.status == O.CONVERGED or tf == O.F32:
+        assert O.rel_err_inf(x, ref.x) <= tol, (O.rel_err_inf(x, ref.x), tol)
+        assert O.rel_err_inf(x, xr) <= tol, (O.rel_err_inf(x, xr), tol)
+
+
+def test_ir_promoted_single_single_double(ctx):
+    """TW = TF = binary32, TR = binary64 (Sec. 2.2.2): correction-stagnation rule and
+    the bound of Thm. carsonh1 against the promoted problem's solution."""
+    n = 384
+    A, b = irgen.case_svd(n, 1004, kappa=1e4)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    x, rep = f.solve(dev_vec(b))
+    ref = O.ir_solve(A, b, O.F32)
+    xp = O.reference_solution(A, b)
+    kappa = O.cond_inf(A)
+    assert x.dtype == torch.float32
+    assert rep.status == "stagnated" and ref.status == O.STAGNATED
+    bound = 4 * (n + 1) * kappa * 2.0 ** -53 + 2.0 ** -24
+    assert O.rel_err_inf(x.cpu().numpy(), xp) <= bound
+
+
+def test_ir_singular_and_nonfinite(ctx):
+    S = np.asfortranarray(np.ones((4, 4)))
+    f = ctx.factor(dev_colmajor(S), tf="f32")
+    with pytest.raises(ir.IRError) as e:
+        f.solve(dev_vec(np.ones(4)))
+    assert e.value.code == 4 and e.value.report.info == 2 and e.value.report.status == "failed"
+    A, b = irgen.case_gaussian(50, 2)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    b[7] = np.inf
+    with pytest.raises(ir.IRError) as e:
+        f.solve(dev_vec(b))
+    assert e.value.code == 5
+
+
+def test_ir_edge_sizes_and_zero_rhs(ctx):
+    A = np.array([[4.0]], order="F")
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    x, rep = f.solve(dev_vec(np.array([2.0])))
+    assert x.cpu().item() == 0.5 and rep.status == "converged"
+    A0 = np.zeros((0, 0), order="F")
+    f0 = ctx.factor(torch.zeros((0, 0), dtype=torch.float64, device="cuda"), tf="f32")
+    x0, rep0 = f0.solve(torch.zeros(0, dtype=torch.float64, device="cuda"))
+    assert x0.numel() == 0 and rep0.status == "converged"
+    A, _ = irgen.case_gaussian(90, 3)
+    f = ctx.factor(dev_colmajor(A), tf="tf32")
+    x, rep = f.solve(dev_vec(np.zeros(90)))
+    assert rep.status == "converged" and rep.iters == 0 and not torch.any(x)
+
+
+def test_invalid_arguments_and_limits(ctx):
+    from paper_2311_14616_gb300.ir import IRError
+    with pytest.raises(IRError) as e:
+        ctx.factor(torch.zeros((8193, 8193), dtype=torch.float32, device="cuda"), tf="f32")
+    assert e.value.code == 7
+    with pytest.raises(IRError) as e:
+        ctx.factor(dev_colmajor(np.eye(4)), tf=9)
+    assert e.value.code == 1
+
+
+def test_refactor_reuses_storage(ctx):
+    A, b = irgen.case_gaussian(200, 11)
+    B, _ = irgen.case_gaussian(200, 12)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    Bt = dev_colmajor(B)
+    f.refactor(Bt)
+    x, rep = f.solve(dev_vec(b))
+    xr = O.reference_solution(B, b)
+    assert rep.status == "converged"
+    assert O.rel_err_inf(x.cpu().numpy(), xr) <= 1e-12
+    assert np.array_equal(f.factors(), O.getrf_tf(O.cast(B, O.F32), O.F32)[0])
+
+
+def test_solve_host_end_to_end(ctx):
+    A, b = irgen.case_green(300, 800.0)
+    xh, rep = ctx.solve_host(torch.from_numpy(A), torch.from_numpy(b), tf="f32")
+    xr = O.reference_solution(A, b)
+    assert not xh.is_cuda
+    assert O.rel_err_inf(xh.numpy(), xr) <= O.parity_tol(O.cond_inf(A), O.F64)
