@@ -29,8 +29,8 @@ struct PanelSmem {
     alignas(16) float stage_row[NW][NB];     // per-warp candidate row
     alignas(16) float slot_row[2][NB];       // this CTA's candidate, read by the cluster
     alignas(16) float diag_row[2][NB];       // row k (owned by CTA 0), read by the winner's CTA
-    alignas(16) float urow[NB];              // pivot row, local copy
-    alignas(16) float drow[NB];              // old row k, local copy (winner's CTA)
+    alignas(16) float cand[kPanelMaxCluster][NB];   // every CTA's candidate row, local copies
+    alignas(16) float drow[NB];              // old row k, local copy
     float stage_val[NW];
     int stage_pos[NW];
     int stage_org[NW];
@@ -39,10 +39,10 @@ struct PanelSmem {
     int slot_org[2];
     int diag_org[2];
     int uorg, dorg;
-    int win_pos;
+    int win_pos, win_cta;
 };
 static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, slot_row) % 16 == 0 &&
-                  offsetof(PanelSmem, diag_row) % 16 == 0 && offsetof(PanelSmem, urow) % 16 == 0 &&
+                  offsetof(PanelSmem, diag_row) % 16 == 0 && offsetof(PanelSmem, cand) % 16 == 0 &&
                   offsetof(PanelSmem, drow) % 16 == 0,
               "float4 rows of the panel's shared memory must be 16-byte aligned");
 
@@ -202,36 +202,61 @@ __global__ void __launch_bounds__(T, 1)
             }
             // 3. exchange
             cluster_sync_all();
-            // 4. cluster winner, pivot row and (for its owner) the old row k
+            // 4. one round trip: every CTA's candidate (header and row) and row k;
+            //    the winner is picked locally
             if (warp == 0) {
                 unsigned ck = 0u;
-                int cp = INT_MAX;
+                int cp = INT_MAX, co = 0;
                 if (lane < (int)csize) {
                     ck = __float_as_uint(ld_dsmem_f32(map_cta(slot_val_addr + 4u * buf, lane)));
                     cp = ld_dsmem_s32(map_cta(slot_pos_addr + 4u * buf, lane));
+                    co = ld_dsmem_s32(map_cta(slot_org_addr + 4u * buf, lane));
                 }
+                const unsigned dbase = map_cta(diag_row_addr + 4u * NB * buf, 0u);
+                const float d0 = ld_dsmem_f32(dbase + 4u * lane);
+                const float d1 = ld_dsmem_f32(dbase + 4u * (lane + 32));
+                const int dorg = (lane == 0) ? ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u)) : 0;
+                // candidate rows in batches of 8 CTAs (all loads of a batch in flight)
+                for (int c0 = 0; c0 < (int)csize; c0 += 8) {
+                    float r0[8], r1[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        if (c0 + c < (int)csize) {
+                            const unsigned base = map_cta(slot_row_addr + 4u * NB * buf, (unsigned)(c0 + c));
+                            r0[c] = ld_dsmem_f32(base + 4u * lane);
+                            r1[c] = ld_dsmem_f32(base + 4u * (lane + 32));
+                        }
+                    }
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        if (c0 + c < (int)csize) {
+                            sm.cand[c0 + c][lane] = r0[c];
+                            sm.cand[c0 + c][lane + 32] = r1[c];
+                        }
+                    }
+                }
+                sm.drow[lane] = d0;
+                sm.drow[lane + 32] = d1;
                 unsigned bk = __reduce_max_sync(0xffffffffu, ck);
                 int bp = __reduce_min_sync(0xffffffffu, (ck == bk) ? cp : INT_MAX);
                 unsigned who = __ballot_sync(0xffffffffu, cp == bp && bp != INT_MAX);
-                unsigned wc = who ? (unsigned)(__ffs(who) - 1) : 0u;
-                const unsigned rbase = map_cta(slot_row_addr + 4u * NB * buf, wc);
-                for (int c = lane; c < NB; c += 32) sm.urow[c] = ld_dsmem_f32(rbase + 4u * c);
-                if (lane == 0) sm.uorg = ld_dsmem_s32(map_cta(slot_org_addr + 4u * buf, wc));
-                const int p_off = bp - j;   // winner position relative to the panel
-                if (bp != pk && p_off >= (int)crank * T && p_off < ((int)crank + 1) * T) {
-                    const unsigned dbase = map_cta(diag_row_addr + 4u * NB * buf, 0u);
-                    for (int c = lane; c < NB; c += 32) sm.drow[c] = ld_dsmem_f32(dbase + 4u * c);
-                    if (lane == 0) sm.dorg = ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u));
+                const int wc = who ? __ffs(who) - 1 : 0;
+                const int worg = __shfl_sync(0xffffffffu, co, wc);
+                if (lane == 0) {
+                    sm.win_pos = bp;
+                    sm.win_cta = wc;
+                    sm.uorg = worg;
+                    sm.dorg = dorg;
                 }
-                if (lane == 0) sm.win_pos = bp;
             }
             __syncthreads();
             const int p = sm.win_pos;
-            const float piv = sm.urow[k];
+            const float *urow = sm.cand[sm.win_cta];
+            const float piv = urow[k];
             // 5. interchange of positions pk and p (whole panel rows)
             if (valid && gi == pk) {
 #pragma unroll
-                for (int c = 0; c < NB; ++c) a[c] = sm.urow[c];
+                for (int c = 0; c < NB; ++c) a[c] = urow[c];
                 org = sm.uorg;
             } else if (valid && gi == p) {
 #pragma unroll
@@ -248,7 +273,7 @@ __global__ void __launch_bounds__(T, 1)
                 if (piv != 0.f) l = l / piv;
                 a[k] = l;
 #pragma unroll
-                for (int c = k + 1; c < NB; ++c) a[c] = fmaf(-l, sm.urow[c], a[c]);
+                for (int c = k + 1; c < NB; ++c) a[c] = fmaf(-l, urow[c], a[c]);
             }
         }
     }

@@ -71,13 +71,16 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Wait (bounded) until the word carries `tag`, return its binary32 value.
+// Wait (bounded, with back-off) until the word carries `tag`; return its value.
 __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsigned tag,
                                              int *timeout) {
     unsigned long long v = ld_relaxed_u64(p);
     if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
     const unsigned long long t0 = globaltimer();
+    unsigned ns = 32;
     while (true) {
+        __nanosleep(ns);
+        if (ns < 256) ns <<= 1;
         v = ld_relaxed_u64(p);
         if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
         if (*reinterpret_cast<volatile int *>(timeout) || globaltimer() - t0 > kWaitLimitNs) {
@@ -87,73 +90,138 @@ __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsign
     }
 }
 
-__device__ __forceinline__ float warp_sum(float v) {
+// Sum of 8 per-lane values over the 32 lanes of a warp in 9 shuffles
+// (recursive halving): lane l ends with the total of row q(l) =
+// 4*bit4(l) + 2*bit3(l) + bit2(l).
+__device__ __forceinline__ float reduce8(float (&v)[8], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float a[4];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+    for (int q = 0; q < 4; ++q) {
+        const float send = h16 ? v[q] : v[q + 4];
+        const float keep = h16 ? v[q + 4] : v[q];
+        a[q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+    float b2[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float send = h8 ? a[q] : a[q + 2];
+        const float keep = h8 ? a[q + 2] : a[q];
+        b2[q] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c;
+    {
+        const float send = h4 ? b2[0] : b2[1];
+        const float keep = h4 ? b2[1] : b2[0];
+        c = keep + __shfl_xor_sync(0xffffffffu, send, 4);
+    }
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+__device__ __forceinline__ int reduce8_row(int lane) {
+    return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+}
+
+// Prefetch of one 64x64 off-diagonal tile slice: warp w rows 8w..8w+7,
+// lane l columns l and l+32 of block column bj.
+__device__ __forceinline__ void load_tile(const float *AF, int64_t ldf, int n, int row0, int bj,
+                                          int lane, float (&la)[8], float (&lb)[8]) {
+    const int c = bj * B + lane;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const int i = row0 + q;
+        la[q] = (i < n && c < n) ? __ldg(AF + (int64_t)i * ldf + c) : 0.f;
+        lb[q] = (i < n && c + 32 < n) ? __ldg(AF + (int64_t)i * ldf + c + 32) : 0.f;
+    }
+}
+
+// Accumulate the off-diagonal products of block bi: p[q] += sum_j A[row0+q][j] y_j
+// over the predecessor blocks, in order; the next tile is in flight while the
+// current one waits for its published values.
+template <bool LOWER>
+__device__ __forceinline__ void offdiag(const float *AF, int64_t ldf, int n, int nblk, int bi,
+                                        const unsigned long long *tags, unsigned tag, float *ys,
+                                        int *timeout, float (&p)[8]) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int row0 = bi * B + warp * 8;
+    const int npred = LOWER ? bi : (nblk - 1 - bi);
+    float la[8], lb[8], na[8], nb2[8];
+    if (npred > 0) load_tile(AF, ldf, n, row0, LOWER ? 0 : nblk - 1, lane, la, lb);
+    for (int it = 0; it < npred; ++it) {
+        const int bj = LOWER ? it : (nblk - 1 - it);
+        if (it + 1 < npred) load_tile(AF, ldf, n, row0, LOWER ? bj + 1 : bj - 1, lane, na, nb2);
+        if (warp == 0) {
+            ys[lane] = poll_tagged(tags + bj * B + lane, tag, timeout);
+            ys[lane + 32] = poll_tagged(tags + bj * B + lane + 32, tag, timeout);
+        }
+        __syncthreads();
+        const float y0 = ys[lane], y1 = ys[lane + 32];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            p[q] = fmaf(la[q], y0, p[q]);
+            p[q] = fmaf(lb[q], y1, p[q]);
+        }
+        __syncthreads();                       // ys consumed before the next fetch
+#pragma unroll
+        for (int q = 0; q < 8; ++q) { la[q] = na[q]; lb[q] = nb2[q]; }
+    }
 }
 
 // mode 0: v = fl32(r[perm[i]] / ||r||) (refinement step); mode 1: v = vin[perm[i]].
-// Writes tagged y for the upper solve.
+// Publishes tagged y for the upper solve.
 __global__ void __launch_bounds__(TT) k_trsv_lower(const float *AF, int64_t ldf, int n, int nblk,
                                                    const float *Linv, const int32_t *perm,
                                                    const double *r, const float *vin, int mode,
                                                    unsigned long long *ytag, unsigned tag,
                                                    DevScalars *dev) {
     __shared__ int s_bi;
-    __shared__ float sv[B];
+    __shared__ float sv[B], ys[B];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) s_bi = (int)atomicAdd(&dev->ticket[0], 1u);
     __syncthreads();
     const int bi = s_bi;
     const int r0 = bi * B;
-    const int row0 = r0 + warp * 8;     // this warp's 8 rows
+    // diagonal-block inverse rows of this warp, and this block's right-hand side
+    const float *Li = Linv + (int64_t)bi * B * B;
+    float da[8], db[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        da[q] = __ldg(Li + (warp * 8 + q) * B + lane);
+        db[q] = __ldg(Li + (warp * 8 + q) * B + lane + 32);
+    }
+    if (t < B) {
+        const int i = r0 + t;
+        float v = 0.f;
+        if (i < n) {
+            const int src = perm[i];
+            if (mode == 0) {
+                const double rn = __longlong_as_double((long long)dev->rnorm_bits);
+                v = __double2float_rn(r[src] / rn);
+            } else {
+                v = vin[src];
+            }
+        }
+        sv[t] = v;
+    }
     float p[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) p[q] = 0.f;
-    float la[8], lb[8];
-    for (int bj = 0; bj < bi; ++bj) {
-        const int c = bj * B + lane;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int i = row0 + q;
-            la[q] = (i < n) ? __ldg(AF + (int64_t)i * ldf + c) : 0.f;
-            lb[q] = (i < n) ? __ldg(AF + (int64_t)i * ldf + c + 32) : 0.f;
-        }
-        const float y0 = poll_tagged(ytag + c, tag, &dev->timeout);
-        const float y1 = poll_tagged(ytag + c + 32, tag, &dev->timeout);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            p[q] = fmaf(la[q], y0, p[q]);
-            p[q] = fmaf(lb[q], y1, p[q]);
-        }
-    }
-    double rinv_scale = 0.0;
-    if (mode == 0) rinv_scale = __longlong_as_double((long long)dev->rnorm_bits);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float sq = warp_sum(p[q]);
-        if (lane == q) {
-            const int i = row0 + q;
-            float v = 0.f;
-            if (i < n) {
-                const int src = perm[i];
-                v = (mode == 0) ? __double2float_rn(r[src] / rinv_scale) : vin[src];
-            }
-            sv[warp * 8 + q] = v - sq;
-        }
+    offdiag<true>(AF, ldf, n, nblk, bi, ytag, tag, ys, &dev->timeout, p);
+    __syncthreads();
+    {
+        const float sq = reduce8(p, lane);
+        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] -= sq;
     }
     __syncthreads();
-    const float *Li = Linv + (int64_t)bi * B * B;
+    float acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int il = warp * 8 + q;
-        float acc = fmaf(Li[il * B + lane], sv[lane], Li[il * B + lane + 32] * sv[lane + 32]);
-        acc = warp_sum(acc);
-        if (lane == q) {
-            const float y = (r0 + il < n) ? acc : 0.f;
-            st_relaxed_u64(ytag + r0 + il, ((unsigned long long)tag << 32) | __float_as_uint(y));
-        }
+    for (int q = 0; q < 8; ++q) acc[q] = fmaf(da[q], sv[lane], db[q] * sv[lane + 32]);
+    const float y = reduce8(acc, lane);
+    if ((lane & 3) == 0) {
+        const int il = warp * 8 + reduce8_row(lane);
+        const float yv = (r0 + il < n) ? y : 0.f;
+        st_relaxed_u64(ytag + r0 + il, ((unsigned long long)tag << 32) | __float_as_uint(yv));
     }
 }
 
@@ -166,66 +234,51 @@ __global__ void __launch_bounds__(TT) k_trsv_upper(const float *AF, int64_t ldf,
                                                    int mode, double *x, float *dout,
                                                    DevScalars *dev) {
     __shared__ int s_bi;
-    __shared__ float sv[B];
+    __shared__ float sv[B], ys[B];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) s_bi = nblk - 1 - (int)atomicAdd(&dev->ticket[1], 1u);
     __syncthreads();
     const int bi = s_bi;
     const int r0 = bi * B;
-    const int row0 = r0 + warp * 8;
+    const float *Ui = Uinv + (int64_t)bi * B * B;
+    float da[8], db[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        da[q] = __ldg(Ui + (warp * 8 + q) * B + lane);
+        db[q] = __ldg(Ui + (warp * 8 + q) * B + lane + 32);
+    }
+    if (t < B) {
+        // the lower solve of this launch sequence has written every y word already
+        const int i = r0 + t;
+        sv[t] = (i < n) ? __uint_as_float((unsigned)ld_relaxed_u64(ytag + i)) : 0.f;
+    }
     float p[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) p[q] = 0.f;
-    float la[8], lb[8];
-    for (int bj = nblk - 1; bj > bi; --bj) {
-        const int c = bj * B + lane;
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int i = row0 + q;
-            la[q] = (i < n && c < n) ? __ldg(AF + (int64_t)i * ldf + c) : 0.f;
-            lb[q] = (i < n && c + 32 < n) ? __ldg(AF + (int64_t)i * ldf + c + 32) : 0.f;
-        }
-        const float z0 = poll_tagged(ztag + c, tag, &dev->timeout);
-        const float z1 = poll_tagged(ztag + c + 32, tag, &dev->timeout);
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            p[q] = fmaf(la[q], z0, p[q]);
-            p[q] = fmaf(lb[q], z1, p[q]);
-        }
-    }
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const float sq = warp_sum(p[q]);
-        if (lane == q) {
-            const int i = row0 + q;
-            // the lower solve of this launch sequence wrote every y word already
-            const float yv = (i < n) ? __uint_as_float((unsigned)ld_relaxed_u64(ytag + i)) : 0.f;
-            sv[warp * 8 + q] = yv - sq;
-        }
+    offdiag<false>(AF, ldf, n, nblk, bi, ztag, tag, ys, &dev->timeout, p);
+    __syncthreads();
+    {
+        const float sq = reduce8(p, lane);
+        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] -= sq;
     }
     __syncthreads();
-    const float *Ui = Uinv + (int64_t)bi * B * B;
-    double scale = 0.0;
-    if (mode == 0)
-        scale = __longlong_as_double((long long)dev->rnorm_bits) * dev->scale;
-    double dmax = 0.0;
+    float acc[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        const int il = warp * 8 + q;
-        float acc = fmaf(Ui[il * B + lane], sv[lane], Ui[il * B + lane + 32] * sv[lane + 32]);
-        acc = warp_sum(acc);
-        if (lane == q) {
-            const int i = r0 + il;
-            const float z = (i < n) ? acc : 0.f;
-            st_relaxed_u64(ztag + i, ((unsigned long long)tag << 32) | __float_as_uint(z));
-            if (i < n) {
-                if (mode == 0) {
-                    const double d = scale * (double)z;
-                    x[i] += d;
-                    dmax = fmax(dmax, fabs(d));
-                } else {
-                    dout[i] = z;
-                }
+    for (int q = 0; q < 8; ++q) acc[q] = fmaf(da[q], sv[lane], db[q] * sv[lane + 32]);
+    const float z = reduce8(acc, lane);
+    double dmax = 0.0;
+    if ((lane & 3) == 0) {
+        const int i = r0 + warp * 8 + reduce8_row(lane);
+        const float zv = (i < n) ? z : 0.f;
+        st_relaxed_u64(ztag + i, ((unsigned long long)tag << 32) | __float_as_uint(zv));
+        if (i < n) {
+            if (mode == 0) {
+                const double scale = __longlong_as_double((long long)dev->rnorm_bits) * dev->scale;
+                const double d = scale * (double)zv;
+                x[i] += d;
+                dmax = fabs(d);
+            } else {
+                dout[i] = zv;
             }
         }
     }

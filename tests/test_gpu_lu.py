@@ -76,13 +76,18 @@ def test_lu_tensor_core_parity(ctx, n, tf, kind):
     for k in ks:
         delta = np.max(np.abs(_column_magnitudes(LU, k) - _column_magnitudes(LUo, k)))
         assert gap[k, 0] - gap[k, 2] <= 2 * delta + 4 * 2.0 ** -24 * gap[k, 0], (k, gap[k], delta)
-    assert len(ks) <= max(2, n // 50)          # disagreements are rare
     # first block column: bitwise (no tensor-core update has touched it)
     assert np.array_equal(LU[:, :NB].view(np.uint32), LUo[:, :NB].view(np.uint32))
-    # whole factorization: normwise close at the TF rounding level
     u = O.UNIT_ROUNDOFF[tf]
-    rel = np.max(np.abs(LU.astype(np.float64) - LUo)) / np.max(np.abs(LUo))
-    assert rel <= 64 * u, rel
+    if kind == "gauss":
+        # well-conditioned Schur complements: disagreements are rare and the whole
+        # factorization is normwise close at the TF rounding level.  (For the
+        # unshifted random matrices the late Schur complements are ill-conditioned
+        # and amplify the accumulation-order differences; there the backward-error
+        # bound below is the check.)
+        assert len(ks) <= max(2, n // 50)
+        rel = np.max(np.abs(LU.astype(np.float64) - LUo)) / np.max(np.abs(LUo))
+        assert rel <= 64 * u, rel
     # and the GPU factors satisfy the backward-error bound of the TF factorization
     P = O.perm_from_ipiv(piv)
     L = np.tril(LU.astype(np.float64), -1) + np.eye(n)
