@@ -152,6 +152,27 @@ ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_
                       const void *b, const double *x, double *r, double *rnorm,
                       void *stream);
 
+/* Residual without device allocation (the paper has no counterpart): the
+ * same r = b - A x and rnorm[0] = ||r||_inf as ir_residual, with the same
+ * argument meaning and layout, for callers that must not call cudaMalloc --
+ * code inside a framework whose caching allocator owns the device memory,
+ * latency-critical loops that cannot afford cudaMalloc's implicit
+ * synchronisation, deployments that allow allocation only at start-up.  Its
+ * workspace is a fixed array of IR_RESIDUAL_NOALLOC_SCRATCH doubles (8 MiB)
+ * in the library's device image, held by every GPU that loads the library
+ * until exit.  No context is needed; the current device is used.
+ *   n <= IR_RESIDUAL_NOALLOC_MAX_N, else IR_EUNSUPPORTED (nothing launched).
+ *   The first call on a device looks up the array's address (once per device,
+ *   with that device current): make it before any stream capture.
+ *   All calls share the array: calls that overlap on the GPU race and give
+ *   wrong results; calls ordered on one stream are safe (each call writes
+ *   every partial sum it reads and clears rnorm itself). */
+#define IR_RESIDUAL_NOALLOC_SCRATCH (1 << 20)
+#define IR_RESIDUAL_NOALLOC_MAX_N (1 << 20)
+ir_status ir_residual_noalloc(int64_t n, ir_dtype TW, const void *A, int64_t lda,
+                              const void *b, const double *x, double *r, double *rnorm,
+                              void *stream);
+
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */
 ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);
 
