@@ -15,6 +15,7 @@
 namespace ir {
 static std::atomic<unsigned long long> g_launch_count{0};
 void count_launch() { g_launch_count.fetch_add(1, std::memory_order_relaxed); }
+void count_launches(unsigned long long k) { g_launch_count.fetch_add(k, std::memory_order_relaxed); }
 unsigned long long launches() { return g_launch_count.load(std::memory_order_relaxed); }
 }  // namespace ir
 
@@ -129,6 +130,8 @@ void free_fact(ir_fact *f) {
     cudaFree(f->r);
     cudaFree(f->dev);
     if (f->host_dev) cudaFreeHost(f->host_dev);
+    if (f->graph) cudaGraphExecDestroy(f->graph);
+    if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     delete f;
 }
 
@@ -186,7 +189,7 @@ fail:
 }
 
 // Cast + blocked right-looking LU with partial pivoting + diagonal-block inverses.
-ir_status run_factor(ir_fact *f, cudaStream_t s) {
+ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
     const int n = (int)f->n;
     const int64_t ldf = f->ldf;
     CK(cudaMemsetAsync(f->dev, 0, sizeof(DevScalars), s));
@@ -199,8 +202,8 @@ ir_status run_factor(ir_fact *f, cudaStream_t s) {
     const int NB = kPanelNB;
     for (int j = 0; j < n; j += NB) {
         const int nbp = (n - j < NB) ? n - j : NB;
-        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, f->swap_list, f->dev, f->TF,
-                        f->Aop, s));
+        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, f->swap_list, f->dev,
+                                      f->TF, f->Aop, s));
         RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, n, j, nbp, f->swap_list, s));
         if (j + nbp < n) {
             RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, n, j, NB, f->TF, f->Bop, s));
@@ -211,6 +214,48 @@ ir_status run_factor(ir_fact *f, cudaStream_t s) {
         }
     }
     RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, s));
+    return IR_OK;
+}
+
+bool graphs_enabled() {
+    const char *e = std::getenv("IR_NO_GRAPH");
+    return !(e && e[0] && e[0] != '0');
+}
+
+// The factorization's launch sequence is captured once per (A, lda) into a
+// CUDA graph on a private stream and replayed on the caller's stream; with
+// per-launcher profiling on, the launches are issued directly instead.
+ir_status run_factor(ir_fact *f, cudaStream_t s) {
+    if (g_prof.on || !graphs_enabled() || f->n == 0) return enqueue_factor(f, s);
+    if (!f->graph || f->graph_A != f->A || f->graph_lda != f->lda) {
+        if (f->graph) {
+            cudaGraphExecDestroy(f->graph);
+            f->graph = nullptr;
+        }
+        if (!f->cap_stream) CK(cudaStreamCreateWithFlags(&f->cap_stream, cudaStreamNonBlocking));
+        const unsigned long long l0 = ir::launches();
+        CK(cudaStreamBeginCapture(f->cap_stream, cudaStreamCaptureModeThreadLocal));
+        ir_status st = enqueue_factor(f, f->cap_stream);
+        cudaGraph_t g = nullptr;
+        cudaError_t e = cudaStreamEndCapture(f->cap_stream, &g);
+        if (st != IR_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(&f->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            f->graph = nullptr;
+            return cuda_fail(e, "cudaGraphInstantiate");
+        }
+        f->graph_launches = ir::launches() - l0;
+        g_launch_count.fetch_sub(f->graph_launches, std::memory_order_relaxed);  // captured, not run
+        f->graph_A = f->A;
+        f->graph_lda = f->lda;
+    }
+    CK(cudaGraphLaunch(f->graph, s));
+    ir::count_launches(f->graph_launches);
     return IR_OK;
 }
 

@@ -68,12 +68,19 @@ struct ir_fact {
     double *x, *r;           // binary64 iterate and residual
     ir::DevScalars *dev;
     ir::DevScalars *host_dev;  // pinned mirror
+    // the factorization's launch sequence as a CUDA graph (captured for one A)
+    cudaStream_t cap_stream;
+    cudaGraphExec_t graph;
+    const void *graph_A;
+    int64_t graph_lda;
+    unsigned long long graph_launches;  // kernels in the graph
 };
 
 namespace ir {
 
 // ---- launch accounting and optional per-launcher event timing --------------
 void count_launch();                       // one call per kernel launch
+void count_launches(unsigned long long k);  // k kernels launched at once (a graph replay)
 unsigned long long launches();
 
 // ---- launchers (each returns the launch error) -----------------------------

@@ -6,11 +6,15 @@
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
 //   warp 0      TMA producer: both operand tiles of a 128x128 output tile
-//               (K = 64) into a 2-stage shared-memory ring (128-byte swizzle)
+//               (K = 64, 128-byte swizzle) into a shared-memory ring, and the
+//               binary32 C tile itself (four 128x32 boxes) into one of two
+//               C buffers
 //   warp 1      allocates TMEM (2 accumulators x 128 columns) and issues the
 //               MMAs from one thread; tcgen05.commit frees the stage and
 //               signals the accumulator
-//   warps 2-9   epilogue: tcgen05.ld the accumulator, C -= D in global memory
+//   warps 2-9   epilogue: tcgen05.ld the accumulator, C -= D in shared memory,
+//               one thread stores the tile back with TMA (edges are clipped
+//               by the tensor map, so ragged tiles need no guards)
 // Every mbarrier wait is bounded (globaltimer); on timeout the CTA records
 // the error, waits (bounded) for its own copies in flight, frees TMEM and
 // returns.
@@ -22,7 +26,6 @@ namespace ir {
 namespace {
 
 constexpr int BM = 128, BN = 128, K = kPanelNB;
-constexpr int kStages = 2;
 constexpr int kAtomBytes = BM * 128;      // one 128-row x 128-byte swizzle tile = 16 KB
 constexpr int kThreads = 320;             // 10 warps
 constexpr int kEpiThreads = 256;
@@ -142,39 +145,57 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
     for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
 }
 
-template <int KATOMS>   // 128-byte K atoms per operand row: 2 for TF32, 1 for 16-bit types
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int c0, int c1, unsigned src) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(c0), "r"(c1), "r"(src)
+                 : "memory");
+}
+
+constexpr int kCBoxBytes = BM * 32 * 4;       // one 128-row x 32-column binary32 box = 16 KB
+constexpr int kCBufBytes = 4 * kCBoxBytes;    // a 128 x 128 C tile = 64 KB
+constexpr int kCBufs = 2;
+
+template <int KATOMS, int STAGES>   // 128-byte K atoms per operand row: 2 for TF32, 1 for 16-bit
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
-              TcParams p) {
+              const __grid_constant__ CUtensorMap tmC, TcParams p) {
     constexpr bool kTF32 = (KATOMS == 2);
     constexpr int kAtomElems = kTF32 ? 32 : 64;          // elements per 128-byte K atom
     constexpr int kKSteps = 128 / 32;                    // MMAs per atom (32-byte K per MMA)
     constexpr unsigned kStageBytes = 2u * KATOMS * kAtomBytes;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    // 1024-byte aligned operand area
     const unsigned sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    const unsigned sA = sbase;                                   // stages x KATOMS x 16 KB
-    const unsigned sB = sbase + kStages * KATOMS * kAtomBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gbase + 2 * kStages * KATOMS * kAtomBytes);
+    const unsigned sA = sbase;                                   // STAGES x KATOMS x 16 KB
+    const unsigned sB = sbase + STAGES * KATOMS * kAtomBytes;
+    const unsigned sC = sbase + 2 * STAGES * KATOMS * kAtomBytes; // kCBufs x 64 KB
+    unsigned char *gC = gbase + 2 * STAGES * KATOMS * kAtomBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gC + kCBufs * kCBufBytes);
     const unsigned bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
-    auto empty_bar = [&](int s) { return bar0 + 8u * (kStages + s); };
-    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * kStages + b); };
-    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * kStages + 2 + b); };
-    const unsigned drain_bar = bar0 + 8u * (2 * kStages + 4);
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * kStages + 5);
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
+    auto cfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 4 + b); };
+    auto cempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 6 + b); };
+    auto cdone_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 8 + b); };   // epilogue wrote C
+    const unsigned drain_bar = bar0 + 8u * (2 * STAGES + 10);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * STAGES + 11);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < kStages; ++s) {
+        for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(accf_bar(b), 1);
             mbar_init(acce_bar(b), kEpiThreads);
+            mbar_init(cfull_bar(b), 1);
+            mbar_init(cempty_bar(b), 1);
+            mbar_init(cdone_bar(b), kEpiThreads);
         }
         mbar_init(drain_bar, 1);
         *abort_flag = 0;
@@ -195,10 +216,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int s = 0;
             unsigned ph = 0;
-            unsigned last_ph[kStages];  // parity of the latest fill of each stage
-            bool issued[kStages];
-            for (int q = 0; q < kStages; ++q) issued[q] = false;
-            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x) {
+            unsigned last_ph[STAGES], last_cph[kCBufs];  // parity of the latest fill of each buffer
+            bool issued[STAGES], cissued[kCBufs];
+            for (int q = 0; q < STAGES; ++q) issued[q] = false;
+            for (int q = 0; q < kCBufs; ++q) cissued[q] = false;
+            int it = 0;
+            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
                 const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
                 if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.timeout)) break;
                 mbar_arrive_expect_tx(full_bar(s), kStageBytes);
@@ -209,14 +232,26 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 last_ph[s] = ph;
                 issued[s] = true;
-                if (++s == kStages) { s = 0; ph ^= 1u; }
+                if (++s == STAGES) { s = 0; ph ^= 1u; }
+                // the C tile
+                const int cb = it & 1;
+                const unsigned cph = (unsigned)(it >> 1) & 1u;
+                if (!mbar_wait(cempty_bar(cb), cph ^ 1u, abort_flag, p.timeout)) break;
+                mbar_arrive_expect_tx(cfull_bar(cb), (unsigned)kCBufBytes);
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    tma_load_2d(sC + cb * kCBufBytes + q * kCBoxBytes, &tmC, tn * BN + 32 * q, tm * BM, cfull_bar(cb));
+                last_cph[cb] = cph;
+                cissued[cb] = true;
             }
             if (*abort_flag) {
                 // drain: wait (bounded) until the copies this thread issued have landed
                 int dummy = 0;
                 volatile int no_abort = 0;
-                for (int q = 0; q < kStages; ++q)
+                for (int q = 0; q < STAGES; ++q)
                     if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, &dummy);
+                for (int q = 0; q < kCBufs; ++q)
+                    if (cissued[q]) mbar_wait(cfull_bar(q), last_cph[q], &no_abort, &dummy);
             }
         }
     } else if (warp == 1) {
@@ -242,7 +277,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 mma_commit(empty_bar(s));
                 mma_commit(accf_bar(ab));
-                if (++s == kStages) { s = 0; ph ^= 1u; }
+                if (++s == STAGES) { s = 0; ph ^= 1u; }
             }
             if (*abort_flag) {
                 // wait (bounded) until the tensor core has finished everything issued
@@ -253,43 +288,55 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
         }
     } else {
-        // epilogue: warps 2..9; TMEM lane quarter = warp % 4, column half = (warp - 2) / 4
+        // epilogue: warps 2..9; TMEM lane quarter = warp % 4 (tile rows 32q..32q+31),
+        // column half = (warp - 2) / 4 (tile columns 64h..64h+63, two 32-column boxes)
         const int quarter = warp & 3;
         const int half = (warp - 2) >> 2;
+        const int r = quarter * 32 + lane;                 // row within the tile
+        const bool leader = (warp == 2 && lane == 0);
         int it = 0;
         for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
             const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
-            const int ab = it & 1;
+            const int ab = it & 1, cb = it & 1;
             const unsigned aph = (unsigned)(it >> 1) & 1u;
             if (!mbar_wait(accf_bar(ab), aph, abort_flag, p.timeout)) break;
             tc_fence_after();
-            const int row = tm * BM + quarter * 32 + lane;
+            float v0[32], v1[32];
+            const unsigned tl = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * BN + half * 64);
+            tmem_ld32(tl, v0);
+            tmem_ld32(tl + 32, v1);
+            tc_fence_before();
+            mbar_arrive(acce_bar(ab));                     // the accumulator may be reused
+            if (!mbar_wait(cfull_bar(cb), aph, abort_flag, p.timeout)) break;
+            // C -= D in the 128B-swizzled boxes: 16-byte chunk c16 of row r sits at c16 ^ (r & 7)
 #pragma unroll
-            for (int cc = 0; cc < 2; ++cc) {
-                const int chunk = half * 2 + cc;
-                float v[32];
-                tmem_ld32(tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * BN + chunk * 32), v);
-                const int col0 = tn * BN + chunk * 32;
-                if (row < p.M) {
-                    float *crow = p.C + (int64_t)row * p.ldc + col0;
-                    float4 c[8];
+            for (int h = 0; h < 2; ++h) {
+                const float *v = h ? v1 : v0;
+                unsigned char *box = gC + cb * kCBufBytes + (half * 2 + h) * kCBoxBytes + r * 128;
 #pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (col0 + 4 * q < p.N) c[q] = reinterpret_cast<const float4 *>(crow)[q];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q)
-                        if (col0 + 4 * q < p.N) {
-                            c[q].x -= v[4 * q + 0];
-                            c[q].y -= v[4 * q + 1];
-                            c[q].z -= v[4 * q + 2];
-                            c[q].w -= v[4 * q + 3];
-                            reinterpret_cast<float4 *>(crow)[q] = c[q];
-                        }
+                for (int c16 = 0; c16 < 8; ++c16) {
+                    float4 *q4 = reinterpret_cast<float4 *>(box + ((c16 ^ (r & 7)) << 4));
+                    float4 c = *q4;
+                    c.x -= v[4 * c16 + 0];
+                    c.y -= v[4 * c16 + 1];
+                    c.z -= v[4 * c16 + 2];
+                    c.w -= v[4 * c16 + 3];
+                    *q4 = c;
                 }
             }
-            tc_fence_before();
-            mbar_arrive(acce_bar(ab));
+            // make the generic-proxy writes visible to the TMA store, then signal
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(cdone_bar(cb));
+            if (leader) {
+                if (!mbar_wait(cdone_bar(cb), aph, abort_flag, p.timeout)) break;
+#pragma unroll
+                for (int q = 0; q < 4; ++q) tma_store_2d(&tmC, tn * BN + 32 * q, tm * BM, sC + cb * kCBufBytes + q * kCBoxBytes);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+                mbar_arrive(cempty_bar(cb));               // the C buffer may be refilled
+            }
         }
+        if (leader) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
     }
     tc_fence_before();
     __syncthreads();
@@ -335,6 +382,20 @@ bool make_map(CUtensorMap *m, const void *base, int rows, ir_dtype tf) {
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The binary32 trailing matrix C (rows x cols, row stride ld floats): boxes of
+// 128 rows x 32 columns (128 bytes), 128-byte swizzle.
+bool make_c_map(CUtensorMap *m, float *base, int rows, int cols, int64_t ld) {
+    EncodeTiledFn enc = get_encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {32, (cuuint32_t)BM};
+    cuuint32_t estr[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Instruction descriptor for kind::tf32 / kind::f16: D = F32 (bits 4-5 = 1),
 // A/B format (bits 7-9 / 10-12: F16 0, BF16 1, TF32 2), both K-major,
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
@@ -343,11 +404,9 @@ unsigned make_idesc(ir_dtype tf) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(BM >> 4) << 24);
 }
 
-// At least 116 KB, so that one CTA (one TMEM allocation of 256 columns) runs per SM.
-template <int KATOMS>
+template <int KATOMS, int STAGES>
 size_t smem_bytes() {
-    const size_t need = 1024 + 2 * kStages * KATOMS * kAtomBytes + 8 * (2 * kStages + 5) + 16;
-    return need > 116 * 1024 ? need : 116 * 1024;
+    return 1024 + 2 * STAGES * KATOMS * kAtomBytes + kCBufs * kCBufBytes + 8 * (2 * STAGES + 11) + 16;
 }
 
 }  // namespace
@@ -369,27 +428,29 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtyp
     p.num_tiles = tiles_m * p.tiles_n;
     p.idesc = make_idesc(tf);
     p.timeout = &dev->timeout;
+    CUtensorMap tc;
+    if (!make_c_map(&tc, p.C, m, m, ldf)) return cudaErrorInvalidValue;
     const int grid = p.num_tiles < sms ? p.num_tiles : sms;
     if (tf == IR_TF32) {
         static bool attr = false;
-        const size_t sm = smem_bytes<2>();
+        const size_t sm = smem_bytes<2, 1>();
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
         count_launch();
-        k_gemm_tc<2><<<grid, kThreads, sm, s>>>(ta, tb, p);
+        k_gemm_tc<2, 1><<<grid, kThreads, sm, s>>>(ta, tb, tc, p);
     } else {
         static bool attr = false;
-        const size_t sm = smem_bytes<1>();
+        const size_t sm = smem_bytes<1, 2>();
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
         count_launch();
-        k_gemm_tc<1><<<grid, kThreads, sm, s>>>(ta, tb, p);
+        k_gemm_tc<1, 2><<<grid, kThreads, sm, s>>>(ta, tb, tc, p);
     }
     return cudaGetLastError();
 }

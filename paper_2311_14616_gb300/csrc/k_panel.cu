@@ -20,6 +20,7 @@ namespace {
 constexpr int NB = kPanelNB;
 constexpr int T = kPanelT;
 constexpr int NW = T / 32;
+constexpr int kFetchBatch = 4;   // candidate rows fetched per DSMEM round trip
 
 // Every panel row carries the index of the row it started the panel in
 // ("origin"), so the panel's net permutation is known at the end without
@@ -29,7 +30,9 @@ struct PanelSmem {
     alignas(16) float stage_row[NW][NB];     // per-warp candidate row
     alignas(16) float slot_row[2][NB];       // this CTA's candidate, read by the cluster
     alignas(16) float diag_row[2][NB];       // row k (owned by CTA 0), read by the winner's CTA
-    alignas(16) float cand[kPanelMaxCluster][NB];   // every CTA's candidate row, local copies
+    // every CTA's candidate row, local copies; value i at index i + 3 so that
+    // values 1..64 form 16-byte aligned quadruples (index 67 stays zero)
+    alignas(16) float cand[kPanelMaxCluster][NB + 4];
     alignas(16) float drow[NB];              // old row k, local copy
     float stage_val[NW];
     int stage_pos[NW];
@@ -40,7 +43,12 @@ struct PanelSmem {
     int diag_org[2];
     int uorg, dorg;
     int win_pos, win_cta;
+    int piv_log[NB];             // p_k of every step (the panel's interchanges)
+    int zero_piv;                // first zero pivot of this panel (1-based), or 0
 };
+// Dynamic shared memory after PanelSmem: Ls[NB][T] multipliers by step and
+// position, Us[NB][NB] pivot rows (CTA 0).
+constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * T + sizeof(float) * NB * NB + 16;
 static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, slot_row) % 16 == 0 &&
                   offsetof(PanelSmem, diag_row) % 16 == 0 && offsetof(PanelSmem, cand) % 16 == 0 &&
                   offsetof(PanelSmem, drow) % 16 == 0,
@@ -119,17 +127,27 @@ __device__ __forceinline__ void store_op_row(void *op, int64_t row, const float 
 }
 
 // One cluster factors the panel AF[j:n, j:j+nbp].  CTA c of the cluster owns
-// panel rows (positions) j + c*T + t, one per thread, held in registers.
-// Per column k: warp argmax (redux.sync) -> CTA candidate -> DSMEM exchange
-// across the cluster (one cluster barrier) -> winner row copied locally ->
-// interchange of positions k and p -> scale and rank-1 update in registers.
-// At the end the rows whose content moved are listed as (destination,
-// origin) pairs in swap_list (count in swap_list[0]) for the gather of the
-// other columns, and perm is composed with the panel's permutation.
+// panel rows (positions) j + c*T + t, one per thread.  A thread keeps the
+// not-yet-eliminated part of its row in a rotating register window: at step k,
+// a[i] holds column j+k+i (zero past the panel), so the current column is
+// always a[0] and the update a[i] <- fmaf(-l, u[i+1], a[i+1]) also shifts the
+// window.  Per column k: warp argmax (redux.sync) -> CTA candidate -> DSMEM
+// exchange across the cluster (one cluster barrier, one round trip) ->
+// interchange of positions k and p -> scale and rank-1 update.
+// The column loop touches no global memory (a release barrier would wait for
+// it): multipliers go to shared memory by step and position, pivot rows and
+// the interchanges to shared memory; at the end every row gathers its
+// multipliers by walking the interchanges backward (DSMEM reads).  The rows
+// whose content moved are listed as (destination, origin) pairs in swap_list
+// (count in swap_list[0]) for the gather of the other columns, and perm is
+// composed with the panel's permutation.
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
-    __shared__ __align__(16) PanelSmem sm;
+    extern __shared__ __align__(16) unsigned char panel_smem[];
+    PanelSmem &sm = *reinterpret_cast<PanelSmem *>(panel_smem);
+    float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [NB][T]
+    float *Us = Ls + (size_t)NB * T;                                          // [NB][NB]
     const unsigned crank = cluster_rank();
     const unsigned csize = cluster_size();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -138,6 +156,8 @@ __global__ void __launch_bounds__(T, 1)
 
     int org = gi;
     if (crank == 0 && t == 0) swap_list[0] = 0;
+    if (t == 0) sm.zero_piv = 0;
+    for (int e = t; e < kPanelMaxCluster * (NB + 4); e += T) (&sm.cand[0][0])[e] = 0.f;
     float a[NB];
     if (valid) {
         const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)gi * ldf + j);
@@ -146,6 +166,9 @@ __global__ void __launch_bounds__(T, 1)
             float4 v = (c < nbp) ? src[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
             a[c] = v.x; a[c + 1] = v.y; a[c + 2] = v.z; a[c + 3] = v.w;
         }
+#pragma unroll
+        for (int c = 0; c < NB; ++c)
+            if (c >= nbp) a[c] = 0.f;
     } else {
 #pragma unroll
         for (int c = 0; c < NB; ++c) a[c] = 0.f;
@@ -159,82 +182,85 @@ __global__ void __launch_bounds__(T, 1)
     const unsigned slot_org_addr = smem_u32(&sm.slot_org[0]);
     const unsigned diag_org_addr = smem_u32(&sm.diag_org[0]);
 
+#pragma unroll 1
+    for (int k = 0; k < nbp; ++k) {
+        const int buf = k & 1;
+        const int pk = j + k;   // position being eliminated
+        // 1. local candidate: first maximal |a_ik| over rows i >= pk
+        const bool cand = valid && gi >= pk;
+        unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
+        int pos = cand ? gi : INT_MAX;
+        unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+        int pmin = __reduce_min_sync(0xffffffffu, (key == kmax) ? pos : INT_MAX);
+        if (pos == pmin && pmin != INT_MAX) {
 #pragma unroll
-    for (int k = 0; k < NB; ++k) {
-        if (k < nbp) {
-            const int buf = k & 1;
-            const int pk = j + k;   // position being eliminated
-            // 1. local candidate: first maximal |a_ik| over rows i >= pk
-            const bool cand = valid && gi >= pk;
-            unsigned key = cand ? __float_as_uint(fabsf(a[k])) : 0u;
-            int pos = cand ? gi : INT_MAX;
-            unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-            int pmin = __reduce_min_sync(0xffffffffu, (key == kmax) ? pos : INT_MAX);
-            if (pos == pmin && pmin != INT_MAX) {
+            for (int c = 0; c < NB; c += 4)
+                *reinterpret_cast<float4 *>(&sm.stage_row[warp][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+            sm.stage_org[warp] = org;
+        }
+        if (lane == 0) { sm.stage_val[warp] = __uint_as_float(kmax); sm.stage_pos[warp] = pmin; }
+        // row k is published by its owner (always CTA 0: positions j..j+NB-1)
+        if (valid && gi == pk) {
 #pragma unroll
-                for (int c = 0; c < NB; c += 4)
-                    *reinterpret_cast<float4 *>(&sm.stage_row[warp][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-                sm.stage_org[warp] = org;
+            for (int c = 0; c < NB; c += 4)
+                *reinterpret_cast<float4 *>(&sm.diag_row[buf][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+            sm.diag_org[buf] = org;
+        }
+        __syncthreads();
+        // 2. CTA candidate
+        if (warp == 0) {
+            unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
+            int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
+            unsigned bk = __reduce_max_sync(0xffffffffu, wk);
+            int bp = __reduce_min_sync(0xffffffffu, (wk == bk) ? wp : INT_MAX);
+            unsigned who = __ballot_sync(0xffffffffu, wp == bp && bp != INT_MAX);
+            int w = who ? __ffs(who) - 1 : 0;
+            for (int c = lane; c < NB; c += 32) sm.slot_row[buf][c] = sm.stage_row[w][c];
+            if (lane == 0) {
+                sm.slot_val[buf] = __uint_as_float(bk);
+                sm.slot_pos[buf] = bp;
+                sm.slot_org[buf] = sm.stage_org[w];
             }
-            if (lane == 0) { sm.stage_val[warp] = __uint_as_float(kmax); sm.stage_pos[warp] = pmin; }
-            // row k is published by its owner (always CTA 0: positions j..j+NB-1)
-            if (valid && gi == pk) {
+        }
+        // 3. exchange
+        cluster_sync_all();
+        // 4. one round trip: every CTA's candidate (header and row) and row k;
+        //    warp w pulls the rows of CTAs kFetchBatch*w .. +kFetchBatch-1,
+        //    warp 0 also the headers and row k, and picks the winner locally
+        if (warp * kFetchBatch < (int)csize) {
+            const int c0 = warp * kFetchBatch;
+            float r0[kFetchBatch], r1[kFetchBatch];
 #pragma unroll
-                for (int c = 0; c < NB; c += 4)
-                    *reinterpret_cast<float4 *>(&sm.diag_row[buf][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-                sm.diag_org[buf] = org;
-            }
-            __syncthreads();
-            // 2. CTA candidate
-            if (warp == 0) {
-                unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
-                int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
-                unsigned bk = __reduce_max_sync(0xffffffffu, wk);
-                int bp = __reduce_min_sync(0xffffffffu, (wk == bk) ? wp : INT_MAX);
-                unsigned who = __ballot_sync(0xffffffffu, wp == bp && bp != INT_MAX);
-                int w = who ? __ffs(who) - 1 : 0;
-                for (int c = lane; c < NB; c += 32) sm.slot_row[buf][c] = sm.stage_row[w][c];
-                if (lane == 0) {
-                    sm.slot_val[buf] = __uint_as_float(bk);
-                    sm.slot_pos[buf] = bp;
-                    sm.slot_org[buf] = sm.stage_org[w];
+            for (int c = 0; c < kFetchBatch; ++c) {
+                if (c0 + c < (int)csize) {
+                    const unsigned base = map_cta(slot_row_addr + 4u * NB * buf, (unsigned)(c0 + c));
+                    r0[c] = ld_dsmem_f32(base + 4u * lane);
+                    r1[c] = ld_dsmem_f32(base + 4u * (lane + 32));
                 }
             }
-            // 3. exchange
-            cluster_sync_all();
-            // 4. one round trip: every CTA's candidate (header and row) and row k;
-            //    the winner is picked locally
+            unsigned ck = 0u;
+            int cp = INT_MAX, co = 0;
+            float d0 = 0.f, d1 = 0.f;
+            int dorg = 0;
             if (warp == 0) {
-                unsigned ck = 0u;
-                int cp = INT_MAX, co = 0;
                 if (lane < (int)csize) {
                     ck = __float_as_uint(ld_dsmem_f32(map_cta(slot_val_addr + 4u * buf, lane)));
                     cp = ld_dsmem_s32(map_cta(slot_pos_addr + 4u * buf, lane));
                     co = ld_dsmem_s32(map_cta(slot_org_addr + 4u * buf, lane));
                 }
                 const unsigned dbase = map_cta(diag_row_addr + 4u * NB * buf, 0u);
-                const float d0 = ld_dsmem_f32(dbase + 4u * lane);
-                const float d1 = ld_dsmem_f32(dbase + 4u * (lane + 32));
-                const int dorg = (lane == 0) ? ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u)) : 0;
-                // candidate rows in batches of 8 CTAs (all loads of a batch in flight)
-                for (int c0 = 0; c0 < (int)csize; c0 += 8) {
-                    float r0[8], r1[8];
+                d0 = ld_dsmem_f32(dbase + 4u * lane);
+                d1 = ld_dsmem_f32(dbase + 4u * (lane + 32));
+                if (lane == 0) dorg = ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u));
+            }
 #pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        if (c0 + c < (int)csize) {
-                            const unsigned base = map_cta(slot_row_addr + 4u * NB * buf, (unsigned)(c0 + c));
-                            r0[c] = ld_dsmem_f32(base + 4u * lane);
-                            r1[c] = ld_dsmem_f32(base + 4u * (lane + 32));
-                        }
-                    }
-#pragma unroll
-                    for (int c = 0; c < 8; ++c) {
-                        if (c0 + c < (int)csize) {
-                            sm.cand[c0 + c][lane] = r0[c];
-                            sm.cand[c0 + c][lane + 32] = r1[c];
-                        }
-                    }
+            for (int c = 0; c < kFetchBatch; ++c) {
+                if (c0 + c < (int)csize) {
+                    sm.cand[c0 + c][lane + 3] = r0[c];
+                    sm.cand[c0 + c][lane + 35] = r1[c];
                 }
+            }
+            if (warp == 0) {
                 sm.drow[lane] = d0;
                 sm.drow[lane + 32] = d1;
                 unsigned bk = __reduce_max_sync(0xffffffffu, ck);
@@ -247,43 +273,42 @@ __global__ void __launch_bounds__(T, 1)
                     sm.win_cta = wc;
                     sm.uorg = worg;
                     sm.dorg = dorg;
+                    sm.piv_log[k] = bp;
                 }
             }
-            __syncthreads();
-            const int p = sm.win_pos;
-            const float *urow = sm.cand[sm.win_cta];
-            const float piv = urow[k];
-            // 5. interchange of positions pk and p (whole panel rows)
-            if (valid && gi == pk) {
+        }
+        __syncthreads();
+        const int p = sm.win_pos;
+        const float *u = sm.cand[sm.win_cta];    // u[3 + i] = pivot row, column k + i
+        const float piv = u[3];
+        // 5. interchange of positions pk and p; the pivot row is final (kept in Us)
+        if (valid && gi == pk) {
+            org = sm.uorg;
+        } else if (valid && gi == p) {
 #pragma unroll
-                for (int c = 0; c < NB; ++c) a[c] = urow[c];
-                org = sm.uorg;
-            } else if (valid && gi == p) {
+            for (int c = 0; c < NB; ++c) a[c] = sm.drow[c];
+            org = sm.dorg;
+        }
+        if (crank == 0 && warp == 1) {
+            Us[k * NB + lane] = u[3 + lane];
+            Us[k * NB + lane + 32] = u[35 + lane];
+        }
+        if (piv == 0.f && t == 0 && sm.zero_piv == 0) sm.zero_piv = pk + 1;
+        // 6. scale column k, update and shift the window: a[i] <- a[i+1] - l u[i+1]
+        if (valid && gi > pk) {
+            float l = a[0];
+            if (piv != 0.f) l = l / piv;
+            Ls[k * T + t] = l;
+            const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
 #pragma unroll
-                for (int c = 0; c < NB; ++c) a[c] = sm.drow[c];
-                org = sm.dorg;
-            }
-            if (crank == 0 && t == 0) {
-                ipiv[pk] = p;
-                if (piv == 0.f) atomicMin(&dev->info, pk + 1);
-            }
-            // 6. scale column k and update the rest of the panel
-            if (valid && gi > pk) {
-                float l = a[k];
-                if (piv != 0.f) l = l / piv;
-                a[k] = l;
-#pragma unroll
-                for (int c = k + 1; c < NB; ++c) a[c] = fmaf(-l, urow[c], a[c]);
+            for (int q = 0; q < NB / 4; ++q) {
+                const float4 w = us[q];
+                a[4 * q + 0] = fmaf(-l, w.x, a[4 * q + 1]);
+                a[4 * q + 1] = fmaf(-l, w.y, a[4 * q + 2]);
+                a[4 * q + 2] = fmaf(-l, w.z, a[4 * q + 3]);
+                a[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l, w.w, a[4 * q + 4]) : 0.f;
             }
         }
-    }
-    // write the factored panel back, and rTF(L21) for the tensor-core update
-    if (valid) {
-        float4 *dst = reinterpret_cast<float4 *>(AF + (int64_t)gi * ldf + j);
-#pragma unroll
-        for (int c = 0; c < NB; c += 4)
-            if (c < nbp) dst[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-        if (has_trailing && Aop != nullptr && gi >= j + NB) store_op_row(Aop, gi - (j + NB), a, tf);
     }
     // net permutation of the panel: position gi now holds the row from org
     int porg = 0;
@@ -294,8 +319,50 @@ __global__ void __launch_bounds__(T, 1)
         swap_list[2 + 2 * e] = org;
         porg = perm[org];
     }
-    cluster_sync_all();   // all reads of perm done; no CTA leaves while its smem may be read
+    if (crank == 0) {
+        for (int k = t; k < nbp; k += T) ipiv[j + k] = sm.piv_log[k];
+        if (t == 0 && sm.zero_piv) atomicMin(&dev->info, sm.zero_piv);
+    }
+    // all multipliers of the cluster are in shared memory; perm reads done
+    cluster_sync_all();
     if (moved) perm[gi] = porg;
+    if (valid) {
+        // multipliers of this row's content: walk the interchanges backward
+        // from the final position; at step k the content sat at position pos
+        const int kend = (gi - j < nbp) ? gi - j : nbp;
+        const unsigned ls_base = smem_u32(Ls);
+        int pos = gi;
+#pragma unroll
+        for (int k = NB - 1; k >= 0; --k) {
+            if (k < nbp) {
+                if (k < kend) {
+                    const int rel = pos - j;
+                    a[k] = ld_dsmem_f32(map_cta(ls_base + 4u * (unsigned)(k * T + (rel % T)), (unsigned)(rel / T)));
+                } else {
+                    a[k] = 0.f;
+                }
+                const int pkk = j + k, pp = sm.piv_log[k];
+                if (pos == pkk) pos = pp;
+                else if (pos == pp) pos = pkk;
+            } else {
+                a[k] = 0.f;
+            }
+        }
+        float *dst = AF + (int64_t)gi * ldf + j;
+        if (kend == NB) {
+#pragma unroll
+            for (int c = 0; c < NB; c += 4)
+                reinterpret_cast<float4 *>(dst)[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+        } else {
+            // a pivot row of this panel: L part, then its U part from Us
+#pragma unroll
+            for (int c = 0; c < NB; ++c)
+                if (c < kend) dst[c] = a[c];
+            for (int c = kend; c < nbp; ++c) dst[c] = Us[kend * NB + (c - kend)];
+        }
+        if (has_trailing && Aop != nullptr && gi >= j + NB) store_op_row(Aop, gi - (j + NB), a, tf);
+    }
+    cluster_sync_all();   // no CTA leaves while its shared memory may be read
 }
 
 // Apply the panel's row permutation to the columns outside the panel:
@@ -359,6 +426,8 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelDynSmem);
+        if (e != cudaSuccess) return e;
         attr_done = true;
     }
     int M = n - j;
@@ -367,7 +436,7 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(T, 1, 1);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kPanelDynSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
