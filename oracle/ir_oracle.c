@@ -25,6 +25,7 @@
  * rounding functions against numpy/torch conversions, the closed-form spectrum
  * of the Green's matrix, and the paper's printed residual histories.
  */
+#include <float.h>
 #include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -115,7 +116,10 @@ double orc_maxabs(int64_t n, int tw, const void *A, int64_t lda)
 
 /* Unblocked right-looking LU with partial pivoting in binary64.
  * Step k: p = first row i >= k with maximal |a_ik|; interchange rows k and p
- * across all columns; l_ik = a_ik / a_kk; a_ij = a_ij - l_ik a_kj for i, j > k.
+ * across all columns; scale the column the way LAPACK's getf2 does (which is
+ * what Julia's lu! runs for binary32/binary64 matrices): l_ik = a_ik * fl(1/a_kk)
+ * when |a_kk| is at least the smallest normal number, l_ik = a_ik / a_kk
+ * otherwise; then a_ij = a_ij - l_ik a_kj for i, j > k.
  * A zero pivot is recorded (1-based, first one) in the return value and the
  * column is left unscaled (its entries below the diagonal are all zero). */
 int64_t orc_getrf_f64(int64_t n, double *A, int64_t lda, int32_t *ipiv)
@@ -133,7 +137,12 @@ int64_t orc_getrf_f64(int64_t n, double *A, int64_t lda, int32_t *ipiv)
             }
         double akk = A[k + k * lda];
         if (akk == 0.0) { if (!info) info = k + 1; continue; }
-        for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] / akk;
+        if (fabs(akk) >= DBL_MIN) {
+            const double r = 1.0 / akk;
+            for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] * r;
+        } else {
+            for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] / akk;
+        }
 #pragma omp parallel for schedule(static)
         for (int64_t j = k + 1; j < n; ++j) {
             double u = A[k + j * lda];
@@ -147,7 +156,8 @@ int64_t orc_getrf_f64(int64_t n, double *A, int64_t lda, int32_t *ipiv)
 /* One pivot step of the binary32 factorization: choose the pivot row for
  * column k among rows k..n-1 (first maximal |a_ik|, or the forced row when
  * force >= 0), record max / runner-up / chosen magnitudes, interchange whole
- * rows, and scale column k.  Returns the chosen row. */
+ * rows, and scale column k as LAPACK's getf2 does (reciprocal of the pivot,
+ * plain division below the smallest normal).  Returns the chosen row. */
 static int64_t pivot_step_f32(int64_t n, float *A, int64_t lda, int64_t k,
                               int32_t force, float *gap, int64_t *info)
 {
@@ -166,7 +176,12 @@ static int64_t pivot_step_f32(int64_t n, float *A, int64_t lda, int64_t k,
         }
     float akk = A[k + k * lda];
     if (akk == 0.0f) { if (!*info) *info = k + 1; return p; }
-    for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] / akk;
+    if (fabsf(akk) >= FLT_MIN) {           /* LAPACK getf2: scale by the reciprocal */
+        const float r = 1.0f / akk;
+        for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] * r;
+    } else {
+        for (int64_t i = k + 1; i < n; ++i) A[i + k * lda] = A[i + k * lda] / akk;
+    }
     return p;
 }
 
@@ -245,20 +260,24 @@ int64_t orc_getrf_tf(int64_t n, float *A, int64_t lda, int32_t *ipiv, int tf,
 /* Triangular solves d = U^{-1} L^{-1} P v (Algorithm IR; eq. vdlow).         */
 /* ------------------------------------------------------------------------ */
 
-/* binary32: interchanges of ipiv applied in order, then forward substitution
- * with unit lower L (v_i = v_i - sum_{j<i} l_ij v_j, j ascending), then back
- * substitution with U (v_i = (v_i - sum_{j>i} u_ij v_j) / u_ii, j ascending). */
+/* binary32: interchanges of ipiv applied in order, then the two triangular
+ * solves in the order of the reference BLAS trsv for a column-major matrix
+ * (the solve LAPACK getrs performs):
+ *   forward, unit lower L: for j ascending, v_i -= l_ij v_j for all i > j;
+ *   back, U: for j descending, v_j /= u_jj, then v_i -= u_ij v_j for all i < j.
+ * Each entry therefore sees its updates in ascending j (forward) and in
+ * descending j (back), each a single-rounding fma. */
 void orc_getrs_f32(int64_t n, const float *LU, int64_t lda, const int32_t *ipiv, float *v)
 {
     for (int64_t k = 0; k < n; ++k) {
         int64_t p = ipiv[k];
         if (p != k) { float t = v[k]; v[k] = v[p]; v[p] = t; }
     }
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < i; ++j) v[i] = fmaf(-LU[i + j * lda], v[j], v[i]);
-    for (int64_t i = n - 1; i >= 0; --i) {
-        for (int64_t j = i + 1; j < n; ++j) v[i] = fmaf(-LU[i + j * lda], v[j], v[i]);
-        v[i] = v[i] / LU[i + i * lda];
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j + 1; i < n; ++i) v[i] = fmaf(-LU[i + j * lda], v[j], v[i]);
+    for (int64_t j = n - 1; j >= 0; --j) {
+        v[j] = v[j] / LU[j + j * lda];
+        for (int64_t i = 0; i < j; ++i) v[i] = fmaf(-LU[i + j * lda], v[j], v[i]);
     }
 }
 
@@ -269,11 +288,11 @@ void orc_getrs_f64(int64_t n, const double *LU, int64_t lda, const int32_t *ipiv
         int64_t p = ipiv[k];
         if (p != k) { double t = v[k]; v[k] = v[p]; v[p] = t; }
     }
-    for (int64_t i = 0; i < n; ++i)
-        for (int64_t j = 0; j < i; ++j) v[i] = fma(-LU[i + j * lda], v[j], v[i]);
-    for (int64_t i = n - 1; i >= 0; --i) {
-        for (int64_t j = i + 1; j < n; ++j) v[i] = fma(-LU[i + j * lda], v[j], v[i]);
-        v[i] = v[i] / LU[i + i * lda];
+    for (int64_t j = 0; j < n; ++j)
+        for (int64_t i = j + 1; i < n; ++i) v[i] = fma(-LU[i + j * lda], v[j], v[i]);
+    for (int64_t j = n - 1; j >= 0; --j) {
+        v[j] = v[j] / LU[j + j * lda];
+        for (int64_t i = 0; i < j; ++i) v[i] = fma(-LU[i + j * lda], v[j], v[i]);
     }
 }
 

@@ -421,3 +421,18 @@ def test_reference_solution_exact_small():
     xr = O.reference_solution(A, b)
     xe = [float(v) for v in _exact_solve(A, b)]
     assert max(abs(a - e) / abs(e) for a, e in zip(xr, xe)) <= 2 ** -52
+
+
+def test_lu_column_scaling_is_lapack_reciprocal():
+    """getf2 scales the pivot column by fl(1/a_kk) (binary32: fl32(a * fl32(1/a_kk))),
+    and divides only when |a_kk| is below the smallest normal number."""
+    # pivot 7, entry 3: 3 * fl(1/7) = 0.42857146 while 3 / 7 = 0.42857143 in binary32
+    LUd, _, _ = O.getrf_tf(np.asfortranarray(np.array([[7.0, 0.0], [3.0, 1.0]], dtype=np.float32)), O.F32)
+    assert LUd[1, 0] == np.float32(0.42857146)          # 3 * fl(1/7); 3 / 7 would give 0.42857143
+    assert LUd[1, 0] != np.float32(np.float32(3.0) / np.float32(7.0))
+    LU64, _, _ = O.getrf_f64(np.asfortranarray(np.array([[7.0, 0.0], [3.0, 1.0]])))
+    assert LU64[1, 0] == 3.0 * (1.0 / 7.0)
+    tiny = np.float32(1e-39)     # subnormal pivot: plain division
+    B = np.asfortranarray(np.array([[tiny, 0.0], [np.float32(5e-40), 1.0]], dtype=np.float32))
+    LUb, _, _ = O.getrf_tf(B, O.F32)
+    assert LUb[1, 0] == np.float32(np.float32(5e-40) / tiny)
