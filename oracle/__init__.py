@@ -259,6 +259,10 @@ def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: 
     rn = rhist[-1]
     if not np.isfinite(rn):
         return DIVERGED
+    if rn == 0.0:
+        # x solves the (promoted) system exactly; the scaling r / ||r|| of
+        # eq. (vdlow) is undefined for the next step, so stop here
+        return CONVERGED
     if tr_wider:
         # eq. (wilkterm): corrections stagnate
         if len(dhist) >= 2 and dhist[-1] >= term.Rmax * dhist[-2]:

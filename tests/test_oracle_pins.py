@@ -436,3 +436,22 @@ def test_lu_column_scaling_is_lapack_reciprocal():
     B = np.asfortranarray(np.array([[tiny, 0.0], [np.float32(5e-40), 1.0]], dtype=np.float32))
     LUb, _, _ = O.getrf_tf(B, O.F32)
     assert LUb[1, 0] == np.float32(np.float32(5e-40) / tiny)
+
+
+@pytest.mark.parametrize("a,b", [(3.0, 1.0), (-177.78664, 1.0), (7.0, 2.0), (0.1, 0.3)])
+def test_scalar_promoted_problem_stops_at_exact_solution(a, b):
+    """n = 1, TW = TF = binary32, TR = binary64 (the promoted problem, Sec. 2.2.2).
+
+    The iterate approaches b/a geometrically, so the residual eventually
+    vanishes exactly (fl(a x) = b) before eq. (wilkterm) ever fires; IR must
+    stop there as converged, with the binary32 solution fl32(b/a), instead of
+    dividing by ||r|| = 0 in the next scaled solve (eq. vdlow)."""
+    A = np.array([[a]], dtype=np.float32, order="F")
+    bb = np.array([b], dtype=np.float32)
+    res = O.ir_solve(A, bb, O.F32, term=O.Term(litmax=30))
+    assert res.status == O.CONVERGED
+    assert res.rhist[-1] == 0.0
+    assert np.all(np.isfinite(res.x))
+    exact = np.float64(bb[0]) / np.float64(A[0, 0])
+    assert res.sol[0] == np.float32(exact)
+    assert abs(res.x[0] - exact) <= 2 * np.spacing(abs(exact))
