@@ -47,7 +47,7 @@ typedef enum {
 
 /* Outcome of the refinement loop (numerical non-convergence is not an error). */
 typedef enum {
-    IR_CONVERGED = 0,     /* eq. (residterm) held */
+    IR_CONVERGED = 0,     /* eq. (residterm) held, or the residual is exactly zero */
     IR_STAGNATED = 1,     /* eq. (stag), or eq. (wilkterm) when TR is wider than TW */
     IR_MAXIT = 2,         /* litmax residual computations without termination */
     IR_DIVERGED = 3,      /* the residual norm became non-finite */
@@ -55,7 +55,8 @@ typedef enum {
 } ir_solve_status;
 
 /* Termination parameters: the TERM structure of Sec. 5.1.3.
- *   converged   if ||r|| <= Cr * eps(TW) * ||b||        (eq. residterm)
+ *   converged   if ||r|| == 0 (x is exact; r / ||r|| would be undefined)
+ *               or ||r|| <= Cr * eps(TW) * ||b||         (eq. residterm)
  *               or, when abs_rel_tol > 0, ||r|| <= abs_rel_tol * ||b||
  *   stagnated   if ||r_new|| >= Rmax ||r_old||           (eq. stag), TR == TW
  *               if ||d_new|| >= Rmax ||d_old||           (eq. wilkterm), TR wider than TW
@@ -172,6 +173,62 @@ ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_
 ir_status ir_residual_noalloc(int64_t n, ir_dtype TW, const void *A, int64_t lda,
                               const void *b, const double *x, double *r, double *rnorm,
                               void *stream);
+
+/* ---- Batched solves ----------------------------------------------------------
+ * The paper solves one system at a time; a batch runs the same steps as
+ * ir_factor + ir_solve (the cast A_F = I_W^F(s A) of Sec. 1, LU with partial
+ * pivoting in TF, Algorithm IR with the termination rules of Sec. 5.1, the
+ * binary16 scaling s = 2^10 / max|a_ij|) for `count` independent systems of
+ * uneven size inside ONE persistent kernel launch: one CTA per SM takes the
+ * systems largest first from a device-side ticket.  The solves of a batch run
+ * in binary32 by column sweeps (the reference BLAS trsv order); the residual
+ * in binary64.  Sizes: 0 <= n_i <= IR_BATCH_MAX_N.
+ *
+ * Per-system outcome, written to device memory by the launch: */
+#define IR_BATCH_MAX_N 512
+typedef struct {
+    int32_t status;      /* ir_solve_status */
+    int32_t iters;       /* residual computations */
+    int64_t info;        /* first zero pivot (1-based) or 0 */
+    int32_t nonfinite;   /* 1: NaN/Inf in A or b, or overflow of the rounded copy */
+    int32_t pad;
+    double rnorm;        /* ||r||_inf after the last residual (||b|| when none ran) */
+    double scale;        /* s of the rounded copy */
+} ir_batch_result;
+
+typedef struct ir_batch ir_batch;
+
+/* Plan a batch: check the arguments, order the systems, upload their
+ * descriptors and allocate the workspace (one slot of max_i n_i^2 binary32
+ * values per resident CTA).  Synchronous; allocates device memory.
+ *   count >= 0; n_host[i]: sizes; A_dev[i], b_dev[i], x_dev[i]: DEVICE
+ *   pointers held in HOST arrays (A_i column-major n_i x n_i in TW, b_i and
+ *   x_i n_i values in TW); lda_host may be NULL (lda_i = n_i), else
+ *   lda_host[i] >= max(1, n_i).  opts: TW in {F64, F32}, TF in {F32, TF32,
+ *   BF16, F16}, TR = F64, nb in {0, 64}.  term may be NULL (defaults).
+ * The plan BORROWS every A_i, b_i and x_i: they must stay allocated until
+ * ir_batch_destroy.  A size above IR_BATCH_MAX_N gives IR_EUNSUPPORTED. */
+ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host,
+                          const void *const *A_dev, const int64_t *lda_host,
+                          const void *const *b_dev, void *const *x_dev,
+                          const ir_opts *opts, const ir_term *term, ir_batch **out);
+
+/* Run a planned batch on `stream`: a 4-byte memset and one kernel launch,
+ * with no allocation and no host synchronisation, so it can be captured in
+ * a CUDA graph and replayed.  results_dev: `count` ir_batch_result in device
+ * memory, in the order of the plan's arrays.  x_i is written unless
+ * results_dev[i].status is IR_FAILED.  Runs of one plan must not overlap
+ * (they share its workspace): order them on one stream. */
+ir_status ir_batch_run(ir_batch *batch, ir_batch_result *results_dev, void *stream);
+void ir_batch_destroy(ir_batch *batch);
+
+/* One-shot batch: ir_batch_create + ir_batch_run + synchronisation of
+ * `stream` + ir_batch_destroy. */
+ir_status ir_factor_solve_batched(ir_ctx *ctx, int64_t count, const int64_t *n_host,
+                                  const void *const *A_dev, const int64_t *lda_host,
+                                  const void *const *b_dev, void *const *x_dev,
+                                  const ir_opts *opts, const ir_term *term, void *stream,
+                                  ir_batch_result *results_dev);
 
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */
 ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);

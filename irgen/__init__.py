@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "green_g", "gmat_midpoint", "gmat_trapezoid", "midpoint_nodes",
     "case_green", "case_green_sine", "case_gaussian", "case_svd", "case_batch",
-    "case_random", "SEED_BASE",
+    "case_random", "case_batch_sizes", "SEED_BASE",
 ]
 
 SEED_BASE = 1000
@@ -135,3 +135,18 @@ def case_batch(count: int, seed: int, nmin: int = 32, nmax: int = 512):
         As.append(np.asfortranarray(A))
         bs.append(np.ones(n))
     return ns.astype(np.int64), alphas, As, bs
+
+
+def case_batch_sizes(ns, seed: int):
+    """The recipe of case_batch with the sizes given: A_i = I - alpha_i G_mid + 1e-3 E_i
+    (alpha_i ~ U[1, 800], E_i N(0,1)), b_i = 1.  Returns (alphas, As, bs)."""
+    g = _rng(seed)
+    alphas = g.uniform(1.0, 800.0, size=len(ns))
+    As, bs = [], []
+    for n, a in zip(ns, alphas):
+        n = int(n)
+        E = g.standard_normal((n, n))
+        A = np.eye(n) - a * gmat_midpoint(n) + 1e-3 * E if n else np.zeros((0, 0))
+        As.append(np.asfortranarray(A))
+        bs.append(np.ones(n))
+    return alphas, As, bs

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <algorithm>
 #include <atomic>
 #include <new>
 #include <vector>
@@ -27,10 +28,11 @@ namespace {
 // call on the launching stream, summed per kind when profiling stops.
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
-    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_N
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
-                                "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x"};
+                                "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
+                                "batched"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -92,6 +94,8 @@ ir_status cuda_fail(cudaError_t e, const char *what) {
     } while (0)
 
 constexpr int kInfoNone = 0x7F7F7F7F;   // memset(0x7F) pattern: no zero pivot
+constexpr int kSwapListInts = 1 + 4 * kPanelNB;
+constexpr int kPanelReserveSMs = 16;     // SMs the trailing update leaves to the next panel
 
 bool tw_ok(ir_dtype t) { return t == IR_F64 || t == IR_F32; }
 bool tf_ok(ir_dtype t) { return t == IR_F32 || t == IR_TF32 || t == IR_BF16 || t == IR_F16; }
@@ -132,6 +136,9 @@ void free_fact(ir_fact *f) {
     if (f->host_dev) cudaFreeHost(f->host_dev);
     if (f->graph) cudaGraphExecDestroy(f->graph);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
+    if (f->la_stream) cudaStreamDestroy(f->la_stream);
+    for (int i = 0; i < f->la_nevents; ++i) cudaEventDestroy(f->la_events[i]);
+    delete[] f->la_events;
     delete f;
 }
 
@@ -157,10 +164,10 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     AL(f->AF, (size_t)nn * f->ldf * sizeof(float));
     AL(f->ipiv, nn * sizeof(int32_t));
     AL(f->perm, nn * sizeof(int32_t));
-    AL(f->swap_list, (1 + 4 * kPanelNB) * sizeof(int32_t));
+    AL(f->swap_list, 2 * kSwapListInts * sizeof(int32_t));
     if (o->TF != IR_F32) {
-        AL(f->Aop, (size_t)nn * kPanelNB * op_elem(o->TF));
-        AL(f->Bop, (size_t)nn * kPanelNB * op_elem(o->TF));
+        AL(f->Aop, 2 * (size_t)nn * kPanelNB * op_elem(o->TF));
+        AL(f->Bop, 2 * (size_t)nn * kPanelNB * op_elem(o->TF));
     }
     AL(f->Linv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
     AL(f->Uinv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
@@ -188,7 +195,43 @@ fail:
     return st;
 }
 
+bool lookahead_enabled() {
+    const char *e = std::getenv("IR_NO_LOOKAHEAD");
+    return !(e && e[0] && e[0] != '0');
+}
+
+ir_status ensure_lookahead(ir_fact *f) {
+    const int need = 2 * (int)((f->n + kPanelNB - 1) / kPanelNB) + 2;
+    if (!f->la_stream) {
+        int lo = 0, hi = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
+        CK(cudaStreamCreateWithPriority(&f->la_stream, cudaStreamNonBlocking, lo));
+    }
+    if (f->la_nevents < need) {
+        for (int i = 0; i < f->la_nevents; ++i) cudaEventDestroy(f->la_events[i]);
+        delete[] f->la_events;
+        f->la_events = new (std::nothrow) cudaEvent_t[need];
+        f->la_nevents = 0;
+        if (!f->la_events) return IR_ENOMEM;
+        for (int i = 0; i < need; ++i) {
+            CK(cudaEventCreateWithFlags(&f->la_events[i], cudaEventDisableTiming));
+            f->la_nevents = i + 1;
+        }
+    }
+    return IR_OK;
+}
+
 // Cast + blocked right-looking LU with partial pivoting + diagonal-block inverses.
+//
+// With lookahead (two streams, captured into one graph): step j runs
+//   s1: panel(j), [wait R(j-1)], row interchanges, U12 and update of the next
+//       block column only, then panel(j+1) ...
+//   s2: [wait P(j)] row interchanges of the other columns, U12 and update of
+//       the remaining trailing columns (persistent kernels that leave SMs to
+//       the panel), record R(j)
+// so the next panel overlaps the bulk of the trailing update.  The swap list
+// and the tensor-core operand buffers alternate between two copies by step
+// parity.  Every element still receives its updates in block order.
 ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
     const int n = (int)f->n;
     const int64_t ldf = f->ldf;
@@ -200,19 +243,71 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
     RUN(KC_CAST, s, launch_cast(n, f->TW, f->A, f->lda, f->TF, use_scale, f->AF, ldf, f->dev, s));
     RUN(KC_IOTA, s, launch_iota(n, f->perm, s));
     const int NB = kPanelNB;
-    for (int j = 0; j < n; j += NB) {
+    const int sms = f->ctx->sms;
+    const size_t opsz = (f->TF == IR_F32) ? 0 : (size_t)n * NB * op_elem(f->TF);
+    const bool la = !g_prof.on && lookahead_enabled() && n > 2 * NB;
+    cudaStream_t s2 = s;
+    int ev = 0;
+    if (la) {
+        ir_status st = ensure_lookahead(f);
+        if (st != IR_OK) return st;
+        s2 = f->la_stream;
+        CK(cudaEventRecord(f->la_events[ev], s));       // s2 joins after the cast
+        CK(cudaStreamWaitEvent(s2, f->la_events[ev], 0));
+        ++ev;
+    }
+    cudaEvent_t pending_rest = nullptr;                  // R(j-1): s2's work of the previous step
+    for (int j = 0, step = 0; j < n; j += NB, ++step) {
         const int nbp = (n - j < NB) ? n - j : NB;
-        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, f->swap_list, f->dev,
-                                      f->TF, f->Aop, s));
-        RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, n, j, nbp, f->swap_list, s));
-        if (j + nbp < n) {
-            RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, n, j, NB, f->TF, f->Bop, s));
+        const int par = step & 1;
+        int32_t *sl = f->swap_list + par * kSwapListInts;
+        void *aop = f->Aop ? static_cast<char *>(f->Aop) + par * opsz : nullptr;
+        void *bop = f->Bop ? static_cast<char *>(f->Bop) + par * opsz : nullptr;
+        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s));
+        const bool trailing = j + nbp < n;
+        if (la) {
+            cudaEvent_t evP = f->la_events[ev++];
+            CK(cudaEventRecord(evP, s));
+            if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
+            pending_rest = nullptr;
+            if (!trailing) {
+                RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, 0, j, 0, 0, sl, s));
+                break;
+            }
+            const int nx0 = j + NB, nx1 = (j + 2 * NB < n) ? j + 2 * NB : n;
+            // s1: the next block column
+            RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, nx0, nx1, 0, 0, sl, s));
+            RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, s));
             if (f->TF == IR_F32)
-                RUN(KC_GEMM_SIMT, s, launch_gemm_simt(f->AF, ldf, n, j, NB, s));
+                RUN(KC_GEMM_SIMT, s, launch_gemm_simt(f->AF, ldf, n, j, NB, nx0, nx1, 0, s));
             else
-                RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, f->TF, f->Aop, f->Bop, f->ctx->sms, f->dev, s));
+                RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, nx0, nx1, f->TF, aop, bop, sms, 0, f->dev, s));
+            // s2: everything else of this step
+            CK(cudaStreamWaitEvent(s2, evP, 0));
+            RUN(KC_LASWP, s2, launch_laswp(f->AF, ldf, 0, j, nx1, n, sl, s2));
+            if (nx1 < n) {
+                RUN(KC_TRSM, s2, launch_trsm(f->AF, ldf, nx1, n, j, f->TF, bop, s2));
+                if (f->TF == IR_F32)
+                    RUN(KC_GEMM_SIMT, s2, launch_gemm_simt(f->AF, ldf, n, j, NB, nx1, n, sms - kPanelReserveSMs, s2));
+                else
+                    RUN(KC_GEMM_TC, s2, launch_gemm_tc(f->AF, ldf, n, j, NB, nx1, n, f->TF, aop, bop, sms,
+                                                       sms - kPanelReserveSMs, f->dev, s2));
+            }
+            pending_rest = f->la_events[ev++];
+            CK(cudaEventRecord(pending_rest, s2));
+        } else {
+            RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, 0, j, j + nbp, n, sl, s));
+            if (trailing) {
+                RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, j + NB, n, j, f->TF, bop, s));
+                if (f->TF == IR_F32)
+                    RUN(KC_GEMM_SIMT, s, launch_gemm_simt(f->AF, ldf, n, j, NB, j + NB, n, 0, s));
+                else
+                    RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, j + NB, n, f->TF, aop, bop, sms, 0,
+                                                      f->dev, s));
+            }
         }
     }
+    if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
     RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, s));
     return IR_OK;
 }
@@ -271,6 +366,7 @@ int term_decide(const double *rh, const double *dh, int k, double bnorm, double 
                 const ir_term *t, bool tr_wider) {
     const double rn = rh[k];
     if (!std::isfinite(rn)) return IR_DIVERGED;
+    if (rn == 0.0) return IR_CONVERGED;    // exact solution: r / ||r|| (eq. vdlow) is undefined next
     if (tr_wider) {
         if (k >= 2 && dh[k - 1] >= t->Rmax * dh[k - 2]) return IR_STAGNATED;   // eq. (wilkterm)
     } else {
@@ -280,6 +376,35 @@ int term_decide(const double *rh, const double *dh, int k, double bnorm, double 
     }
     if (k >= t->litmax) return IR_MAXIT;
     return -1;
+}
+
+}  // namespace
+
+// A planned batch (ir_batch_create): descriptors and the largest-first order on
+// the device, the ticket counter of the persistent launch, the workspace slots.
+struct ir_batch {
+    ir_ctx *ctx;
+    int64_t count;
+    ir_dtype TW, TF;
+    int fp16_scale;
+    ir_term term;
+    void *desc;          // count descriptors (device)
+    int *order;          // count system indices, largest n first (device)
+    unsigned *ticket;    // next position in `order` (device)
+    float *ws;           // grid slots of ws_stride floats
+    int64_t ws_stride;
+    int grid;
+};
+
+namespace {
+
+void free_batch(ir_batch *b) {
+    if (!b) return;
+    cudaFree(b->desc);
+    cudaFree(b->order);
+    cudaFree(b->ticket);
+    cudaFree(b->ws);
+    delete b;
 }
 
 }  // namespace
@@ -440,6 +565,12 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     ir_status st = read_dev(f, s);
     if (st != IR_OK) return st;
     R.scale = f->host_dev->scale;
+    if (f->host_dev->timeout) {
+        snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the factorization timed out");
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ETIMEOUT;
+    }
     if (f->host_dev->nonfinite) {
         R.status = IR_FAILED;
         if (rep) *rep = R;
@@ -521,6 +652,103 @@ ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_
     CK(launch_residual(n, TW, A, lda, b, x, r, ctx->partials, ctx->partials_cap,
                        reinterpret_cast<unsigned long long *>(rnorm), ctx->sms, (cudaStream_t)stream));
     return IR_OK;
+}
+
+ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host, const void *const *A_dev,
+                          const int64_t *lda_host, const void *const *b_dev, void *const *x_dev,
+                          const ir_opts *opts, const ir_term *term, ir_batch **out) {
+    if (!ctx || !out || count < 0) return IR_EINVAL;
+    *out = nullptr;
+    if (count > 0 && (!n_host || !A_dev || !b_dev || !x_dev)) return IR_EINVAL;
+    if (count > INT_MAX / 2) return IR_EUNSUPPORTED;
+    ir_opts o;
+    if (opts) o = *opts;
+    else ir_default_opts(&o);
+    if (!tw_ok(o.TW) || !tf_ok(o.TF) || o.TR != IR_F64) return IR_EINVAL;
+    if (o.nb != 0 && o.nb != kPanelNB) return IR_EUNSUPPORTED;
+    ir_term t;
+    if (term) t = *term;
+    else ir_default_term(&t);
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    int64_t maxn = 0;
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t n = n_host[i];
+        const int64_t lda = lda_host ? lda_host[i] : (n > 1 ? n : 1);
+        if (n < 0 || lda < (n > 1 ? n : 1)) return IR_EINVAL;
+        if (n > 0 && (!A_dev[i] || !b_dev[i] || !x_dev[i])) return IR_EINVAL;
+        if (n > IR_BATCH_MAX_N) {
+            snprintf(g_last_error, sizeof g_last_error, "system %lld has n = %lld > IR_BATCH_MAX_N",
+                     (long long)i, (long long)n);
+            return IR_EUNSUPPORTED;
+        }
+        maxn = std::max(maxn, n);
+    }
+    CK(cudaSetDevice(ctx->device));
+    ir_batch *b = new (std::nothrow) ir_batch();
+    if (!b) return IR_ENOMEM;
+    b->ctx = ctx;
+    b->count = count;
+    b->TW = o.TW;
+    b->TF = o.TF;
+    b->fp16_scale = o.fp16_scale;
+    b->term = t;
+    ir_status st = IR_OK;
+    cudaError_t e = batch_grid(ctx->sms, count, &b->grid);
+    const int64_t cnt = count > 0 ? count : 1;
+    // one slot per resident CTA: max n rows of (n rounded up to a multiple of 4) floats
+    b->ws_stride = std::max<int64_t>((maxn * ((maxn + 3) / 4 * 4) + 31) / 32 * 32, 32);
+    std::vector<unsigned char> desc(batch_desc_bytes() * cnt);
+    std::vector<int> order(cnt, 0);
+    for (int64_t i = 0; i < count; ++i) {
+        const int64_t n = n_host[i];
+        batch_fill_desc(desc.data(), i, A_dev[i], lda_host ? lda_host[i] : (n > 1 ? n : 1), b_dev[i], x_dev[i],
+                        (int)n);
+        order[i] = (int)i;
+    }
+    // longest first: the CTAs take the big systems first and the small ones fill the tail
+    std::stable_sort(order.begin(), order.begin() + count,
+                     [&](int x, int y) { return n_host[x] > n_host[y]; });
+    if (e == cudaSuccess) e = cudaMalloc(&b->desc, desc.size());
+    if (e == cudaSuccess) e = cudaMalloc(&b->order, cnt * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->ws, (size_t)b->grid * b->ws_stride * sizeof(float));
+    if (e == cudaSuccess) e = cudaMemcpy(b->desc, desc.data(), desc.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), cnt * sizeof(int), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        st = cuda_fail(e, "ir_batch_create");
+        free_batch(b);
+        return st;
+    }
+    *out = b;
+    return IR_OK;
+}
+
+ir_status ir_batch_run(ir_batch *b, ir_batch_result *results_dev, void *stream) {
+    if (!b || (b->count > 0 && !results_dev)) return IR_EINVAL;
+    if (b->count == 0) return IR_OK;
+    CK(cudaSetDevice(b->ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    RUN(KC_BATCHED, s, launch_batched(b->desc, b->order, b->count, b->ticket, b->ws, b->ws_stride, b->grid, b->TW,
+                                      b->TF, b->fp16_scale, &b->term, results_dev, s));
+    return IR_OK;
+}
+
+void ir_batch_destroy(ir_batch *b) { free_batch(b); }
+
+ir_status ir_factor_solve_batched(ir_ctx *ctx, int64_t count, const int64_t *n_host, const void *const *A_dev,
+                                  const int64_t *lda_host, const void *const *b_dev, void *const *x_dev,
+                                  const ir_opts *opts, const ir_term *term, void *stream,
+                                  ir_batch_result *results_dev) {
+    ir_batch *b = nullptr;
+    ir_status st = ir_batch_create(ctx, count, n_host, A_dev, lda_host, b_dev, x_dev, opts, term, &b);
+    if (st != IR_OK) return st;
+    st = ir_batch_run(b, results_dev, stream);
+    if (st == IR_OK) {
+        const cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) st = cuda_fail(e, "ir_factor_solve_batched");
+    }
+    ir_batch_destroy(b);
+    return st;
 }
 
 ir_status ir_fact_pivots(const ir_fact *f, int32_t *ipiv_host) {

@@ -60,8 +60,11 @@ struct ir_fact {
     float *AF;
     int32_t *ipiv;           // 0-based pivots
     int32_t *perm;           // (P A)[i] = A[perm[i]]
-    int32_t *swap_list;      // 1 + 2*2*NB ints: count, then (dst, src) pairs of a panel
-    void *Aop, *Bop;         // tensor-core operands (NULL for TF = F32)
+    int32_t *swap_list;      // 2 x (1 + 2*2*NB) ints: count, then (dst, src) pairs, by step parity
+    void *Aop, *Bop;         // tensor-core operands, 2 buffers each by step parity (NULL for TF = F32)
+    cudaStream_t la_stream;  // low-priority stream of the lookahead schedule
+    cudaEvent_t *la_events;  // fork/join events of the lookahead schedule
+    int la_nevents;
     float *Linv, *Uinv;      // diagonal-block inverses, nblk x 64 x 64
     unsigned long long *tags;  // 2 x nblk*64 tagged solve values (epoch << 32 | bits)
     unsigned epoch;            // tag of the latest solve
@@ -95,14 +98,15 @@ cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, c
 cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
                          int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
                          void *Aop, cudaStream_t s);
-cudaError_t launch_laswp(float *AF, int64_t ldf, int n, int j, int nbp, const int32_t *swap_list,
-                         cudaStream_t s);
-cudaError_t launch_trsm(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, void *Bop,
+cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b,
+                         const int32_t *swap_list, cudaStream_t s);
+cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
                         cudaStream_t s);
-cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, cudaStream_t s);
-cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf,
-                           const void *Aop, const void *Bop, int sms, DevScalars *dev,
-                           cudaStream_t s);
+cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
+                             int max_ctas, cudaStream_t s);
+cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
+                           ir_dtype tf, const void *Aop, const void *Bop, int sms, int max_ctas,
+                           DevScalars *dev, cudaStream_t s);
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
@@ -116,6 +120,14 @@ cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, 
                             const double *x, double *r, double *partials, int64_t partials_cap,
                             unsigned long long *rnorm_bits, int sms, cudaStream_t s);
 int64_t residual_partials_needed(int64_t n, int sms);
+
+// batched driver (many systems with n <= IR_BATCH_MAX_N, one persistent launch)
+size_t batch_desc_bytes();
+void batch_fill_desc(void *desc, int64_t i, const void *A, int64_t lda, const void *b, void *x, int n);
+cudaError_t batch_grid(int sms, int64_t count, int *grid);
+cudaError_t launch_batched(const void *sys, const int *order, int64_t count, unsigned *ticket, float *ws,
+                           int64_t ws_stride, int grid, ir_dtype tw, ir_dtype tf, int fp16_scale,
+                           const ir_term *t, ir_batch_result *results, cudaStream_t s);
 
 // ---- device helpers --------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p) {

@@ -8,13 +8,19 @@ namespace ir {
 namespace {
 
 constexpr int BM = 128, BN = 128, BK = 32, NB = kPanelNB;
+constexpr int kShareCluster = 8;
 
-__global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n, int j) {
+// Columns [cb, ce) of the trailing matrix (cb, ce multiples of 64, or ce = n);
+// tiles are taken in a grid-stride loop so the grid can leave SMs free.
+__global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n, int j, int cb, int ce) {
     __shared__ __align__(16) float As[BK][BM + 4];   // As[k][i] = L21[i][k]
     __shared__ __align__(16) float Bs[BK][BN + 4];   // Bs[k][c] = U12[k][c]
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int i0 = j + NB + blockIdx.y * BM;
-    const int c0 = j + NB + blockIdx.x * BN;
+    const int m = n - (j + NB);
+    const int tiles_m = (m + BM - 1) / BM, tiles_n = (ce - cb + BN - 1) / BN;
+    for (int tile = blockIdx.x; tile < tiles_m * tiles_n; tile += gridDim.x) {
+    const int i0 = j + NB + (tile / tiles_n) * BM;
+    const int c0 = cb + (tile % tiles_n) * BN;
 
     // C micro-tile: rows i0 + {ty*4 + r, 64 + ty*4 + r}, cols c0 + {tx*4 + q, 64 + tx*4 + q}
     float acc[8][8];
@@ -25,7 +31,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n
         for (int h = 0; h < 2; ++h) {
             const int c = c0 + h * 64 + tx * 4;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (i < n && c < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c);
+            if (i < n && c < ce) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c);
             acc[r][h * 4 + 0] = v.x; acc[r][h * 4 + 1] = v.y;
             acc[r][h * 4 + 2] = v.z; acc[r][h * 4 + 3] = v.w;
         }
@@ -48,7 +54,7 @@ __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n
             const int m = idx >> 5, cq = (idx & 31) * 4;
             const int c = c0 + cq;
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (c < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + kb + m) * ldf + c);
+            if (c < ce) v = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + kb + m) * ldf + c);
             *reinterpret_cast<float4 *>(&Bs[m][cq]) = v;
         }
         __syncthreads();
@@ -74,22 +80,51 @@ __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int c = c0 + h * 64 + tx * 4;
-            if (c < n)
+            if (c < ce)
                 *reinterpret_cast<float4 *>(AF + (int64_t)i * ldf + c) =
                     make_float4(acc[r][h * 4 + 0], acc[r][h * 4 + 1], acc[r][h * 4 + 2], acc[r][h * 4 + 3]);
         }
+    }
     }
 }
 
 }  // namespace
 
-cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, cudaStream_t s) {
+// max_ctas > 0: share the GPU with a concurrent panel -- the update runs as
+// clusters of 8 CTAs, two clusters fewer than fit at once, so that whole GPC
+// slots stay free for the panel's cluster.
+cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce, int max_ctas,
+                             cudaStream_t s) {
     const int m = n - (j + nb);
-    if (m <= 0) return cudaSuccess;
-    dim3 grid((m + BN - 1) / BN, (m + BM - 1) / BM);
+    if (m <= 0 || ce <= cb) return cudaSuccess;
+    const int tiles = ((m + BM - 1) / BM) * ((ce - cb + BN - 1) / BN);
     count_launch();
-    k_gemm_simt<<<grid, 256, 0, s>>>(AF, ldf, n, j);
-    return cudaGetLastError();
+    if (max_ctas <= 0) {
+        k_gemm_simt<<<tiles, 256, 0, s>>>(AF, ldf, n, j, cb, ce);
+        return cudaGetLastError();
+    }
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kShareCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    static int max_clusters = -1;
+    if (max_clusters < 0) {
+        cfg.gridDim = dim3(kShareCluster * 64, 1, 1);
+        if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_simt, &cfg) != cudaSuccess) max_clusters = 0;
+        (void)cudaGetLastError();
+    }
+    int clusters = max_clusters - 2;
+    if (clusters < 1) clusters = 1;
+    const int need = (tiles + kShareCluster - 1) / kShareCluster;
+    if (clusters > need) clusters = need;
+    cfg.gridDim = dim3(clusters * kShareCluster, 1, 1);
+    return cudaLaunchKernelEx(&cfg, k_gemm_simt, AF, ldf, n, j, cb, ce);
 }
 
 }  // namespace ir

@@ -64,7 +64,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned addr, unsigned parity, volati
         if (*abort_flag) return false;
         if (globaltimer() - t0 > kWaitLimitNs) {
             *abort_flag = 1;
-            atomicExch(timeout, 1);
+            if (timeout) atomicExch(timeout, 1);
             return false;
         }
     }
@@ -246,12 +246,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (*abort_flag) {
                 // drain: wait (bounded) until the copies this thread issued have landed
-                int dummy = 0;
                 volatile int no_abort = 0;
                 for (int q = 0; q < STAGES; ++q)
-                    if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, &dummy);
+                    if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, nullptr);
                 for (int q = 0; q < kCBufs; ++q)
-                    if (cissued[q]) mbar_wait(cfull_bar(q), last_cph[q], &no_abort, &dummy);
+                    if (cissued[q]) mbar_wait(cfull_bar(q), last_cph[q], &no_abort, nullptr);
             }
         }
     } else if (warp == 1) {
@@ -281,10 +280,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             }
             if (*abort_flag) {
                 // wait (bounded) until the tensor core has finished everything issued
-                int dummy = 0;
                 volatile int no_abort = 0;
                 mma_commit(drain_bar);
-                mbar_wait(drain_bar, 0u, &no_abort, &dummy);
+                mbar_wait(drain_bar, 0u, &no_abort, nullptr);
             }
         }
     } else {
@@ -411,26 +409,63 @@ size_t smem_bytes() {
 
 }  // namespace
 
-cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, const void *Aop,
-                           const void *Bop, int sms, DevScalars *dev, cudaStream_t s) {
+// Columns [cb, ce) of the trailing matrix (cb a multiple of 64); at most
+// max_ctas persistent CTAs (0: one per SM).
+cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce, ir_dtype tf,
+                           const void *Aop, const void *Bop, int sms, int max_ctas, DevScalars *dev,
+                           cudaStream_t s) {
     const int m = n - (j + nb);
-    if (m <= 0) return cudaSuccess;
+    if (m <= 0 || ce <= cb) return cudaSuccess;
     if (nb != K) return cudaErrorInvalidValue;
+    const int ncols = ce - cb;
+    const size_t esz = (tf == IR_TF32) ? 4 : 2;
+    const void *Bsub = static_cast<const char *>(Bop) + (size_t)(cb - (j + nb)) * K * esz;
     CUtensorMap ta, tb;
-    if (!make_map(&ta, Aop, m, tf) || !make_map(&tb, Bop, m, tf)) return cudaErrorInvalidValue;
+    if (!make_map(&ta, Aop, m, tf) || !make_map(&tb, Bsub, ncols, tf)) return cudaErrorInvalidValue;
     TcParams p;
-    p.C = AF + (int64_t)(j + nb) * ldf + (j + nb);
+    p.C = AF + (int64_t)(j + nb) * ldf + cb;
     p.ldc = ldf;
     p.M = m;
-    p.N = m;
+    p.N = ncols;
     const int tiles_m = (m + BM - 1) / BM;
-    p.tiles_n = (m + BN - 1) / BN;
+    p.tiles_n = (ncols + BN - 1) / BN;
     p.num_tiles = tiles_m * p.tiles_n;
     p.idesc = make_idesc(tf);
     p.timeout = &dev->timeout;
     CUtensorMap tc;
-    if (!make_c_map(&tc, p.C, m, m, ldf)) return cudaErrorInvalidValue;
-    const int grid = p.num_tiles < sms ? p.num_tiles : sms;
+    if (!make_c_map(&tc, p.C, m, ncols, ldf)) return cudaErrorInvalidValue;
+    const bool share = max_ctas > 0;
+    int grid = p.num_tiles < sms ? p.num_tiles : sms;
+    auto launch = [&](auto kern, size_t smem) -> cudaError_t {
+        count_launch();
+        if (!share) {
+            kern<<<grid, kThreads, smem, s>>>(ta, tb, tc, p);
+            return cudaGetLastError();
+        }
+        // share the GPU with a concurrent panel: clusters of 8 CTAs, two
+        // clusters fewer than fit at once, so whole GPC slots stay free
+        cudaLaunchConfig_t cfg = {};
+        cfg.blockDim = dim3(kThreads, 1, 1);
+        cfg.dynamicSmemBytes = smem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 8;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cfg.gridDim = dim3(8 * 32, 1, 1);
+        int maxc = 0;
+        if (cudaOccupancyMaxActiveClusters(&maxc, kern, &cfg) != cudaSuccess) maxc = 0;
+        (void)cudaGetLastError();
+        int clusters = maxc - 2;
+        if (clusters < 1) clusters = 1;
+        const int need = (p.num_tiles + 7) / 8;
+        if (clusters > need) clusters = need;
+        cfg.gridDim = dim3(8 * clusters, 1, 1);
+        return cudaLaunchKernelEx(&cfg, kern, ta, tb, tc, p);
+    };
     if (tf == IR_TF32) {
         static bool attr = false;
         const size_t sm = smem_bytes<2, 1>();
@@ -439,8 +474,7 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtyp
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        count_launch();
-        k_gemm_tc<2, 1><<<grid, kThreads, sm, s>>>(ta, tb, tc, p);
+        return launch(k_gemm_tc<2, 1>, sm);
     } else {
         static bool attr = false;
         const size_t sm = smem_bytes<1, 2>();
@@ -449,10 +483,8 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, ir_dtyp
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        count_launch();
-        k_gemm_tc<1, 2><<<grid, kThreads, sm, s>>>(ta, tb, tc, p);
+        return launch(k_gemm_tc<1, 2>, sm);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace ir

@@ -7,6 +7,7 @@
 // division), a_ij = fmaf(-l_ik, u_kj, a_ij) with k ascending for every
 // element.  Blocking only regroups these chains, so the factors are bitwise
 // those of the unblocked algorithm whenever the trailing update is binary32.
+#include <cfloat>
 #include <climits>
 #include <cstddef>
 #include <cuda_bf16.h>
@@ -20,39 +21,42 @@ namespace {
 constexpr int NB = kPanelNB;
 constexpr int T = kPanelT;
 constexpr int NW = T / 32;
-constexpr int kFetchBatch = 4;   // candidate rows fetched per DSMEM round trip
 
 // Every panel row carries the index of the row it started the panel in
 // ("origin"), so the panel's net permutation is known at the end without
 // replaying the interchanges.
+//
+// Candidate exchange: at step k every CTA pushes one 272-byte record
+// (|a|, position, origin, the 64 row values, pad) into slot [k & 1][its rank]
+// of every CTA of the cluster with st.async, which counts the bytes on the
+// receiver's mbarrier; CTA 0 also pushes the record of row k (slot kDiagSlot).
+// A receiver waits (bounded) on its own mbarrier for all records of the step.
+constexpr int kRec = 68;                     // floats per record
+constexpr int kDiagSlot = kPanelMaxCluster;  // slot of the row-k record
 struct PanelSmem {
     // row arrays first, each 16-byte aligned (they are accessed as float4)
     alignas(16) float stage_row[NW][NB];     // per-warp candidate row
-    alignas(16) float slot_row[2][NB];       // this CTA's candidate, read by the cluster
-    alignas(16) float diag_row[2][NB];       // row k (owned by CTA 0), read by the winner's CTA
-    // every CTA's candidate row, local copies; value i at index i + 3 so that
-    // values 1..64 form 16-byte aligned quadruples (index 67 stays zero)
-    alignas(16) float cand[kPanelMaxCluster][NB + 4];
-    alignas(16) float drow[NB];              // old row k, local copy
+    alignas(16) float diag_row[NB];          // row k, written by its owner (CTA 0)
+    alignas(16) float recv[2][kPanelMaxCluster + 1][kRec];
+    alignas(16) float out[2][2][kRec];       // [parity][candidate, row k] records to send
+    alignas(8) unsigned long long recv_bar[2];
     float stage_val[NW];
     int stage_pos[NW];
     int stage_org[NW];
-    float slot_val[2];
-    int slot_pos[2];
-    int slot_org[2];
-    int diag_org[2];
-    int uorg, dorg;
-    int win_pos, win_cta;
+    int diag_org;
+    float win_r;                 // fl(1/pivot) for the step
+    int win_pos, win_src, uorg, dorg;
     int piv_log[NB];             // p_k of every step (the panel's interchanges)
     int zero_piv;                // first zero pivot of this panel (1-based), or 0
+    int abort_flag;
 };
+static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, diag_row) % 16 == 0 &&
+                  offsetof(PanelSmem, recv) % 16 == 0 && offsetof(PanelSmem, out) % 16 == 0 &&
+                  (kRec * 4) % 16 == 0,
+              "float4 rows of the panel's shared memory must be 16-byte aligned");
 // Dynamic shared memory after PanelSmem: Ls[NB][T] multipliers by step and
 // position, Us[NB][NB] pivot rows (CTA 0).
 constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * T + sizeof(float) * NB * NB + 16;
-static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, slot_row) % 16 == 0 &&
-                  offsetof(PanelSmem, diag_row) % 16 == 0 && offsetof(PanelSmem, cand) % 16 == 0 &&
-                  offsetof(PanelSmem, drow) % 16 == 0,
-              "float4 rows of the panel's shared memory must be 16-byte aligned");
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -78,10 +82,32 @@ __device__ __forceinline__ float ld_dsmem_f32(unsigned addr) {
     asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
     return v;
 }
-__device__ __forceinline__ int ld_dsmem_s32(unsigned addr) {
-    int v;
-    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
-    return v;
+
+// Bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into
+// another CTA's shared memory, counted on that CTA's mbarrier.
+__device__ __forceinline__ void bulk_to_cta(unsigned rdst, unsigned src, unsigned bytes, unsigned rbar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(rdst),
+                 "r"(src), "r"(bytes), "r"(rbar)
+                 : "memory");
+}
+__device__ __forceinline__ void mbar_init_p(unsigned addr, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_arrive(unsigned addr, unsigned bytes) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned addr, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    return ok != 0;
 }
 
 __device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
@@ -131,16 +157,17 @@ __device__ __forceinline__ void store_op_row(void *op, int64_t row, const float 
 // not-yet-eliminated part of its row in a rotating register window: at step k,
 // a[i] holds column j+k+i (zero past the panel), so the current column is
 // always a[0] and the update a[i] <- fmaf(-l, u[i+1], a[i+1]) also shifts the
-// window.  Per column k: warp argmax (redux.sync) -> CTA candidate -> DSMEM
-// exchange across the cluster (one cluster barrier, one round trip) ->
-// interchange of positions k and p -> scale and rank-1 update.
-// The column loop touches no global memory (a release barrier would wait for
-// it): multipliers go to shared memory by step and position, pivot rows and
-// the interchanges to shared memory; at the end every row gathers its
-// multipliers by walking the interchanges backward (DSMEM reads).  The rows
-// whose content moved are listed as (destination, origin) pairs in swap_list
-// (count in swap_list[0]) for the gather of the other columns, and perm is
-// composed with the panel's permutation.
+// window.  Per column k: warp argmax (redux.sync) -> CTA candidate -> records
+// pushed to every CTA (st.async) -> bounded wait on the local mbarrier ->
+// winner picked locally -> interchange of positions k and p -> scaling by the
+// pivot's reciprocal (LAPACK getf2) and rank-1 update.
+// The column loop touches no global memory: multipliers go to shared memory
+// by step and position, pivot rows and the interchanges to shared memory; at
+// the end every row gathers its multipliers by walking the interchanges
+// backward (DSMEM reads).  The rows whose content moved are listed as
+// (destination, origin) pairs in swap_list (count in swap_list[0]) for the
+// gather of the other columns, and perm is composed with the panel's
+// permutation.
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
@@ -153,11 +180,19 @@ __global__ void __launch_bounds__(T, 1)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int gi = j + (int)crank * T + t;           // this thread's row (position)
     const bool valid = gi < n;
+    const unsigned step_bytes = (csize + 1u) * (unsigned)(kRec * 4);
 
     int org = gi;
     if (crank == 0 && t == 0) swap_list[0] = 0;
-    if (t == 0) sm.zero_piv = 0;
-    for (int e = t; e < kPanelMaxCluster * (NB + 4); e += T) (&sm.cand[0][0])[e] = 0.f;
+    if (t == 0) {
+        sm.zero_piv = 0;
+        sm.abort_flag = 0;
+        mbar_init_p(smem_u32(&sm.recv_bar[0]), 1);
+        mbar_init_p(smem_u32(&sm.recv_bar[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_expect_arrive(smem_u32(&sm.recv_bar[0]), step_bytes);
+        if (nbp > 1) mbar_expect_arrive(smem_u32(&sm.recv_bar[1]), step_bytes);
+    }
     float a[NB];
     if (valid) {
         const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)gi * ldf + j);
@@ -173,120 +208,121 @@ __global__ void __launch_bounds__(T, 1)
 #pragma unroll
         for (int c = 0; c < NB; ++c) a[c] = 0.f;
     }
-    cluster_sync_all();   // every CTA of the cluster is running
+    cluster_sync_all();   // every CTA is running and its mbarriers are armed
+    const unsigned long long deadline = globaltimer() + kWaitLimitNs;   // for all waits of this launch
 
-    const unsigned slot_val_addr = smem_u32(&sm.slot_val[0]);
-    const unsigned slot_pos_addr = smem_u32(&sm.slot_pos[0]);
-    const unsigned slot_row_addr = smem_u32(&sm.slot_row[0][0]);
-    const unsigned diag_row_addr = smem_u32(&sm.diag_row[0][0]);
-    const unsigned slot_org_addr = smem_u32(&sm.slot_org[0]);
-    const unsigned diag_org_addr = smem_u32(&sm.diag_org[0]);
+    const unsigned recv_addr = smem_u32(&sm.recv[0][0][0]);
+    const unsigned bar_addr = smem_u32(&sm.recv_bar[0]);
 
 #pragma unroll 1
     for (int k = 0; k < nbp; ++k) {
         const int buf = k & 1;
         const int pk = j + k;   // position being eliminated
-        // 1. local candidate: first maximal |a_ik| over rows i >= pk
+        // 1. local candidate: first maximal |a_ik| over rows i >= pk (rows are
+        //    owned in increasing order, so the lowest lane/warp/CTA wins ties)
         const bool cand = valid && gi >= pk;
-        unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
-        int pos = cand ? gi : INT_MAX;
-        unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-        int pmin = __reduce_min_sync(0xffffffffu, (key == kmax) ? pos : INT_MAX);
-        if (pos == pmin && pmin != INT_MAX) {
+        const unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
+        const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
+        const unsigned tie = __ballot_sync(0xffffffffu, cand && key == kmax);
+        if (tie && lane == __ffs(tie) - 1) {
 #pragma unroll
             for (int c = 0; c < NB; c += 4)
                 *reinterpret_cast<float4 *>(&sm.stage_row[warp][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
             sm.stage_org[warp] = org;
+            sm.stage_val[warp] = __uint_as_float(kmax);
+            sm.stage_pos[warp] = gi;
         }
-        if (lane == 0) { sm.stage_val[warp] = __uint_as_float(kmax); sm.stage_pos[warp] = pmin; }
+        if (lane == 0 && !tie) { sm.stage_val[warp] = 0.f; sm.stage_pos[warp] = INT_MAX; }
         // row k is published by its owner (always CTA 0: positions j..j+NB-1)
         if (valid && gi == pk) {
 #pragma unroll
             for (int c = 0; c < NB; c += 4)
-                *reinterpret_cast<float4 *>(&sm.diag_row[buf][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-            sm.diag_org[buf] = org;
+                *reinterpret_cast<float4 *>(&sm.diag_row[c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+            sm.diag_org = org;
         }
         __syncthreads();
-        // 2. CTA candidate
+        // 2. CTA candidate, pushed to every CTA of the cluster
         if (warp == 0) {
-            unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
-            int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
-            unsigned bk = __reduce_max_sync(0xffffffffu, wk);
-            int bp = __reduce_min_sync(0xffffffffu, (wk == bk) ? wp : INT_MAX);
-            unsigned who = __ballot_sync(0xffffffffu, wp == bp && bp != INT_MAX);
-            int w = who ? __ffs(who) - 1 : 0;
-            for (int c = lane; c < NB; c += 32) sm.slot_row[buf][c] = sm.stage_row[w][c];
+            const unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
+            const int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
+            const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
+            const unsigned who = __ballot_sync(0xffffffffu, wp != INT_MAX && wk == bk);
+            const int w = who ? __ffs(who) - 1 : 0;
+            const int bp = who ? __shfl_sync(0xffffffffu, wp, w) : INT_MAX;
+            // compose the records in local shared memory, then one bulk copy per CTA
+            float *rec = sm.out[buf][0];
+            const float *row = sm.stage_row[w];
+            for (int c = lane; c < NB; c += 32) rec[3 + c] = row[c];
             if (lane == 0) {
-                sm.slot_val[buf] = __uint_as_float(bk);
-                sm.slot_pos[buf] = bp;
-                sm.slot_org[buf] = sm.stage_org[w];
+                rec[0] = __uint_as_float(bk);
+                rec[1] = __int_as_float(bp);
+                rec[2] = __int_as_float(sm.stage_org[w]);
+                rec[kRec - 1] = 0.f;
             }
-        }
-        // 3. exchange
-        cluster_sync_all();
-        // 4. one round trip: every CTA's candidate (header and row) and row k;
-        //    warp w pulls the rows of CTAs kFetchBatch*w .. +kFetchBatch-1,
-        //    warp 0 also the headers and row k, and picks the winner locally
-        if (warp * kFetchBatch < (int)csize) {
-            const int c0 = warp * kFetchBatch;
-            float r0[kFetchBatch], r1[kFetchBatch];
-#pragma unroll
-            for (int c = 0; c < kFetchBatch; ++c) {
-                if (c0 + c < (int)csize) {
-                    const unsigned base = map_cta(slot_row_addr + 4u * NB * buf, (unsigned)(c0 + c));
-                    r0[c] = ld_dsmem_f32(base + 4u * lane);
-                    r1[c] = ld_dsmem_f32(base + 4u * (lane + 32));
-                }
-            }
-            unsigned ck = 0u;
-            int cp = INT_MAX, co = 0;
-            float d0 = 0.f, d1 = 0.f;
-            int dorg = 0;
-            if (warp == 0) {
-                if (lane < (int)csize) {
-                    ck = __float_as_uint(ld_dsmem_f32(map_cta(slot_val_addr + 4u * buf, lane)));
-                    cp = ld_dsmem_s32(map_cta(slot_pos_addr + 4u * buf, lane));
-                    co = ld_dsmem_s32(map_cta(slot_org_addr + 4u * buf, lane));
-                }
-                const unsigned dbase = map_cta(diag_row_addr + 4u * NB * buf, 0u);
-                d0 = ld_dsmem_f32(dbase + 4u * lane);
-                d1 = ld_dsmem_f32(dbase + 4u * (lane + 32));
-                if (lane == 0) dorg = ld_dsmem_s32(map_cta(diag_org_addr + 4u * buf, 0u));
-            }
-#pragma unroll
-            for (int c = 0; c < kFetchBatch; ++c) {
-                if (c0 + c < (int)csize) {
-                    sm.cand[c0 + c][lane + 3] = r0[c];
-                    sm.cand[c0 + c][lane + 35] = r1[c];
-                }
-            }
-            if (warp == 0) {
-                sm.drow[lane] = d0;
-                sm.drow[lane + 32] = d1;
-                unsigned bk = __reduce_max_sync(0xffffffffu, ck);
-                int bp = __reduce_min_sync(0xffffffffu, (ck == bk) ? cp : INT_MAX);
-                unsigned who = __ballot_sync(0xffffffffu, cp == bp && bp != INT_MAX);
-                const int wc = who ? __ffs(who) - 1 : 0;
-                const int worg = __shfl_sync(0xffffffffu, co, wc);
+            if (crank == 0) {
+                float *drec = sm.out[buf][1];
+                for (int c = lane; c < NB; c += 32) drec[3 + c] = sm.diag_row[c];
                 if (lane == 0) {
-                    sm.win_pos = bp;
-                    sm.win_cta = wc;
-                    sm.uorg = worg;
-                    sm.dorg = dorg;
-                    sm.piv_log[k] = bp;
+                    drec[0] = 0.f;
+                    drec[1] = __int_as_float(pk);
+                    drec[2] = __int_as_float(sm.diag_org);
+                    drec[kRec - 1] = 0.f;
                 }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> bulk copy
+            __syncwarp();
+            if (lane < (int)csize) {
+                const unsigned rbar = map_cta(bar_addr + 8u * buf, (unsigned)lane);
+                const unsigned slot = recv_addr + (unsigned)((buf * (kPanelMaxCluster + 1) + (int)crank) * kRec * 4);
+                bulk_to_cta(map_cta(slot, (unsigned)lane), smem_u32(rec), kRec * 4, rbar);
+                if (crank == 0) {
+                    const unsigned dslot = recv_addr + (unsigned)((buf * (kPanelMaxCluster + 1) + kDiagSlot) * kRec * 4);
+                    bulk_to_cta(map_cta(dslot, (unsigned)lane), smem_u32(sm.out[buf][1]), kRec * 4, rbar);
+                }
+            }
+            // 3. wait (bounded) for every record of this step
+            const unsigned par = (unsigned)(k >> 1) & 1u;
+            if (lane == 0 && !sm.abort_flag) {
+                while (!mbar_try_wait_cluster(bar_addr + 8u * buf, par)) {
+                    if (globaltimer() > deadline) {      // give up: report, carry on without waiting
+                        sm.abort_flag = 1;
+                        atomicExch(&dev->timeout, 1);
+                        break;
+                    }
+                }
+            }
+            // re-arm this buffer for step k + 2
+            if (lane == 0 && k + 2 < nbp && !sm.abort_flag) mbar_expect_arrive(bar_addr + 8u * buf, step_bytes);
+            __syncwarp();
+            // 4. the winner, picked locally from the received headers
+            const float *rb = sm.recv[buf][0];
+            const unsigned ck = lane < (int)csize ? __float_as_uint(rb[lane * kRec]) : 0u;
+            const int cp = lane < (int)csize ? __float_as_int(rb[lane * kRec + 1]) : INT_MAX;
+            const unsigned ckmax = __reduce_max_sync(0xffffffffu, ck);
+            const unsigned cwho = __ballot_sync(0xffffffffu, cp != INT_MAX && ck == ckmax);
+            const int wc = cwho ? __ffs(cwho) - 1 : 0;
+            if (lane == 0) {
+                const float *wr = rb + wc * kRec;
+                const float piv = wr[3];
+                sm.win_pos = __float_as_int(wr[1]);
+                sm.win_src = wc;
+                sm.uorg = __float_as_int(wr[2]);
+                sm.dorg = __float_as_int(sm.recv[buf][kDiagSlot][2]);
+                sm.win_r = (piv != 0.f) ? 1.0f / piv : 0.f;
+                sm.piv_log[k] = sm.win_pos;
             }
         }
         __syncthreads();
         const int p = sm.win_pos;
-        const float *u = sm.cand[sm.win_cta];    // u[3 + i] = pivot row, column k + i
+        const float *u = sm.recv[buf][sm.win_src];     // u[3 + i] = pivot row, column k + i
         const float piv = u[3];
         // 5. interchange of positions pk and p; the pivot row is final (kept in Us)
         if (valid && gi == pk) {
             org = sm.uorg;
         } else if (valid && gi == p) {
+            const float *dr = sm.recv[buf][kDiagSlot] + 3;
 #pragma unroll
-            for (int c = 0; c < NB; ++c) a[c] = sm.drow[c];
+            for (int c = 0; c < NB; ++c) a[c] = dr[c];
             org = sm.dorg;
         }
         if (crank == 0 && warp == 1) {
@@ -294,19 +330,23 @@ __global__ void __launch_bounds__(T, 1)
             Us[k * NB + lane + 32] = u[35 + lane];
         }
         if (piv == 0.f && t == 0 && sm.zero_piv == 0) sm.zero_piv = pk + 1;
-        // 6. scale column k, update and shift the window: a[i] <- a[i+1] - l u[i+1]
+        // 6. scale column k (getf2: by the reciprocal, divide below the smallest
+        //    normal), update and shift the live part of the window
         if (valid && gi > pk) {
             float l = a[0];
-            if (piv != 0.f) l = l / piv;
+            if (piv != 0.f) l = (fabsf(piv) >= FLT_MIN) ? l * sm.win_r : l / piv;
             Ls[k * T + t] = l;
             const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
+            const int live = nbp - k;                                        // a[0..live-1] nonzero
 #pragma unroll
             for (int q = 0; q < NB / 4; ++q) {
-                const float4 w = us[q];
-                a[4 * q + 0] = fmaf(-l, w.x, a[4 * q + 1]);
-                a[4 * q + 1] = fmaf(-l, w.y, a[4 * q + 2]);
-                a[4 * q + 2] = fmaf(-l, w.z, a[4 * q + 3]);
-                a[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l, w.w, a[4 * q + 4]) : 0.f;
+                if (4 * q < live) {
+                    const float4 w = us[q];
+                    a[4 * q + 0] = fmaf(-l, w.x, a[4 * q + 1]);
+                    a[4 * q + 1] = fmaf(-l, w.y, a[4 * q + 2]);
+                    a[4 * q + 2] = fmaf(-l, w.z, a[4 * q + 3]);
+                    a[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l, w.w, a[4 * q + 4]) : 0.f;
+                }
             }
         }
     }
@@ -365,11 +405,11 @@ __global__ void __launch_bounds__(T, 1)
     cluster_sync_all();   // no CTA leaves while its shared memory may be read
 }
 
-// Apply the panel's row permutation to the columns outside the panel:
+// Apply the panel's row permutation to the columns [c0a, c1a) and [c0b, c1b):
 // A[dst][c] = A[src][c] for the (dst, src) pairs the panel listed.  All
 // sources of a column are read before any destination is written.
 constexpr int kLaswpT = 64;   // 2*NB*kLaswpT floats of staging stay under 48 KB
-__global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int n, int j, int nbp,
+__global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b,
                                                   const int32_t *swap_list) {
     __shared__ int sd[2 * NB], ss[2 * NB];
     __shared__ float vals[2 * NB][kLaswpT];
@@ -380,9 +420,9 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int n
     }
     __syncthreads();
     int c = blockIdx.x * blockDim.x + threadIdx.x;
-    int ncols = n - nbp;
-    if (c >= ncols || cnt == 0) return;
-    if (c >= j) c += nbp;     // skip the panel's own columns
+    const int na = c1a - c0a;
+    if (c >= na + (c1b - c0b) || cnt == 0) return;
+    c = (c < na) ? c0a + c : c0b + (c - na);
     for (int e = 0; e < cnt; ++e) vals[e][threadIdx.x] = AF[(int64_t)ss[e] * ldf + c];
     for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
 }
@@ -391,7 +431,7 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int n
 // thread per column, its NB values in registers, L11 in shared memory; each
 // u_kc is the fmaf chain over m < k in ascending order.  For tensor-core
 // updates the rounded values rTF(u_mc) are also written to Bop (row c).
-__global__ void __launch_bounds__(128) k_trsm(float *AF, int64_t ldf, int n, int j, ir_dtype tf,
+__global__ void __launch_bounds__(128) k_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
                                               void *Bop) {
     __shared__ float L[NB][NB + 1];
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
@@ -399,8 +439,8 @@ __global__ void __launch_bounds__(128) k_trsm(float *AF, int64_t ldf, int n, int
         L[r][m] = AF[(int64_t)(j + r) * ldf + j + m];
     }
     __syncthreads();
-    const int c = j + NB + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= n) return;
+    const int c = cb + blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ce) return;
     float u[NB];
 #pragma unroll
     for (int m = 0; m < NB; ++m) u[m] = AF[(int64_t)(j + m) * ldf + c];
@@ -451,21 +491,21 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
                               has_trailing);
 }
 
-cudaError_t launch_laswp(float *AF, int64_t ldf, int n, int j, int nbp, const int32_t *swap_list,
+cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b, const int32_t *swap_list,
                          cudaStream_t s) {
-    int ncols = n - nbp;
+    const int ncols = (c1a - c0a) + (c1b - c0b);
     if (ncols <= 0) return cudaSuccess;
     count_launch();
-    k_laswp<<<(ncols + kLaswpT - 1) / kLaswpT, kLaswpT, 0, s>>>(AF, ldf, n, j, nbp, swap_list);
+    k_laswp<<<(ncols + kLaswpT - 1) / kLaswpT, kLaswpT, 0, s>>>(AF, ldf, c0a, c1a, c0b, c1b, swap_list);
     return cudaGetLastError();
 }
 
-cudaError_t launch_trsm(float *AF, int64_t ldf, int n, int j, int nb, ir_dtype tf, void *Bop,
-                        cudaStream_t s) {
-    int ncols = n - (j + nb);
+// U12 for the columns [cb, ce) of the block row j..j+NB.
+cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop, cudaStream_t s) {
+    const int ncols = ce - cb;
     if (ncols <= 0) return cudaSuccess;
     count_launch();
-    k_trsm<<<(ncols + 127) / 128, 128, 0, s>>>(AF, ldf, n, j, tf, tf == IR_F32 ? nullptr : Bop);
+    k_trsm<<<(ncols + 127) / 128, 128, 0, s>>>(AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
     return cudaGetLastError();
 }
 

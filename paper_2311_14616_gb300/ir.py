@@ -51,6 +51,16 @@ class _Report(ctypes.Structure):
                 ("info", ctypes.c_int64), ("scale", ctypes.c_double)]
 
 
+class BatchResult(ctypes.Structure):
+    """ir_batch_result (one per system of a batch)."""
+    _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("info", ctypes.c_int64),
+                ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32), ("rnorm", ctypes.c_double),
+                ("scale", ctypes.c_double)]
+
+
+BATCH_MAX_N = 512
+
+
 @dataclass
 class Report:
     iters: int
@@ -85,6 +95,10 @@ def lib():
             "ir_solve_host": (i32, [vp, i64, vp, i64, vp, vp, P(Opts), P(Term), vp, P(_Report)]),
             "ir_lu_solve": (i32, [vp, vp, vp, vp]),
             "ir_residual": (i32, [vp, i64, i32, vp, i64, vp, vp, vp, vp, vp]),
+            "ir_batch_create": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), P(vp)]),
+            "ir_batch_run": (i32, [vp, vp, vp]),
+            "ir_batch_destroy": (None, [vp]),
+            "ir_factor_solve_batched": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), vp, vp]),
             "ir_fact_pivots": (i32, [vp, vp]),
             "ir_fact_factors": (i32, [vp, vp, i64]),
             "ir_fact_info": (i32, [vp, P(i64), P(i32)]),
@@ -217,6 +231,96 @@ class Context:
                                    ctypes.byref(opts), ctypes.byref(t), _stream_ptr(stream),
                                    ctypes.byref(rep)))
         return x, _report(rep)
+
+
+    def batch(self, As, bs, xs=None, tf="f16", term: Optional[Term] = None, fp16_scale: bool = True):
+        """Plan a batch of independent systems (ir_batch_create); see Batch."""
+        return Batch(self, As, bs, xs, tf, term, fp16_scale)
+
+    def solve_batched(self, As, bs, tf="f16", term: Optional[Term] = None, fp16_scale: bool = True,
+                      stream=None):
+        """One-shot batch (ir_factor_solve_batched): returns (xs, results)."""
+        b = Batch(self, As, bs, None, tf, term, fp16_scale, plan=False)
+        code = lib().ir_factor_solve_batched(self._h, b.count, b._n_arr, b._A_arr, b._lda_arr, b._b_arr,
+                                             b._x_arr, ctypes.byref(b.opts), ctypes.byref(b.term),
+                                             _stream_ptr(stream), ctypes.c_void_p(b.results_dev.data_ptr()))
+        _check(code)
+        return b.xs, b.results()
+
+
+def _ptr_array(ts):
+    arr = (ctypes.c_void_p * max(len(ts), 1))()
+    for i, t in enumerate(ts):
+        arr[i] = t.data_ptr() if t.numel() else None
+    return arr
+
+
+class Batch:
+    """ir_batch: many independent systems solved by one persistent launch.
+
+    As: list of square device tensors (TW = float64 or float32, all the same
+    dtype, n_i <= 512); bs: right-hand sides; xs: solution buffers (allocated
+    when None).  The plan borrows all of them.  run() enqueues the batch on a
+    stream (no host synchronisation, capturable in a CUDA graph);
+    results() reads the per-system outcomes after the stream has finished.
+    """
+
+    def __init__(self, ctx: Context, As, bs, xs=None, tf="f16", term: Optional[Term] = None,
+                 fp16_scale: bool = True, plan: bool = True):
+        if len(As) != len(bs) or (xs is not None and len(xs) != len(As)):
+            raise ValueError("As, bs and xs must have the same length")
+        self.ctx, self.count = ctx, len(As)
+        cols = [as_colmajor(A) for A in As]
+        self.As = [c[0] for c in cols]
+        tws = {_tw_code(A) for A in self.As}
+        if len(tws) > 1:
+            raise TypeError("all matrices of a batch need the same working precision")
+        tw = tws.pop() if tws else F64
+        dt = torch.float64 if tw == F64 else torch.float32
+        dev = self.As[0].device if self.As else torch.device("cuda", ctx.device)
+        self.bs = [b.to(device=dev, dtype=dt).contiguous() for b in bs]
+        self.xs = list(xs) if xs is not None else [torch.empty_like(b) for b in self.bs]
+        self.ns = [A.shape[0] for A in self.As]
+        tfc = DTYPES[tf] if isinstance(tf, str) else int(tf)
+        self.opts = make_opts(tw, tfc, fp16_scale)
+        self.term = term if term is not None else default_term()
+        self._n_arr = (ctypes.c_int64 * max(self.count, 1))(*self.ns)
+        self._lda_arr = (ctypes.c_int64 * max(self.count, 1))(*[c[1] for c in cols])
+        self._A_arr = _ptr_array(self.As)
+        self._b_arr = _ptr_array(self.bs)
+        self._x_arr = _ptr_array(self.xs)
+        nbytes = ctypes.sizeof(BatchResult) * max(self.count, 1)
+        self.results_dev = torch.zeros(nbytes, dtype=torch.uint8, device=dev)
+        self._h = ctypes.c_void_p()
+        if plan:
+            _check(lib().ir_batch_create(ctx._h, self.count, self._n_arr, self._A_arr, self._lda_arr,
+                                         self._b_arr, self._x_arr, ctypes.byref(self.opts),
+                                         ctypes.byref(self.term), ctypes.byref(self._h)))
+
+    def run(self, stream=None):
+        _check(lib().ir_batch_run(self._h, ctypes.c_void_p(self.results_dev.data_ptr()), _stream_ptr(stream)))
+
+    def results(self):
+        """Per-system outcomes as a list of dicts (synchronises the device)."""
+        raw = bytes(self.results_dev.cpu().numpy().tobytes())
+        arr = (BatchResult * max(self.count, 1)).from_buffer_copy(raw)
+        out = []
+        for i in range(self.count):
+            r = arr[i]
+            out.append({"status": STATUS.get(r.status, str(r.status)), "iters": r.iters, "info": r.info,
+                        "nonfinite": bool(r.nonfinite), "rnorm": r.rnorm, "scale": r.scale})
+        return out
+
+    def destroy(self):
+        if self._h:
+            lib().ir_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
 
 
 class Factorization:

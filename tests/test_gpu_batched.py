@@ -1,0 +1,214 @@
+"""Batched driver (one persistent launch over many uneven systems) against the oracle.
+
+* TF = binary32: every step of the batch kernel takes the oracle's rounding
+  decisions (fmaf chains in the unblocked LU's order, LAPACK getf2 reciprocal
+  scaling, the reference trsv order of the solves, the residual's fma chain),
+  so iterates, statuses, iteration counts and residual norms are bitwise the
+  oracle's ir_solve results, for TW = binary64 and for TW = binary32 (where
+  TR is wider and eq. (wilkterm) decides).
+* TF = binary16 / bfloat16 / TF32: the trailing update sums in binary32 where
+  the oracle sums exactly, so the factors differ by rounding; converged
+  solutions must agree with the oracle's within the parity tolerance, and
+  every reported residual norm must equal, bitwise, the oracle's binary64
+  residual of the returned iterate.
+* The full-size workload (2000 systems, N uniform in [32, 512]) is checked on
+  a sample of systems against the oracle and on all systems by the residual
+  property; runs replayed from a CUDA graph equal direct runs.
+"""
+import numpy as np
+import pytest
+import torch
+
+import irgen
+import oracle as O
+from gpu_util import dev_colmajor, dev_vec
+from paper_2311_14616_gb300 import ir
+
+pytestmark = pytest.mark.gpu
+
+STATUS = {O.CONVERGED: "converged", O.STAGNATED: "stagnated", O.MAXIT: "maxit",
+          O.DIVERGED: "diverged", O.FAILED: "failed"}
+TF = {"f32": O.F32, "tf32": O.TF32, "bf16": O.BF16, "f16": O.F16}
+EDGE_SIZES = [0, 1, 2, 3, 31, 63, 64, 65, 100, 127, 128, 129, 255, 300, 447, 511, 512]
+
+
+def _upload(As, bs, dtype=np.float64):
+    return ([dev_colmajor(np.asfortranarray(A.astype(dtype))) for A in As],
+            [dev_vec(b.astype(dtype)) for b in bs])
+
+
+def _run(ctx, As, bs, tf, dtype=np.float64, term=None):
+    Ad, bd = _upload(As, bs, dtype)
+    plan = ctx.batch(Ad, bd, tf=tf, term=term)
+    plan.run()
+    torch.cuda.synchronize()
+    res = plan.results()
+    xs = [x.cpu().numpy() for x in plan.xs]
+    plan.destroy()
+    return xs, res
+
+
+def _clearly_converged(o):
+    """The oracle converged with every residual ratio well below Rmax."""
+    h = o.rhist
+    return o.status == O.CONVERGED and all(h[k + 1] < 0.25 * h[k] for k in range(len(h) - 2))
+
+
+def _rnorm_of(A, b, x):
+    r = O.residual(A, b.astype(np.float64), x.astype(np.float64))
+    if not r.size:
+        return 0.0
+    return float("nan") if np.isnan(r).any() else float(np.max(np.abs(r)))
+
+
+def _same(a, b):
+    return a == b or (np.isnan(a) and np.isnan(b))
+
+
+@pytest.mark.parametrize("tw", [np.float64, np.float32])
+def test_batch_f32_bitwise_equals_oracle(ctx, tw):
+    _, As, bs = irgen.case_batch_sizes(EDGE_SIZES, 4100)
+    As = [np.asfortranarray(A.astype(tw)) for A in As]
+    bs = [b.astype(tw) for b in bs]
+    xs, res = _run(ctx, As, bs, "f32", tw)
+    for A, b, x, r in zip(As, bs, xs, res):
+        n = A.shape[0]
+        if n == 0:
+            assert r["status"] == "converged" and r["iters"] == 0
+            continue
+        o = O.ir_solve(A, b, O.F32, nb=64)
+        assert r["info"] == o.info == 0
+        assert r["status"] == STATUS[o.status], (n, r, o.status)
+        assert r["iters"] == len(o.rhist) - 1, n
+        assert np.array_equal(x.view(np.uint8), o.sol.view(np.uint8)), n
+        assert r["rnorm"] == o.rhist[-1], n
+
+
+@pytest.mark.parametrize("tf", ["f16", "bf16", "tf32"])
+def test_batch_low_precision_vs_oracle(ctx, tf):
+    ns = [32, 47, 64, 65, 96, 130, 192, 257, 320, 384, 449, 512]
+    alphas, As, bs = irgen.case_batch_sizes(ns, 4200 + len(tf))
+    xs, res = _run(ctx, As, bs, tf)
+    for A, b, x, r, alpha in zip(As, bs, xs, res, alphas):
+        n = A.shape[0]
+        o = O.ir_solve(A, b, TF[tf], nb=64)
+        if tf == "f16":
+            assert r["scale"] == 1024.0 / np.max(np.abs(A))
+        assert r["status"] != "failed" and not r["nonfinite"]
+        # the reported norm is the binary64 residual of the returned iterate, bit for bit
+        assert _same(r["rnorm"], _rnorm_of(A, b, x)), n
+        if _clearly_converged(o):
+            assert r["status"] == "converged", (n, alpha, r, o.rhist)
+            kappa = O.cond_inf(A)
+            tol = O.parity_tol(kappa, O.F64)
+            assert np.max(np.abs(x - o.sol)) <= tol * np.max(np.abs(o.sol)), (n, alpha)
+            xr = O.reference_solution(A, b)
+            assert O.rel_err_inf(x, xr) <= tol, (n, alpha)
+        elif r["status"] == "converged":
+            # converged where the oracle did not: the residual test itself must hold
+            assert r["rnorm"] <= 2.0 ** -52 * np.max(np.abs(b))
+
+
+def test_batch_edge_sizes_low_precision(ctx):
+    _, As, bs = irgen.case_batch_sizes(EDGE_SIZES, 4300)
+    xs, res = _run(ctx, As, bs, "bf16")
+    for A, b, x, r in zip(As, bs, xs, res):
+        if A.shape[0] == 0:
+            assert r["status"] == "converged" and r["iters"] == 0
+            continue
+        assert r["status"] != "failed"
+        assert _same(r["rnorm"], _rnorm_of(A, b, x))
+
+
+def test_batch_failures_are_per_system(ctx):
+    _, As, bs = irgen.case_batch_sizes([40, 70, 90, 33], 4400)
+    As[1] = np.zeros((70, 70), order="F")                 # zero pivot at step 1
+    As[2] = As[2].copy(order="F")
+    As[2][5, 7] = np.nan                                  # non-finite input
+    bs[3] = bs[3].copy()
+    bs[3][0] = np.inf
+    xs, res = _run(ctx, As, bs, "f16")
+    # the healthy systems are solved as if alone
+    for i in (0,):
+        assert res[i]["status"] != "failed"
+        assert _same(res[i]["rnorm"], _rnorm_of(As[i], bs[i], xs[i]))
+        o = O.ir_solve(As[i], bs[i], O.F16, nb=64)
+        if _clearly_converged(o):
+            assert res[i]["status"] == "converged"
+    assert res[1]["status"] == "failed" and res[1]["info"] == 1 and not res[1]["nonfinite"]
+    assert res[2]["status"] == "failed" and res[2]["nonfinite"]
+    assert res[3]["status"] == "failed" and res[3]["nonfinite"]
+
+
+def test_batch_rejects_bad_arguments(ctx):
+    A = dev_colmajor(np.eye(513))
+    b = dev_vec(np.ones(513))
+    with pytest.raises(ir.IRError) as e:
+        ctx.batch([A], [b], tf="f16")
+    assert e.value.code == 7                                # IR_EUNSUPPORTED
+    with pytest.raises(ir.IRError) as e:
+        ctx.batch([dev_colmajor(np.eye(4))], [dev_vec(np.ones(4))], tf="f64")
+    assert e.value.code == 1                                # IR_EINVAL: TF = binary64
+
+
+def test_empty_batch(ctx):
+    plan = ctx.batch([], [], tf="f16")
+    plan.run()
+    assert plan.results() == []
+
+
+@pytest.fixture(scope="module")
+def full_batch():
+    ns, alphas, As, bs = irgen.case_batch(2000, 1005)
+    return ns, alphas, As, bs
+
+
+@pytest.mark.parametrize("tf", ["f16", "bf16"])
+def test_full_batch_2000_systems(ctx, full_batch, tf):
+    ns, alphas, As, bs = full_batch
+    Ad, bd = _upload(As, bs)
+    plan = ctx.batch(Ad, bd, tf=tf)
+    plan.run()
+    torch.cuda.synchronize()
+    res = plan.results()
+    xs = [x.cpu().numpy() for x in plan.xs]
+    # every system: the reported norm is the binary64 residual of the returned iterate
+    for A, b, x, r in zip(As, bs, xs, res):
+        assert r["status"] != "failed"
+        assert _same(r["rnorm"], _rnorm_of(A, b, x))
+        if r["status"] == "converged":
+            assert r["rnorm"] <= 2.0 ** -52 * np.max(np.abs(b))
+    # a sample against the oracle's own IR
+    g = np.random.Generator(np.random.PCG64(77))
+    for i in g.choice(len(ns), size=12, replace=False):
+        o = O.ir_solve(As[i], bs[i], TF[tf], nb=64)
+        if _clearly_converged(o):
+            assert res[i]["status"] == "converged", (i, ns[i], alphas[i])
+            tol = O.parity_tol(O.cond_inf(As[i]), O.F64)
+            assert np.max(np.abs(xs[i] - o.sol)) <= tol * np.max(np.abs(o.sol))
+    # a replay from a CUDA graph gives the same bits
+    first = [x.clone() for x in plan.xs]
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run()
+    for x in plan.xs:
+        x.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, b in zip(first, plan.xs):
+        assert torch.equal(a, b)
+    assert plan.results() == res
+    plan.destroy()
+
+
+def test_one_shot_entry_point_matches_plan(ctx):
+    _, As, bs = irgen.case_batch_sizes([77, 300, 129], 4500)
+    Ad, bd = _upload(As, bs)
+    xs, res = ctx.solve_batched(Ad, bd, tf="f16")
+    xs2, res2 = _run(ctx, As, bs, "f16")
+    assert res == res2
+    for a, b in zip(xs, xs2):
+        assert np.array_equal(a.cpu().numpy(), b)
