@@ -191,7 +191,7 @@ typedef struct {
     int32_t iters;       /* residual computations */
     int64_t info;        /* first zero pivot (1-based) or 0 */
     int32_t nonfinite;   /* 1: NaN/Inf in A or b, or overflow of the rounded copy */
-    int32_t pad;
+    int32_t timeout;     /* 1: a bounded device-side wait gave up (status IR_FAILED) */
     double rnorm;        /* ||r||_inf after the last residual (||b|| when none ran) */
     double scale;        /* s of the rounded copy */
 } ir_batch_result;

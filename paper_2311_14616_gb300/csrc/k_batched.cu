@@ -15,10 +15,15 @@
 //                 candidate row; every warp then picks the winner)
 //   interchanges  gather of the moved rows for the columns outside the panel
 //   U12           L11^{-1} A12 by fmaf chains (binary32, ascending k)
-//   update        two groups of 256 threads, 64x64 tiles, 4x4 per thread;
-//                 TF = binary32: the fmaf chain from C (so the factors are
-//                 bitwise those of the unblocked LU); other TF: C - sum_k
-//                 rTF(l) rTF(u), sum in binary32 (as the tensor-core update)
+//   update        binary16 / bfloat16 factors: tcgen05.mma on the tensor
+//                 cores (operands rounded to TF while staged in shared
+//                 memory, binary32 accumulation in tensor memory, C -= D in
+//                 the epilogue), 128x128 tiles, four per wave;
+//                 binary32 / TF32 factors (and trailing blocks of <= 64
+//                 rows): two groups of 256 threads, 64x64 tiles, 4x4 per
+//                 thread; TF = binary32 runs the fmaf chain from C (so the
+//                 factors are bitwise those of the unblocked LU), TF32 sums
+//                 rTF(l) rTF(u) in binary32 and subtracts the sum
 //   solves        the reference-BLAS trsv order (forward: columns ascending;
 //                 back: columns descending, the division first), blocked by
 //                 32 columns: one warp solves the diagonal block with
@@ -31,6 +36,7 @@
 #include <cuda_fp16.h>
 
 #include "ir_internal.cuh"
+#include "tc_util.cuh"
 
 namespace ir {
 namespace {
@@ -60,15 +66,19 @@ struct BSmem {
     int moved_cnt;
     int moved_dst[2 * NB], moved_src[2 * NB];
     unsigned long long red[BW];
-    int info, nonfinite, cur;
+    unsigned long long mma_bar;               // tensor-core completion (tcgen05.commit)
+    unsigned tmem_base;
+    int info, nonfinite, cur, abort;
 };
 static_assert(offsetof(BSmem, stage) % 16 == 0 && offsetof(BSmem, drow) % 16 == 0 && (kRow * 4) % 16 == 0,
               "staged rows must be 16-byte aligned");
-constexpr size_t kBigFloats = (size_t)NB * BT;      // 128 KB of multi-use scratch
-constexpr size_t kBatchSmem = (sizeof(BSmem) + 15) / 16 * 16 + (kBigFloats + NB * NB) * sizeof(float);
+constexpr size_t kBigFloats = (size_t)NB * BT;      // 128 KB of multi-use scratch, 1024-byte aligned
+constexpr size_t kBatchSmem = 1024 + (kBigFloats + NB * NB) * sizeof(float) + sizeof(BSmem);
+constexpr unsigned kTmemCols = 512;                 // four 128x128 binary32 accumulators
 static_assert(kBatchSmem <= 227 * 1024, "shared memory per CTA");
 static_assert(4 * NB * kLd <= (int)kBigFloats, "update tiles of both groups fit the scratch");
 static_assert(2 * NB * 256 <= (int)kBigFloats, "interchange staging fits the scratch");
+static_assert(2 * 512 * 128 <= (int)kBigFloats * 4, "both 16-bit operands (512 rows x 128 bytes) fit the scratch");
 
 struct BatchSys {
     const void *A;
@@ -403,6 +413,126 @@ __device__ void b_update(float *W, int n, int ldw, int j0, ir_dtype tf, float *s
 // block J - 1 (as every warp below does), then solves its diagonal block one
 // column at a time with shuffles and publishes the 32 values; the row entries
 // of the next block are loaded before the barrier so the wait hides them.
+// Eight binary32 values rounded to TF (binary16 or bfloat16, nearest even) and
+// packed as one 16-byte chunk, element 0 in the lowest half-word.
+__device__ __forceinline__ uint4 pack8(const float *v, ir_dtype tf) {
+    unsigned w[4];
+#pragma unroll
+    for (int h = 0; h < 4; ++h) {
+        if (tf == IR_BF16) {
+            const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * h], v[2 * h + 1]);
+            w[h] = *reinterpret_cast<const unsigned *>(&p);
+        } else {
+            const __half2 p = __floats2half2_rn(v[2 * h], v[2 * h + 1]);
+            w[h] = *reinterpret_cast<const unsigned *>(&p);
+        }
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// Bounded wait on an mbarrier phase (globaltimer limit); false when it gave up.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned addr, unsigned parity) {
+    if (mbar_try_wait(addr, parity)) return true;
+    const unsigned long long t0 = globaltimer();
+    while (!mbar_try_wait(addr, parity))
+        if (globaltimer() - t0 > kWaitLimitNs) return false;
+    return true;
+}
+
+// A22 -= rTF(L21) rTF(U12) on the tensor cores (TF = binary16 or bfloat16).
+// Thread t stages row t of both operands: L21 row t and U12 column t, each
+// 64 K values rounded to TF = 128 bytes, written K-major in the 128-byte
+// swizzle (16-byte chunk q of row r at chunk q ^ (r & 7) of the row; eight
+// rows make one 1024-byte atom), rows past the trailing block zero.  Output
+// tiles of 128 x 128, four per wave in the 512 TMEM columns; one thread issues
+// the 4 MMAs (K = 16 each) per tile and commits them to an mbarrier; then warp
+// w reads TMEM lanes 32 (w % 4) .. + 31 of tile w / 4 and subtracts D from C.
+// Returns false if a bounded wait gave up (the caller abandons the system).
+__device__ bool b_update_tc(float *W, int n, int ldw, int j0, ir_dtype tf, unsigned char *big, BSmem &sm,
+                            unsigned &mph) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int r0 = j0 + NB, m = n - r0;
+    const int tiles = (m + 127) >> 7, pad = tiles << 7;
+    unsigned char *gA = big, *gB = big + 64 * 1024;
+    if (t < pad) {
+        uint4 ca[8], cb[8];
+        if (t < m) {
+            const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)(r0 + t) * ldw + j0);
+            float u[NB];
+#pragma unroll
+            for (int k = 0; k < NB; ++k) u[k] = W[(int64_t)(j0 + k) * ldw + r0 + t];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float4 x = src[2 * q], y = src[2 * q + 1];
+                const float v[8] = {x.x, x.y, x.z, x.w, y.x, y.y, y.z, y.w};
+                ca[q] = pack8(v, tf);
+                cb[q] = pack8(u + 8 * q, tf);
+            }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) ca[q] = cb[q] = make_uint4(0u, 0u, 0u, 0u);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            *reinterpret_cast<uint4 *>(gA + t * 128 + ((q ^ (t & 7)) << 4)) = ca[q];
+            *reinterpret_cast<uint4 *>(gB + t * 128 + ((q ^ (t & 7)) << 4)) = cb[q];
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> MMA operand reads
+    __syncthreads();
+    const unsigned sA = smem_u32(gA), sB = smem_u32(gB), bar = smem_u32(&sm.mma_bar);
+    const unsigned fmt = (tf == IR_BF16) ? 1u : 0u;
+    const unsigned idesc = (1u << 4) | (fmt << 7) | (fmt << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+    const int ntile = tiles * tiles;
+    for (int w0 = 0; w0 < ntile; w0 += 4) {
+        const int nw = (ntile - w0 < 4) ? ntile - w0 : 4;
+        if (t == 0) {
+            tc_fence_after();
+            for (int a = 0; a < nw; ++a) {
+                const int ti = (w0 + a) / tiles, tj = (w0 + a) % tiles;
+#pragma unroll
+                for (int kk = 0; kk < NB / 16; ++kk)
+                    mma<false>(sm.tmem_base + (unsigned)(a * 128), make_desc(sA + ti * 16384 + kk * 32),
+                               make_desc(sB + tj * 16384 + kk * 32), idesc, kk);
+            }
+            mma_commit(bar);
+        }
+        const bool ok = mbar_wait_bounded(bar, mph);
+        mph ^= 1u;
+        if (!__syncthreads_and(ok)) return false;
+        tc_fence_after();
+        const int a = warp >> 2, quarter = warp & 3;
+        if (a < nw) {
+            const int ti = (w0 + a) / tiles, tj = (w0 + a) % tiles;
+            const int i = ti * 128 + quarter * 32 + lane;
+#pragma unroll 1
+            for (int h = 0; h < 4; ++h) {
+                float v[32];
+                tmem_ld32(sm.tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(a * 128 + h * 32), v);
+                const int c0 = tj * 128 + h * 32;
+                if (i < m) {
+                    // 16-byte groups that start inside the block end inside the padded row
+                    float4 *cp = reinterpret_cast<float4 *>(W + (int64_t)(r0 + i) * ldw + r0 + c0);
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        if (c0 + 4 * q < m) {
+                            float4 c = cp[q];
+                            c.x -= v[4 * q];
+                            c.y -= v[4 * q + 1];
+                            c.z -= v[4 * q + 2];
+                            c.w -= v[4 * q + 3];
+                            cp[q] = c;
+                        }
+                    }
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    return true;
+}
+
 __device__ __forceinline__ void load_block(const float4 *row4, int c0, int n, bool on, float (&dst)[32]) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -482,7 +612,7 @@ __device__ float b_upper(const float *W, int n, int ldw, float vi, BSmem &sm) {
 
 template <typename TW>
 __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_batch_result *res, BSmem &sm,
-                         float *big, float *Us) {
+                         float *big, float *Us, bool use_tc, unsigned &mph) {
     const int t = threadIdx.x;
     const int n = S.n;
     const ir_dtype tf = cfg.tf;
@@ -495,7 +625,7 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
             res->iters = 0;
             res->info = 0;
             res->nonfinite = 0;
-            res->pad = 0;
+            res->timeout = 0;
             res->rnorm = 0.0;
             res->scale = 1.0;
         }
@@ -595,7 +725,24 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
         b_laswp(W, n, ldw, j0, nbp, sm, big);
         if (j0 + nbp < n) {
             b_trsm(W, n, ldw, j0, big);
-            b_update(W, n, ldw, j0, tf, big);
+            if (use_tc && n - j0 - NB > NB) {
+                if (!b_update_tc(W, n, ldw, j0, tf, reinterpret_cast<unsigned char *>(big), sm, mph)) {
+                    if (t == 0) {
+                        sm.abort = 1;
+                        res->status = IR_FAILED;
+                        res->iters = 0;
+                        res->info = 0;
+                        res->nonfinite = 0;
+                        res->timeout = 1;
+                        res->rnorm = 0.0;
+                        res->scale = 1.0;
+                    }
+                    __syncthreads();
+                    return;
+                }
+            } else {
+                b_update(W, n, ldw, j0, tf, big);
+            }
         }
     }
     // x = 0, r = b, rhist[0] = ||b||
@@ -685,7 +832,7 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
         res->iters = k;
         res->info = info;
         res->nonfinite = nonfinite;
-        res->pad = 0;
+        res->timeout = 0;
         res->rnorm = rprev;
         res->scale = s;
     }
@@ -696,22 +843,55 @@ __global__ void __launch_bounds__(BT, 1)
     k_batched(const BatchSys *sys, const int *order, unsigned *ticket, float *ws, int64_t ws_stride, BatchCfg cfg,
               ir_batch_result *results) {
     extern __shared__ __align__(16) unsigned char bsm[];
-    BSmem &sm = *reinterpret_cast<BSmem *>(bsm);
-    float *big = reinterpret_cast<float *>(bsm + (sizeof(BSmem) + 15) / 16 * 16);
+    const unsigned s0 = smem_u32(bsm);
+    unsigned char *base = bsm + (((s0 + 1023u) & ~1023u) - s0);
+    float *big = reinterpret_cast<float *>(base);                   // 1024-byte aligned
     float *Us = big + kBigFloats;
+    BSmem &sm = *reinterpret_cast<BSmem *>(Us + NB * NB);
     float *W = ws + (int64_t)blockIdx.x * ws_stride;
+    const bool use_tc = (cfg.tf == IR_F16 || cfg.tf == IR_BF16);
+    if (threadIdx.x == 0) {
+        sm.abort = 0;
+        mbar_init(smem_u32(&sm.mma_bar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (use_tc && threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&sm.tmem_base)),
+                     "r"(kTmemCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    unsigned mph = 0;
     for (;;) {
         if (threadIdx.x == 0) sm.cur = (int)atomicAdd(ticket, 1u);
         __syncthreads();
         const int idx = sm.cur;
+        const int abort = sm.abort;
         __syncthreads();
-        if (idx >= cfg.count) break;
+        if (idx >= cfg.count || abort) break;
         const int id = order[idx];
         const BatchSys S = sys[id];
         if (cfg.tw == IR_F64)
-            b_system<double>(S, W, cfg, results + id, sm, big, Us);
+            b_system<double>(S, W, cfg, results + id, sm, big, Us, use_tc, mph);
         else
-            b_system<float>(S, W, cfg, results + id, sm, big, Us);
+            b_system<float>(S, W, cfg, results + id, sm, big, Us, use_tc, mph);
+    }
+    if (use_tc) {
+        if (sm.abort) {
+            // a wait gave up: let the tensor core finish what was issued (bounded) before freeing TMEM
+            if (threadIdx.x == 0) mma_commit(smem_u32(&sm.mma_bar));
+            mbar_wait_bounded(smem_u32(&sm.mma_bar), mph);
+        }
+        tc_fence_before();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            tc_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(sm.tmem_base), "r"(kTmemCols)
+                         : "memory");
+        }
     }
 }
 

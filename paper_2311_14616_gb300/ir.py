@@ -54,7 +54,7 @@ class _Report(ctypes.Structure):
 class BatchResult(ctypes.Structure):
     """ir_batch_result (one per system of a batch)."""
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("info", ctypes.c_int64),
-                ("nonfinite", ctypes.c_int32), ("pad", ctypes.c_int32), ("rnorm", ctypes.c_double),
+                ("nonfinite", ctypes.c_int32), ("timeout", ctypes.c_int32), ("rnorm", ctypes.c_double),
                 ("scale", ctypes.c_double)]
 
 
@@ -308,7 +308,8 @@ class Batch:
         for i in range(self.count):
             r = arr[i]
             out.append({"status": STATUS.get(r.status, str(r.status)), "iters": r.iters, "info": r.info,
-                        "nonfinite": bool(r.nonfinite), "rnorm": r.rnorm, "scale": r.scale})
+                        "nonfinite": bool(r.nonfinite), "timeout": bool(r.timeout), "rnorm": r.rnorm,
+                        "scale": r.scale})
         return out
 
     def destroy(self):
