@@ -19,6 +19,13 @@ torch.linalg) on the same system, the LU rate in TFLOP/s, a roofline line for
 the kernel that takes the most time, an end-to-end number through the
 host-buffer entry point, and the CPU oracle timed on the host cores.
 
+The batched workload (2000 systems, N uniform in [32, 512], A = I - alpha G
++ 1e-3 E with alpha uniform in [1, 800], b = 1; TW = binary64, TF = binary16
+scaled and bfloat16, one persistent launch per batch) is reported in the same
+line under "batched": solves per second, accuracy against binary64 LU
+solutions, and the binary64 LU solve of the same systems (cuSOLVER through
+torch.linalg, systems of equal N stacked) for comparison.
+
 `--impl reference` times the CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
@@ -54,6 +61,10 @@ def parse():
     ap.add_argument("--n", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the binary64 cuSOLVER comparators (e.g. under a profiler)")
+    ap.add_argument("--batch-count", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -204,6 +215,149 @@ def run_reference(args):
 
 
 # ---------------------------------------------------------------------------
+# batched workload
+# ---------------------------------------------------------------------------
+
+BATCH_SEED = 1005
+
+
+def run_batched(args, ctx, dev, stream, flush, ws, rank):
+    """2000 uneven systems per step, one persistent launch (ir_batch_run)."""
+    import numpy as np
+    import torch
+
+    import irgen
+    from paper_2311_14616_gb300 import ir
+
+    count = args.batch_count
+    ns, alphas, As, bs = irgen.case_batch(count, BATCH_SEED)
+    Ad = [torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t() for A in As]
+    bd = [torch.from_numpy(b).to(dev) for b in bs]
+    flops = float(sum(2.0 * int(n) ** 3 / 3.0 for n in ns))
+    # binary64 LU solves of the same systems (cuSOLVER via torch.linalg), equal sizes stacked
+    groups = {}
+    for i, n in enumerate(ns):
+        groups.setdefault(int(n), []).append(i)
+    stacks = [(idx, torch.stack([torch.from_numpy(As[i]).to(dev) for i in idx]),
+               torch.stack([bd[i] for i in idx]).unsqueeze(2)) for idx in groups.values()]
+
+    def fp64_step():
+        return [torch.linalg.lu_solve(*torch.linalg.lu_factor(S), B) for _, S, B in stacks]
+
+    # the same systems padded to one [count, nmax, nmax] batch (identity on the padding)
+    nmax = int(max(ns))
+
+    def fp64_padded():
+        P = torch.zeros(count, nmax, nmax, dtype=torch.float64, device=dev)
+        Pb = torch.zeros(count, nmax, 1, dtype=torch.float64, device=dev)
+        for i, n in enumerate(ns):
+            n = int(n)
+            P[i, :n, :n] = Ad[i]
+            P[i, n:, n:] = torch.eye(nmax - n, dtype=torch.float64, device=dev)
+            Pb[i, :n, 0] = bd[i]
+        return P, Pb
+
+    def fp64_padded_step():
+        return torch.linalg.lu_solve(*torch.linalg.lu_factor(P), Pb)
+
+    def time_ref(fn):
+        for _ in range(2):
+            r = fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(max(2, args.steps // 2)):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return statistics.mean(t), r
+
+    if args.no_fp64:
+        t_grouped = t_padded = float("nan")
+        xref = [np.linalg.solve(A, b) for A, b in zip(As, bs)]
+    else:
+        t_grouped, x64 = time_ref(fp64_step)
+        P, Pb = fp64_padded()
+        t_padded, _ = time_ref(fp64_padded_step)
+        del P, Pb
+        xref = [None] * count
+        for (idx, _, _), X in zip(stacks, x64):
+            for k, i in enumerate(idx):
+                xref[i] = X[k, :, 0].cpu().numpy()
+    t64 = min(t_grouped, t_padded)
+    # binary64 floor: the batch's LU flops at the rate of a large binary64 GEMM on this GPU
+    G = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(G, G)
+    torch.cuda.synchronize()
+    t_g = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(G, G)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_g.append(e0.elapsed_time(e1))
+    del G
+    dgemm_tflops = 2 * 4096 ** 3 / (min(t_g) * 1e-3) / 1e12
+    floor64 = flops / (dgemm_tflops * 1e12) * 1e3
+    out = {"workload": f"batch_{count}_N32-512_green_alpha1-800_E1e-3_TWf64", "count": count,
+           "seed": BATCH_SEED, "fp64_lu_solve_ms": t64,
+           "fp64_lu_solve": "binary64 LU solve with torch.linalg.lu_factor + lu_solve (cuSOLVER): the "
+                            "faster of one batch padded to N=512 with identity blocks "
+                            f"({t_padded:.1f} ms) and systems of equal N stacked ({t_grouped:.1f} ms)",
+           "lu_flops_per_batch": flops, "fp64_gemm_tflops": dgemm_tflops,
+           "fp64_lu_floor_ms": floor64,
+           "fp64_lu_floor": "the batch's 2N^3/3 LU flops at the measured binary64 GEMM rate "
+                            "(torch.matmul 4096^3): no binary64 LU of these systems can be faster"}
+    for tf in ("f16", "bf16"):
+        plan = ctx.batch(Ad, bd, tf=tf)
+        for _ in range(max(3, args.warmup)):
+            plan.run()
+        torch.cuda.synchronize()
+        barrier(ws)
+        ms = []
+        l0 = ir.kernel_launches()
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        launches = ir.kernel_launches() - l0
+        t = max_over_ranks(statistics.mean(ms), ws)
+        res = plan.results()
+        errs = np.array([np.max(np.abs(x.cpu().numpy() - xr)) / np.max(np.abs(xr))
+                         for x, xr in zip(plan.xs, xref)])
+        st = {}
+        for r in res:
+            st[r["status"]] = st.get(r["status"], 0) + 1
+        out[tf] = {"ms": t, "solves_per_s": ws * count / (t * 1e-3), "speedup_vs_fp64_lu": t64 / t,
+                   "speedup_vs_fp64_floor": floor64 / t,
+                   "gpu_launches_per_step": launches / args.steps,
+                   "status": st, "mean_iters": float(np.mean([r["iters"] for r in res])),
+                   "rel_err_vs_fp64_lu": {"median": float(np.median(errs)), "max": float(np.max(errs)),
+                                          "frac_le_1e-12": float(np.mean(errs <= 1e-12))}}
+        plan.destroy()
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle as O
+        sample = list(range(0, count, max(1, count // 20)))[:20]
+        t0 = time.perf_counter()
+        for i in sample:
+            O.ir_solve(As[i], bs[i], O.F16, nb=64)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": len(sample) / dt, "unit": "solves/s", "cores": cpu_cores(),
+                               "kind": "oracle",
+                               "sample": f"oracle IR (binary16 factors) on {len(sample)} of the systems "
+                                         f"({dt:.2f} s)"}
+    return out
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -288,14 +442,19 @@ def main():
         LU, piv = torch.linalg.lu_factor(A_row)
         return torch.linalg.lu_solve(LU, piv, b_d.unsqueeze(1))
 
-    ms64, x64, _, _ = timed_steps(step64, max(3, args.steps // 2), 1)
-    t64 = max_over_ranks(statistics.mean(ms64), ws)
+    if args.no_fp64:
+        t64, x64 = None, None
+    else:
+        ms64, x64, _, _ = timed_steps(step64, max(3, args.steps // 2), 1)
+        t64 = max_over_ranks(statistics.mean(ms64), ws)
 
     # --- accuracy against the closed form and the binary64 LU solution
     xg = x32.double().cpu().numpy()
-    x64h = x64.squeeze(1).cpu().numpy()
     err_true = float(np.max(np.abs(xg - xt)) / np.max(np.abs(xt)))
-    err_vs_lu64 = float(np.max(np.abs(xg - x64h)) / np.max(np.abs(x64h)))
+    err_vs_lu64 = None
+    if x64 is not None:
+        x64h = x64.squeeze(1).cpu().numpy()
+        err_vs_lu64 = float(np.max(np.abs(xg - x64h)) / np.max(np.abs(x64h)))
     err_tc_true = float(np.max(np.abs(xtc.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
 
     # --- roofline of the kernel kind with the largest share of the profiled step
@@ -369,6 +528,8 @@ def main():
                "sample": f"one oracle IR solve of the same workload at N={sample_n} "
                          f"({dt:.2f} s), scaled by (N/{sample_n})^3"}
 
+    batched = None if args.no_batch else run_batched(args, ctx, dev, stream, flush, ws, rank)
+
     value = t32 / ws if ws > 1 else t32
     out = {
         "metric": "ir_solve_ms", "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -380,7 +541,7 @@ def main():
                    "parallelism": "replicas" if ws > 1 else "single"},
         "iters": rep32.iters, "status": rep32.status,
         "rel_err_vs_closed_form": err_true, "rel_err_vs_fp64_lu": err_vs_lu64,
-        "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": t64 / t32,
+        "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": (t64 / t32) if t64 else None,
         "lu_ms": lu_ms, "lu_tflops": lu_tflops,
         "tf32_tensor_core": {"ms": t_tc, "iters": rep_tc.iters, "status": rep_tc.status,
                              "lu_ms": lu_tc_ms, "rel_err_vs_closed_form": err_tc_true,
@@ -394,6 +555,7 @@ def main():
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
         "clocks": clk,
+        "batched": batched,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

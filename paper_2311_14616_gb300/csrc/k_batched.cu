@@ -11,8 +11,10 @@
 // permutation live in shared memory.
 //   cast          W = rTF(fl32(s A)), A streamed through shared memory by cp.async
 //   panel         64 columns, one row per thread in a rotating register
-//                 window, one CTA barrier per column (each warp stages its
-//                 candidate row; every warp then picks the winner)
+//                 window for the whole panel (rows never move; interchanges
+//                 only swap position labels), one CTA barrier per column
+//                 (each warp stages its candidate row; every warp then
+//                 picks the pivot row)
 //   interchanges  gather of the moved rows for the columns outside the panel
 //   U12           L11^{-1} A12 by fmaf chains (binary32, ascending k)
 //   update        binary16 / bfloat16 factors: tcgen05.mma on the tensor
@@ -51,18 +53,14 @@ static_assert(kMaxBatchN <= BT, "one row per thread");
 
 struct BSmem {
     alignas(16) float stage[2][BW][kRow];     // per-warp candidate rows, by step parity
-    alignas(16) float drow[2][kRow];          // row k, by step parity
     alignas(16) double xs[kMaxBatchN];        // iterate (binary64)
     alignas(16) double rs[kMaxBatchN];        // residual
     alignas(16) double bs[kMaxBatchN];        // right-hand side, promoted
     alignas(16) float vs[kMaxBatchN];         // solve values published by the sweeps
     int perm[kMaxBatchN];                     // (P A)[i] = A[perm[i]]
     float sval[2][BW];
-    int spos[2][BW];
-    int sorg[2][BW];
+    int spos[2][BW];                          // current position of each warp's candidate
     float srec[2][BW];                        // reciprocal of each candidate's pivot value
-    int dorg[2];
-    int piv_log[NB];
     int moved_cnt;
     int moved_dst[2 * NB], moved_src[2 * NB];
     unsigned long long red[BW];
@@ -70,8 +68,7 @@ struct BSmem {
     unsigned tmem_base;
     int info, nonfinite, cur, abort;
 };
-static_assert(offsetof(BSmem, stage) % 16 == 0 && offsetof(BSmem, drow) % 16 == 0 && (kRow * 4) % 16 == 0,
-              "staged rows must be 16-byte aligned");
+static_assert(offsetof(BSmem, stage) % 16 == 0 && (kRow * 4) % 16 == 0, "staged rows must be 16-byte aligned");
 constexpr size_t kBigFloats = (size_t)NB * BT;      // 128 KB of multi-use scratch, 1024-byte aligned
 constexpr size_t kBatchSmem = 1024 + (kBigFloats + NB * NB) * sizeof(float) + sizeof(BSmem);
 constexpr unsigned kTmemCols = 512;                 // four 128x128 binary32 accumulators
@@ -138,18 +135,24 @@ __device__ __forceinline__ void group_sync(int g) {
 }
 
 // ---------------------------------------------------------------------------
-// panel: columns j0 .. j0+nbp-1 of W (rows j0..n-1); thread t owns row j0 + t
+// panel: columns j0 .. j0+nbp-1 of W (rows j0..n-1).  Thread t keeps row
+// j0 + t in a rotating register window for the whole panel; rows never move
+// between threads.  Each thread tracks the row's current position (relative to
+// j0), so an interchange is two integer compares, and the pivot search takes
+// the largest |a_ik| with ties to the lowest current position (the first
+// maximal entry, as in LAPACK's getf2).  A row that becomes the pivot row of
+// step kp stops there; its U part is the staged copy of step kp.
 // ---------------------------------------------------------------------------
 __device__ void b_panel(float *W, int n, int ldw, int j0, int nbp, BSmem &sm, float *Ls, float *Us) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int gi = j0 + t;
-    const bool valid = gi < n;
-    int org = gi;
+    const bool valid = j0 + t < n;
+    int pos = t;            // current position of this row, relative to j0
+    int kp = nbp;           // the step at which it became the pivot row (nbp: never)
     float a[NB];
     {
         // 16-byte loads: j0 and ldw are multiples of 4, and a chunk that starts
         // before column n ends inside the padded row
-        const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)gi * ldw + j0);
+        const float4 *src = reinterpret_cast<const float4 *>(W + (int64_t)(j0 + t) * ldw + j0);
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
             const float4 v = (valid && 4 * q < nbp) ? src[q] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -161,12 +164,12 @@ __device__ void b_panel(float *W, int n, int ldw, int j0, int nbp, BSmem &sm, fl
     }
 #pragma unroll 1
     for (int k = 0; k < nbp; ++k) {
-        const int b = k & 1, pk = j0 + k;
-        const bool cand = valid && gi >= pk;
+        const int b = k & 1;
+        const bool cand = valid && kp == nbp;
         const unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
         const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-        const unsigned tie = __ballot_sync(0xffffffffu, cand && key == kmax);
-        if (tie && lane == __ffs(tie) - 1) {
+        const int mpos = __reduce_min_sync(0xffffffffu, (cand && key == kmax) ? pos : INT_MAX);
+        if (cand && pos == mpos) {
             float *st = sm.stage[b][warp];
             st[3] = a[0];
 #pragma unroll
@@ -178,47 +181,37 @@ __device__ void b_panel(float *W, int n, int ldw, int j0, int nbp, BSmem &sm, fl
             st[66] = a[63];
             st[67] = 0.f;
             sm.sval[b][warp] = __uint_as_float(kmax);
-            sm.spos[b][warp] = gi;
-            sm.sorg[b][warp] = org;
+            sm.spos[b][warp] = mpos;
             sm.srec[b][warp] = (a[0] != 0.f) ? 1.0f / a[0] : 0.f;
         }
-        if (lane == 0 && !tie) {
+        if (lane == 0 && mpos == INT_MAX) {
             sm.sval[b][warp] = 0.f;
             sm.spos[b][warp] = INT_MAX;
         }
-        if (valid && gi == pk) {
-            float *dr = sm.drow[b];
-#pragma unroll
-            for (int c = 0; c < NB; ++c) dr[3 + c] = a[c];
-            sm.dorg[b] = org;
-        }
         __syncthreads();
-        // the CTA winner: largest |value|, lowest row among equals (= lowest warp)
+        // the pivot row: largest |value|, lowest position among equals
         const unsigned wk = lane < BW ? __float_as_uint(sm.sval[b][lane]) : 0u;
         const int wp = lane < BW ? sm.spos[b][lane] : INT_MAX;
         const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
-        const unsigned who = __ballot_sync(0xffffffffu, wp != INT_MAX && wk == bk);
+        const int ppos = __reduce_min_sync(0xffffffffu, (wp != INT_MAX && wk == bk) ? wp : INT_MAX);
+        const unsigned who = __ballot_sync(0xffffffffu, lane < BW && wp == ppos);
         const int w = who ? __ffs(who) - 1 : 0;
-        const int p = sm.spos[b][w];
         const float *u = sm.stage[b][w];          // u[3 + i] = pivot row, column j0 + k + i
         const float piv = u[3];
         const float r = sm.srec[b][w];
-        if (t == 0) {
-            sm.piv_log[k] = p;
-            if (piv == 0.f && sm.info == 0) sm.info = pk + 1;
-        }
-        if (valid && gi == pk) {
-            org = sm.sorg[b][w];                  // this row now holds the pivot row (kept in Us)
-        } else if (valid && gi == p) {
-#pragma unroll
-            for (int c = 0; c < NB; ++c) a[c] = sm.drow[b][3 + c];
-            org = sm.dorg[b];
+        if (t == 0 && piv == 0.f && sm.info == 0) sm.info = j0 + k + 1;
+        // interchange positions k and ppos
+        if (cand && pos == ppos) {
+            pos = k;
+            kp = k;
+        } else if (pos == k) {
+            pos = ppos;
         }
         if (warp == 1) {
             Us[k * NB + lane] = u[3 + lane];
             Us[k * NB + lane + 32] = u[35 + lane];
         }
-        if (valid && gi > pk) {
+        if (valid && kp == nbp) {
             // l = a * fl(1/pivot) (division when the pivot is subnormal): LAPACK getf2
             float l = a[0];
             if (piv != 0.f) l = (fabsf(piv) >= FLT_MIN) ? l * r : l / piv;
@@ -240,36 +233,31 @@ __device__ void b_panel(float *W, int n, int ldw, int j0, int nbp, BSmem &sm, fl
     // moved rows and the composed permutation
     if (t == 0) sm.moved_cnt = 0;
     __syncthreads();
-    const bool moved = valid && org != gi;
+    const bool moved = valid && pos != t;
     int porg = 0;
     if (moved) {
         const int e = atomicAdd(&sm.moved_cnt, 1);
-        sm.moved_dst[e] = gi;
-        sm.moved_src[e] = org;
-        porg = sm.perm[org];
+        sm.moved_dst[e] = j0 + pos;
+        sm.moved_src[e] = j0 + t;
+        porg = sm.perm[j0 + t];
     }
     __syncthreads();
-    if (moved) sm.perm[gi] = porg;
-    // the multipliers of each row's content (walking the interchanges backward) and the U part
+    if (moved) sm.perm[j0 + pos] = porg;
+    // the row at its final position: multipliers of steps < kp, then the U part staged at step kp
     if (valid) {
-        const int kend = (gi - j0 < nbp) ? gi - j0 : nbp;
-        int pos = gi;
+        float4 *dst = reinterpret_cast<float4 *>(W + (int64_t)(j0 + pos) * ldw + j0);
 #pragma unroll
-        for (int k = NB - 1; k >= 0; --k) {
-            if (k < nbp) {
-                a[k] = (k < kend) ? Ls[k * BT + (pos - j0)] : 0.f;
-                const int pkk = j0 + k, pp = sm.piv_log[k];
-                if (pos == pkk) pos = pp;
-                else if (pos == pp) pos = pkk;
-            } else {
-                a[k] = 0.f;
+        for (int q = 0; q < NB / 4; ++q) {
+            if (4 * q < nbp) {
+                float v[4];
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int c = 4 * q + e;
+                    v[e] = (c < kp) ? Ls[c * BT + t] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
+                }
+                dst[q] = make_float4(v[0], v[1], v[2], v[3]);
             }
         }
-        float *dst = W + (int64_t)gi * ldw + j0;
-#pragma unroll
-        for (int c = 0; c < NB; ++c)
-            if (c < kend) dst[c] = a[c];
-        for (int c = kend; c < nbp; ++c) dst[c] = Us[kend * NB + (c - kend)];
     }
     __syncthreads();
 }

@@ -3,10 +3,11 @@
 // Algorithm IR; lu! of Sec. 2.1.1).
 //
 // The binary32 operations are exactly those of the unblocked right-looking
-// algorithm: pivot = first row of maximal |a_ik|, l_ik = a_ik / a_kk (IEEE
-// division), a_ij = fmaf(-l_ik, u_kj, a_ij) with k ascending for every
-// element.  Blocking only regroups these chains, so the factors are bitwise
-// those of the unblocked algorithm whenever the trailing update is binary32.
+// algorithm: pivot = first row of maximal |a_ik|, l_ik = a_ik * fl(1/a_kk)
+// (LAPACK getf2; a division below the smallest normal), a_ij = fmaf(-l_ik,
+// u_kj, a_ij) with k ascending for every element.  Blocking only regroups
+// these chains, so the factors are bitwise those of the unblocked algorithm
+// whenever the trailing update is binary32.
 #include <cfloat>
 #include <climits>
 #include <cstddef>
@@ -22,40 +23,30 @@ constexpr int NB = kPanelNB;
 constexpr int T = kPanelT;
 constexpr int NW = T / 32;
 
-// Every panel row carries the index of the row it started the panel in
-// ("origin"), so the panel's net permutation is known at the end without
-// replaying the interchanges.
+// Rows never move between threads during a panel: every thread keeps its
+// row and tracks the row's current position, so an interchange is two integer
+// compares and the panel's net permutation is known at the end.
 //
-// Candidate exchange: at step k every CTA pushes one 272-byte record
-// (|a|, position, origin, the 64 row values, pad) into slot [k & 1][its rank]
-// of every CTA of the cluster with st.async, which counts the bytes on the
-// receiver's mbarrier; CTA 0 also pushes the record of row k (slot kDiagSlot).
-// A receiver waits (bounded) on its own mbarrier for all records of the step.
+// Candidate exchange: at step k every warp stages its best row as a 272-byte
+// record (|a| bits, position, fl(1/a), the 64 row values, pad) and the CTA's
+// best record is pushed with one bulk copy per destination into slot
+// [k & 1][its rank] of every CTA of the cluster, counted on the receiver's
+// mbarrier.  A receiver waits (bounded) for all records of the step.
 constexpr int kRec = 68;                     // floats per record
-constexpr int kDiagSlot = kPanelMaxCluster;  // slot of the row-k record
 struct PanelSmem {
-    // row arrays first, each 16-byte aligned (they are accessed as float4)
-    alignas(16) float stage_row[NW][NB];     // per-warp candidate row
-    alignas(16) float diag_row[NB];          // row k, written by its owner (CTA 0)
-    alignas(16) float recv[2][kPanelMaxCluster + 1][kRec];
-    alignas(16) float out[2][2][kRec];       // [parity][candidate, row k] records to send
+    // records first, each 16-byte aligned (they are accessed as float4)
+    alignas(16) float stage[2][NW][kRec];    // per-warp candidate records, by step parity
+    alignas(16) float recv[2][kPanelMaxCluster][kRec];
     alignas(8) unsigned long long recv_bar[2];
-    float stage_val[NW];
-    int stage_pos[NW];
-    int stage_org[NW];
-    int diag_org;
-    float win_r;                 // fl(1/pivot) for the step
-    int win_pos, win_src, uorg, dorg;
     int piv_log[NB];             // p_k of every step (the panel's interchanges)
     int zero_piv;                // first zero pivot of this panel (1-based), or 0
     int abort_flag;
 };
-static_assert(offsetof(PanelSmem, stage_row) % 16 == 0 && offsetof(PanelSmem, diag_row) % 16 == 0 &&
-                  offsetof(PanelSmem, recv) % 16 == 0 && offsetof(PanelSmem, out) % 16 == 0 &&
+static_assert(offsetof(PanelSmem, stage) % 16 == 0 && offsetof(PanelSmem, recv) % 16 == 0 &&
                   (kRec * 4) % 16 == 0,
-              "float4 rows of the panel's shared memory must be 16-byte aligned");
+              "float4 records of the panel's shared memory must be 16-byte aligned");
 // Dynamic shared memory after PanelSmem: Ls[NB][T] multipliers by step and
-// position, Us[NB][NB] pivot rows (CTA 0).
+// thread, Us[NB][NB] pivot rows.
 constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * T + sizeof(float) * NB * NB + 16;
 
 __device__ __forceinline__ unsigned cluster_rank() {
@@ -76,11 +67,6 @@ __device__ __forceinline__ unsigned map_cta(unsigned local_addr, unsigned rank) 
     unsigned r;
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
     return r;
-}
-__device__ __forceinline__ float ld_dsmem_f32(unsigned addr) {
-    float v;
-    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(addr) : "memory");
-    return v;
 }
 
 // Bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into
@@ -152,22 +138,22 @@ __device__ __forceinline__ void store_op_row(void *op, int64_t row, const float 
     }
 }
 
-// One cluster factors the panel AF[j:n, j:j+nbp].  CTA c of the cluster owns
-// panel rows (positions) j + c*T + t, one per thread.  A thread keeps the
-// not-yet-eliminated part of its row in a rotating register window: at step k,
-// a[i] holds column j+k+i (zero past the panel), so the current column is
+// One cluster factors the panel AF[j:n, j:j+nbp].  Thread t of CTA c keeps
+// row j + c*T + t for the whole panel in a rotating register window: at step
+// k, a[i] holds column j+k+i (zero past the panel), so the current column is
 // always a[0] and the update a[i] <- fmaf(-l, u[i+1], a[i+1]) also shifts the
-// window.  Per column k: warp argmax (redux.sync) -> CTA candidate -> records
-// pushed to every CTA (st.async) -> bounded wait on the local mbarrier ->
-// winner picked locally -> interchange of positions k and p -> scaling by the
-// pivot's reciprocal (LAPACK getf2) and rank-1 update.
-// The column loop touches no global memory: multipliers go to shared memory
-// by step and position, pivot rows and the interchanges to shared memory; at
-// the end every row gathers its multipliers by walking the interchanges
-// backward (DSMEM reads).  The rows whose content moved are listed as
-// (destination, origin) pairs in swap_list (count in swap_list[0]) for the
-// gather of the other columns, and perm is composed with the panel's
-// permutation.
+// window.  Per column k: warp candidate (largest |a|, ties to the lowest
+// current position: redux.sync) staged as a record -> the CTA's best record
+// pushed to every CTA (bulk copies, issued by one lane per destination) ->
+// bounded wait on the local mbarrier -> every warp picks the pivot row from
+// the received headers -> positions k and p swap labels -> scaling by the
+// pivot's reciprocal and rank-1 update of the rows that are not pivot rows.
+// The column loop touches no global memory.  At the end each thread writes
+// its row to its final position: the multipliers of the steps before the row
+// became a pivot row (its own column of Ls), then the U part staged at that
+// step.  Rows that moved are listed as (destination, origin) pairs in
+// swap_list (count in swap_list[0]) for the interchanges of the other
+// columns, and perm is composed with the panel's permutation.
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
@@ -178,11 +164,12 @@ __global__ void __launch_bounds__(T, 1)
     const unsigned crank = cluster_rank();
     const unsigned csize = cluster_size();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int gi = j + (int)crank * T + t;           // this thread's row (position)
-    const bool valid = gi < n;
-    const unsigned step_bytes = (csize + 1u) * (unsigned)(kRec * 4);
+    const int home = (int)crank * T + t;             // this row's position at the start, relative to j
+    const bool valid = j + home < n;
+    const unsigned step_bytes = csize * (unsigned)(kRec * 4);
 
-    int org = gi;
+    int pos = home;          // current position, relative to j
+    int kp = nbp;            // the step at which the row became the pivot row (nbp: never)
     if (crank == 0 && t == 0) swap_list[0] = 0;
     if (t == 0) {
         sm.zero_piv = 0;
@@ -195,7 +182,7 @@ __global__ void __launch_bounds__(T, 1)
     }
     float a[NB];
     if (valid) {
-        const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)gi * ldf + j);
+        const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)(j + home) * ldf + j);
 #pragma unroll
         for (int c = 0; c < NB; c += 4) {
             float4 v = (c < nbp) ? src[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -217,124 +204,89 @@ __global__ void __launch_bounds__(T, 1)
 #pragma unroll 1
     for (int k = 0; k < nbp; ++k) {
         const int buf = k & 1;
-        const int pk = j + k;   // position being eliminated
-        // 1. local candidate: first maximal |a_ik| over rows i >= pk (rows are
-        //    owned in increasing order, so the lowest lane/warp/CTA wins ties)
-        const bool cand = valid && gi >= pk;
+        // 1. warp candidate: largest |a_ik| over the rows that are not pivot
+        //    rows yet, ties to the lowest current position; staged as a record
+        const bool cand = valid && kp == nbp;
         const unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
         const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-        const unsigned tie = __ballot_sync(0xffffffffu, cand && key == kmax);
-        if (tie && lane == __ffs(tie) - 1) {
+        const int mpos = __reduce_min_sync(0xffffffffu, (cand && key == kmax) ? pos : INT_MAX);
+        float *st = sm.stage[buf][warp];
+        if (cand && pos == mpos) {
+            float4 *s4 = reinterpret_cast<float4 *>(st);
+            s4[0] = make_float4(__uint_as_float(kmax), __int_as_float(mpos), (a[0] != 0.f) ? 1.0f / a[0] : 0.f, a[0]);
 #pragma unroll
-            for (int c = 0; c < NB; c += 4)
-                *reinterpret_cast<float4 *>(&sm.stage_row[warp][c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-            sm.stage_org[warp] = org;
-            sm.stage_val[warp] = __uint_as_float(kmax);
-            sm.stage_pos[warp] = gi;
+            for (int q = 0; q < 15; ++q)
+                s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
+            s4[16] = make_float4(a[61], a[62], a[63], 0.f);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> bulk copy
         }
-        if (lane == 0 && !tie) { sm.stage_val[warp] = 0.f; sm.stage_pos[warp] = INT_MAX; }
-        // row k is published by its owner (always CTA 0: positions j..j+NB-1)
-        if (valid && gi == pk) {
-#pragma unroll
-            for (int c = 0; c < NB; c += 4)
-                *reinterpret_cast<float4 *>(&sm.diag_row[c]) = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-            sm.diag_org = org;
+        if (lane == 0 && mpos == INT_MAX) {
+            st[0] = 0.f;
+            st[1] = __int_as_float(INT_MAX);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncthreads();
-        // 2. CTA candidate, pushed to every CTA of the cluster
+        // 2. the CTA's best record, pushed to every CTA of the cluster (one lane per destination)
         if (warp == 0) {
-            const unsigned wk = lane < NW ? __float_as_uint(sm.stage_val[lane]) : 0u;
-            const int wp = lane < NW ? sm.stage_pos[lane] : INT_MAX;
+            const unsigned wk = lane < NW ? __float_as_uint(sm.stage[buf][lane][0]) : 0u;
+            const int wp = lane < NW ? __float_as_int(sm.stage[buf][lane][1]) : INT_MAX;
             const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
-            const unsigned who = __ballot_sync(0xffffffffu, wp != INT_MAX && wk == bk);
+            const int bp = __reduce_min_sync(0xffffffffu, (wp != INT_MAX && wk == bk) ? wp : INT_MAX);
+            const unsigned who = __ballot_sync(0xffffffffu, lane < NW && wp == bp);
             const int w = who ? __ffs(who) - 1 : 0;
-            const int bp = who ? __shfl_sync(0xffffffffu, wp, w) : INT_MAX;
-            // compose the records in local shared memory, then one bulk copy per CTA
-            float *rec = sm.out[buf][0];
-            const float *row = sm.stage_row[w];
-            for (int c = lane; c < NB; c += 32) rec[3 + c] = row[c];
-            if (lane == 0) {
-                rec[0] = __uint_as_float(bk);
-                rec[1] = __int_as_float(bp);
-                rec[2] = __int_as_float(sm.stage_org[w]);
-                rec[kRec - 1] = 0.f;
-            }
-            if (crank == 0) {
-                float *drec = sm.out[buf][1];
-                for (int c = lane; c < NB; c += 32) drec[3 + c] = sm.diag_row[c];
-                if (lane == 0) {
-                    drec[0] = 0.f;
-                    drec[1] = __int_as_float(pk);
-                    drec[2] = __int_as_float(sm.diag_org);
-                    drec[kRec - 1] = 0.f;
-                }
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> bulk copy
-            __syncwarp();
             if (lane < (int)csize) {
                 const unsigned rbar = map_cta(bar_addr + 8u * buf, (unsigned)lane);
-                const unsigned slot = recv_addr + (unsigned)((buf * (kPanelMaxCluster + 1) + (int)crank) * kRec * 4);
-                bulk_to_cta(map_cta(slot, (unsigned)lane), smem_u32(rec), kRec * 4, rbar);
-                if (crank == 0) {
-                    const unsigned dslot = recv_addr + (unsigned)((buf * (kPanelMaxCluster + 1) + kDiagSlot) * kRec * 4);
-                    bulk_to_cta(map_cta(dslot, (unsigned)lane), smem_u32(sm.out[buf][1]), kRec * 4, rbar);
-                }
-            }
-            // 3. wait (bounded) for every record of this step
-            const unsigned par = (unsigned)(k >> 1) & 1u;
-            if (lane == 0 && !sm.abort_flag) {
-                while (!mbar_try_wait_cluster(bar_addr + 8u * buf, par)) {
-                    if (globaltimer() > deadline) {      // give up: report, carry on without waiting
-                        sm.abort_flag = 1;
-                        atomicExch(&dev->timeout, 1);
-                        break;
-                    }
-                }
-            }
-            // re-arm this buffer for step k + 2
-            if (lane == 0 && k + 2 < nbp && !sm.abort_flag) mbar_expect_arrive(bar_addr + 8u * buf, step_bytes);
-            __syncwarp();
-            // 4. the winner, picked locally from the received headers
-            const float *rb = sm.recv[buf][0];
-            const unsigned ck = lane < (int)csize ? __float_as_uint(rb[lane * kRec]) : 0u;
-            const int cp = lane < (int)csize ? __float_as_int(rb[lane * kRec + 1]) : INT_MAX;
-            const unsigned ckmax = __reduce_max_sync(0xffffffffu, ck);
-            const unsigned cwho = __ballot_sync(0xffffffffu, cp != INT_MAX && ck == ckmax);
-            const int wc = cwho ? __ffs(cwho) - 1 : 0;
-            if (lane == 0) {
-                const float *wr = rb + wc * kRec;
-                const float piv = wr[3];
-                sm.win_pos = __float_as_int(wr[1]);
-                sm.win_src = wc;
-                sm.uorg = __float_as_int(wr[2]);
-                sm.dorg = __float_as_int(sm.recv[buf][kDiagSlot][2]);
-                sm.win_r = (piv != 0.f) ? 1.0f / piv : 0.f;
-                sm.piv_log[k] = sm.win_pos;
+                const unsigned slot = recv_addr + (unsigned)((buf * kPanelMaxCluster + (int)crank) * kRec * 4);
+                bulk_to_cta(map_cta(slot, (unsigned)lane), smem_u32(sm.stage[buf][w]), kRec * 4, rbar);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // the stage slot may be reused
             }
         }
-        __syncthreads();
-        const int p = sm.win_pos;
-        const float *u = sm.recv[buf][sm.win_src];     // u[3 + i] = pivot row, column k + i
+        // 3. every warp waits (bounded) for the records of all CTAs of this step
+        const unsigned par = (unsigned)(k >> 1) & 1u;
+        if (lane == 0 && !sm.abort_flag) {
+            while (!mbar_try_wait_cluster(bar_addr + 8u * buf, par)) {
+                if (globaltimer() > deadline) {      // give up: report, carry on without waiting
+                    sm.abort_flag = 1;
+                    atomicExch(&dev->timeout, 1);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        // re-arm this buffer for step k + 2 (before this CTA sends its next record)
+        if (t == 0 && k + 2 < nbp && !sm.abort_flag) mbar_expect_arrive(bar_addr + 8u * buf, step_bytes);
+        // 4. the pivot row, picked by every warp from the received headers
+        const float *rb = sm.recv[buf][0];
+        const unsigned ck = lane < (int)csize ? __float_as_uint(rb[lane * kRec]) : 0u;
+        const int cp = lane < (int)csize ? __float_as_int(rb[lane * kRec + 1]) : INT_MAX;
+        const unsigned ckmax = __reduce_max_sync(0xffffffffu, ck);
+        const int ppos = __reduce_min_sync(0xffffffffu, (cp != INT_MAX && ck == ckmax) ? cp : INT_MAX);
+        const unsigned cwho = __ballot_sync(0xffffffffu, lane < (int)csize && cp == ppos);
+        const int wc = cwho ? __ffs(cwho) - 1 : 0;
+        const float *u = rb + wc * kRec;                // u[3 + i] = pivot row, column j + k + i
         const float piv = u[3];
-        // 5. interchange of positions pk and p; the pivot row is final (kept in Us)
-        if (valid && gi == pk) {
-            org = sm.uorg;
-        } else if (valid && gi == p) {
-            const float *dr = sm.recv[buf][kDiagSlot] + 3;
-#pragma unroll
-            for (int c = 0; c < NB; ++c) a[c] = dr[c];
-            org = sm.dorg;
+        const float r = u[2];
+        if (t == 0) {
+            sm.piv_log[k] = j + ppos;
+            if (piv == 0.f && sm.zero_piv == 0) sm.zero_piv = j + k + 1;
         }
-        if (crank == 0 && warp == 1) {
+        // 5. interchange of positions k and ppos: labels only
+        if (cand && pos == ppos) {
+            pos = k;
+            kp = k;
+        } else if (pos == k) {
+            pos = ppos;
+        }
+        if (warp == 1) {
             Us[k * NB + lane] = u[3 + lane];
             Us[k * NB + lane + 32] = u[35 + lane];
         }
-        if (piv == 0.f && t == 0 && sm.zero_piv == 0) sm.zero_piv = pk + 1;
         // 6. scale column k (getf2: by the reciprocal, divide below the smallest
         //    normal), update and shift the live part of the window
-        if (valid && gi > pk) {
+        if (valid && kp == nbp) {
             float l = a[0];
-            if (piv != 0.f) l = (fabsf(piv) >= FLT_MIN) ? l * sm.win_r : l / piv;
+            if (piv != 0.f) l = (fabsf(piv) >= FLT_MIN) ? l * r : l / piv;
             Ls[k * T + t] = l;
             const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
             const int live = nbp - k;                                        // a[0..live-1] nonzero
@@ -350,59 +302,32 @@ __global__ void __launch_bounds__(T, 1)
             }
         }
     }
-    // net permutation of the panel: position gi now holds the row from org
+    // net permutation of the panel: position j + pos now holds the row that started at j + home
     int porg = 0;
-    const bool moved = valid && org != gi;
+    const bool moved = valid && pos != home;
     if (moved) {
         int e = atomicAdd(&swap_list[0], 1);
-        swap_list[1 + 2 * e] = gi;
-        swap_list[2 + 2 * e] = org;
-        porg = perm[org];
+        swap_list[1 + 2 * e] = j + pos;
+        swap_list[2 + 2 * e] = j + home;
+        porg = perm[j + home];
     }
     if (crank == 0) {
         for (int k = t; k < nbp; k += T) ipiv[j + k] = sm.piv_log[k];
         if (t == 0 && sm.zero_piv) atomicMin(&dev->info, sm.zero_piv);
     }
-    // all multipliers of the cluster are in shared memory; perm reads done
-    cluster_sync_all();
-    if (moved) perm[gi] = porg;
+    cluster_sync_all();   // every perm read of the cluster is done
+    if (moved) perm[j + pos] = porg;
     if (valid) {
-        // multipliers of this row's content: walk the interchanges backward
-        // from the final position; at step k the content sat at position pos
-        const int kend = (gi - j < nbp) ? gi - j : nbp;
-        const unsigned ls_base = smem_u32(Ls);
-        int pos = gi;
+        // the row at its final position: multipliers of steps < kp, then the U part staged at step kp
 #pragma unroll
-        for (int k = NB - 1; k >= 0; --k) {
-            if (k < nbp) {
-                if (k < kend) {
-                    const int rel = pos - j;
-                    a[k] = ld_dsmem_f32(map_cta(ls_base + 4u * (unsigned)(k * T + (rel % T)), (unsigned)(rel / T)));
-                } else {
-                    a[k] = 0.f;
-                }
-                const int pkk = j + k, pp = sm.piv_log[k];
-                if (pos == pkk) pos = pp;
-                else if (pos == pp) pos = pkk;
-            } else {
-                a[k] = 0.f;
-            }
-        }
-        float *dst = AF + (int64_t)gi * ldf + j;
-        if (kend == NB) {
+        for (int c = 0; c < NB; ++c) a[c] = (c < kp) ? Ls[c * T + t] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
+        float4 *dst = reinterpret_cast<float4 *>(AF + (int64_t)(j + pos) * ldf + j);
 #pragma unroll
-            for (int c = 0; c < NB; c += 4)
-                reinterpret_cast<float4 *>(dst)[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-        } else {
-            // a pivot row of this panel: L part, then its U part from Us
-#pragma unroll
-            for (int c = 0; c < NB; ++c)
-                if (c < kend) dst[c] = a[c];
-            for (int c = kend; c < nbp; ++c) dst[c] = Us[kend * NB + (c - kend)];
-        }
-        if (has_trailing && Aop != nullptr && gi >= j + NB) store_op_row(Aop, gi - (j + NB), a, tf);
+        for (int c = 0; c < NB; c += 4)
+            if (c < nbp) dst[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
+        if (has_trailing && Aop != nullptr && pos >= NB) store_op_row(Aop, pos - NB, a, tf);
     }
-    cluster_sync_all();   // no CTA leaves while its shared memory may be read
+    cluster_sync_all();   // no CTA leaves while its shared memory may be written
 }
 
 // Apply the panel's row permutation to the columns [c0a, c1a) and [c0b, c1b):
