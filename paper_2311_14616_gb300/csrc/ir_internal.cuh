@@ -19,9 +19,10 @@ namespace ir {
 
 constexpr int kTrsvB = 64;        // row block of the triangular solves
 constexpr int kPanelNB = 64;      // panel width = outer block size
-constexpr int kPanelT = 512;      // threads per panel CTA (one row each)
+constexpr int kPanelRows = 512;   // panel rows per CTA (two per thread)
+constexpr int kPanelThreads = 256;
 constexpr int kPanelMaxCluster = 16;
-constexpr int kMaxN = kPanelT * kPanelMaxCluster;  // 8192 rows per panel cluster
+constexpr int kMaxN = kPanelRows * kPanelMaxCluster;  // 8192 rows per panel cluster
 
 // Device-side scalars.  Non-negative doubles are ordered like their bit
 // patterns, so maxima are kept with atomicMax on uint64 (deterministic).

@@ -20,19 +20,22 @@ namespace ir {
 namespace {
 
 constexpr int NB = kPanelNB;
-constexpr int T = kPanelT;
+constexpr int T = kPanelThreads;    // threads per CTA
+constexpr int RPC = kPanelRows;     // rows per CTA: thread t holds rows t and t + T
 constexpr int NW = T / 32;
 
-// Rows never move between threads during a panel: every thread keeps its
-// row and tracks the row's current position, so an interchange is two integer
+// Rows never move between threads during a panel: every thread keeps its two
+// rows and tracks their current positions, so an interchange is a few integer
 // compares and the panel's net permutation is known at the end.
 //
 // Candidate exchange: at step k every warp stages its best row as a 272-byte
 // record (|a| bits, position, fl(1/a), the 64 row values, pad) and the CTA's
-// best record is pushed with one bulk copy per destination into slot
-// [k & 1][its rank] of every CTA of the cluster, counted on the receiver's
-// mbarrier.  A receiver waits (bounded) for all records of the step.
+// best record is pushed, 17 chunks of 16 bytes per destination, each stored by
+// its own thread with st.async, into slot [k & 1][its rank] of every CTA of
+// the cluster, counted on the receiver's mbarrier.  A receiver waits
+// (bounded) for all records of the step.
 constexpr int kRec = 68;                     // floats per record
+constexpr int kChunks = kRec / 4;            // 16-byte chunks per record
 struct PanelSmem {
     // records first, each 16-byte aligned (they are accessed as float4)
     alignas(16) float stage[2][NW][kRec];    // per-warp candidate records, by step parity
@@ -45,9 +48,9 @@ struct PanelSmem {
 static_assert(offsetof(PanelSmem, stage) % 16 == 0 && offsetof(PanelSmem, recv) % 16 == 0 &&
                   (kRec * 4) % 16 == 0,
               "float4 records of the panel's shared memory must be 16-byte aligned");
-// Dynamic shared memory after PanelSmem: Ls[NB][T] multipliers by step and
-// thread, Us[NB][NB] pivot rows.
-constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * T + sizeof(float) * NB * NB + 16;
+// Dynamic shared memory after PanelSmem: Ls[NB][RPC] multipliers by step and
+// row slot, Us[NB][NB] pivot rows.
+constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * RPC + sizeof(float) * NB * NB + 16;
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -69,11 +72,12 @@ __device__ __forceinline__ unsigned map_cta(unsigned local_addr, unsigned rank) 
     return r;
 }
 
-// Bulk copy of `bytes` (multiple of 16) from this CTA's shared memory into
-// another CTA's shared memory, counted on that CTA's mbarrier.
-__device__ __forceinline__ void bulk_to_cta(unsigned rdst, unsigned src, unsigned bytes, unsigned rbar) {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(rdst),
-                 "r"(src), "r"(bytes), "r"(rbar)
+// 16-byte store into another CTA's shared memory, counted (complete_tx) on that
+// CTA's mbarrier; the receiver's acquire of the mbarrier phase makes it visible.
+__device__ __forceinline__ void st_async_v4(unsigned rdst, float4 v, unsigned rbar) {
+    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(rdst),
+                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
+                 "r"(__float_as_uint(v.w)), "r"(rbar)
                  : "memory");
 }
 __device__ __forceinline__ void mbar_init_p(unsigned addr, unsigned count) {
@@ -138,38 +142,58 @@ __device__ __forceinline__ void store_op_row(void *op, int64_t row, const float 
     }
 }
 
+// Stage one row window as a candidate record: |a| bits, position, fl(1/a),
+// the 64 values (record[3 + i] = a[i]), pad.
+__device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], unsigned key, int pos) {
+    float4 *s4 = reinterpret_cast<float4 *>(st);
+    s4[0] = make_float4(__uint_as_float(key), __int_as_float(pos), (a[0] != 0.f) ? __frcp_rn(a[0]) : 0.f, a[0]);
+#pragma unroll
+    for (int q = 0; q < 15; ++q) s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
+    s4[16] = make_float4(a[61], a[62], a[63], 0.f);
+}
+
+// The row's values at its final position: multipliers of the steps before it
+// became the pivot row (kp; nbp if never), then the U part staged at step kp.
+__device__ __forceinline__ void final_row(float (&a)[NB], const float *Ls, int slot, const float *Us, int kp,
+                                          int nbp) {
+#pragma unroll
+    for (int c = 0; c < NB; ++c) a[c] = (c < kp) ? Ls[c * RPC + slot] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
+}
+
 // One cluster factors the panel AF[j:n, j:j+nbp].  Thread t of CTA c keeps
-// row j + c*T + t for the whole panel in a rotating register window: at step
-// k, a[i] holds column j+k+i (zero past the panel), so the current column is
-// always a[0] and the update a[i] <- fmaf(-l, u[i+1], a[i+1]) also shifts the
-// window.  Per column k: warp candidate (largest |a|, ties to the lowest
-// current position: redux.sync) staged as a record -> the CTA's best record
-// pushed to every CTA (bulk copies, issued by one lane per destination) ->
-// bounded wait on the local mbarrier -> every warp picks the pivot row from
-// the received headers -> positions k and p swap labels -> scaling by the
-// pivot's reciprocal and rank-1 update of the rows that are not pivot rows.
-// The column loop touches no global memory.  At the end each thread writes
-// its row to its final position: the multipliers of the steps before the row
-// became a pivot row (its own column of Ls), then the U part staged at that
-// step.  Rows that moved are listed as (destination, origin) pairs in
-// swap_list (count in swap_list[0]) for the interchanges of the other
-// columns, and perm is composed with the panel's permutation.
+// rows j + c*RPC + t and j + c*RPC + T + t for the whole panel in rotating
+// register windows: at step k, a[i] holds column j+k+i (zero past the panel),
+// so the current column is always a[0] and the update a[i] <- fmaf(-l,
+// u[i+1], a[i+1]) also shifts the window.  Per column k: thread, then warp
+// candidate (largest |a|, ties to the lowest current position: redux.sync)
+// staged as a record -> the CTA's best record pushed to every CTA (st.async,
+// one thread per 16-byte chunk and destination) -> bounded wait on the local
+// mbarrier -> every warp picks the pivot row from the received headers ->
+// positions k and p swap labels -> scaling by the pivot's reciprocal and
+// rank-1 update of the rows that are not pivot rows (both rows of a thread
+// share the loads of the pivot row).  The column loop touches no global
+// memory.  At the end each row is written to its final position: the
+// multipliers of the steps before it became a pivot row, then the U part
+// staged at that step.  Rows that moved are listed as (destination, origin)
+// pairs in swap_list (count in swap_list[0]) for the interchanges of the
+// other columns, and perm is composed with the panel's permutation.
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
     extern __shared__ __align__(16) unsigned char panel_smem[];
     PanelSmem &sm = *reinterpret_cast<PanelSmem *>(panel_smem);
-    float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [NB][T]
-    float *Us = Ls + (size_t)NB * T;                                          // [NB][NB]
+    float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [NB][RPC]
+    float *Us = Ls + (size_t)NB * RPC;                                        // [NB][NB]
     const unsigned crank = cluster_rank();
     const unsigned csize = cluster_size();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int home = (int)crank * T + t;             // this row's position at the start, relative to j
-    const bool valid = j + home < n;
+    const int home0 = (int)crank * RPC + t, home1 = home0 + T;   // start positions, relative to j
+    const bool valid0 = j + home0 < n, valid1 = j + home1 < n;
     const unsigned step_bytes = csize * (unsigned)(kRec * 4);
+    const int nsend = (int)csize * kChunks;                       // record chunks to store per step
 
-    int pos = home;          // current position, relative to j
-    int kp = nbp;            // the step at which the row became the pivot row (nbp: never)
+    int pos0 = home0, pos1 = home1;     // current positions, relative to j
+    int kp0 = nbp, kp1 = nbp;           // the step at which each row became the pivot row (nbp: never)
     if (crank == 0 && t == 0) swap_list[0] = 0;
     if (t == 0) {
         sm.zero_piv = 0;
@@ -180,20 +204,20 @@ __global__ void __launch_bounds__(T, 1)
         mbar_expect_arrive(smem_u32(&sm.recv_bar[0]), step_bytes);
         if (nbp > 1) mbar_expect_arrive(smem_u32(&sm.recv_bar[1]), step_bytes);
     }
-    float a[NB];
-    if (valid) {
-        const float4 *src = reinterpret_cast<const float4 *>(AF + (int64_t)(j + home) * ldf + j);
+    float a0[NB], a1[NB];
+    {
+        const float4 *s0 = reinterpret_cast<const float4 *>(AF + (int64_t)(j + home0) * ldf + j);
+        const float4 *s1 = reinterpret_cast<const float4 *>(AF + (int64_t)(j + home1) * ldf + j);
 #pragma unroll
         for (int c = 0; c < NB; c += 4) {
-            float4 v = (c < nbp) ? src[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
-            a[c] = v.x; a[c + 1] = v.y; a[c + 2] = v.z; a[c + 3] = v.w;
+            const float4 v = (valid0 && c < nbp) ? s0[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float4 w = (valid1 && c < nbp) ? s1[c / 4] : make_float4(0.f, 0.f, 0.f, 0.f);
+            a0[c] = v.x; a0[c + 1] = v.y; a0[c + 2] = v.z; a0[c + 3] = v.w;
+            a1[c] = w.x; a1[c + 1] = w.y; a1[c + 2] = w.z; a1[c + 3] = w.w;
         }
 #pragma unroll
         for (int c = 0; c < NB; ++c)
-            if (c >= nbp) a[c] = 0.f;
-    } else {
-#pragma unroll
-        for (int c = 0; c < NB; ++c) a[c] = 0.f;
+            if (c >= nbp) a0[c] = a1[c] = 0.f;
     }
     cluster_sync_all();   // every CTA is running and its mbarriers are armed
     const unsigned long long deadline = globaltimer() + kWaitLimitNs;   // for all waits of this launch
@@ -204,42 +228,45 @@ __global__ void __launch_bounds__(T, 1)
 #pragma unroll 1
     for (int k = 0; k < nbp; ++k) {
         const int buf = k & 1;
-        // 1. warp candidate: largest |a_ik| over the rows that are not pivot
-        //    rows yet, ties to the lowest current position; staged as a record
-        const bool cand = valid && kp == nbp;
-        const unsigned key = cand ? __float_as_uint(fabsf(a[0])) : 0u;
+        // 1. candidate of the thread (its two rows), then of the warp: largest
+        //    |a_ik| over rows that are not pivot rows yet, ties to the lowest
+        //    current position; staged as a record
+        const bool c0 = valid0 && kp0 == nbp, c1 = valid1 && kp1 == nbp;
+        const unsigned k0 = c0 ? __float_as_uint(fabsf(a0[0])) : 0u;
+        const unsigned k1 = c1 ? __float_as_uint(fabsf(a1[0])) : 0u;
+        const bool use1 = c1 && (!c0 || k1 > k0 || (k1 == k0 && pos1 < pos0));
+        const bool tc = c0 || c1;
+        const unsigned key = use1 ? k1 : k0;
+        const int tpos = use1 ? pos1 : pos0;
         const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-        const int mpos = __reduce_min_sync(0xffffffffu, (cand && key == kmax) ? pos : INT_MAX);
+        const int mpos = __reduce_min_sync(0xffffffffu, (tc && key == kmax) ? tpos : INT_MAX);
         float *st = sm.stage[buf][warp];
-        if (cand && pos == mpos) {
-            float4 *s4 = reinterpret_cast<float4 *>(st);
-            s4[0] = make_float4(__uint_as_float(kmax), __int_as_float(mpos), (a[0] != 0.f) ? 1.0f / a[0] : 0.f, a[0]);
-#pragma unroll
-            for (int q = 0; q < 15; ++q)
-                s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
-            s4[16] = make_float4(a[61], a[62], a[63], 0.f);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // generic writes -> bulk copy
+        if (tc && tpos == mpos) {
+            if (use1)
+                stage_record(st, a1, kmax, mpos);
+            else
+                stage_record(st, a0, kmax, mpos);
         }
         if (lane == 0 && mpos == INT_MAX) {
             st[0] = 0.f;
             st[1] = __int_as_float(INT_MAX);
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         }
         __syncthreads();
-        // 2. the CTA's best record, pushed to every CTA of the cluster (one lane per destination)
-        if (warp == 0) {
+        // 2. the CTA's best record, pushed to every CTA of the cluster: chunk
+        //    i % 17 of it into CTA i / 17 for i = t, t + T, ... (st.async, counted
+        //    on the receiver's mbarrier)
+        {
             const unsigned wk = lane < NW ? __float_as_uint(sm.stage[buf][lane][0]) : 0u;
             const int wp = lane < NW ? __float_as_int(sm.stage[buf][lane][1]) : INT_MAX;
             const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
             const int bp = __reduce_min_sync(0xffffffffu, (wp != INT_MAX && wk == bk) ? wp : INT_MAX);
             const unsigned who = __ballot_sync(0xffffffffu, lane < NW && wp == bp);
             const int w = who ? __ffs(who) - 1 : 0;
-            if (lane < (int)csize) {
-                const unsigned rbar = map_cta(bar_addr + 8u * buf, (unsigned)lane);
-                const unsigned slot = recv_addr + (unsigned)((buf * kPanelMaxCluster + (int)crank) * kRec * 4);
-                bulk_to_cta(map_cta(slot, (unsigned)lane), smem_u32(sm.stage[buf][w]), kRec * 4, rbar);
-                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");   // the stage slot may be reused
+            for (int snd = t; snd < nsend; snd += T) {
+                const int dst = snd / kChunks, ch = snd % kChunks;
+                const float4 v = reinterpret_cast<const float4 *>(sm.stage[buf][w])[ch];
+                const unsigned slot = recv_addr + (unsigned)(((buf * kPanelMaxCluster + (int)crank) * kRec + 4 * ch) * 4);
+                st_async_v4(map_cta(slot, (unsigned)dst), v, map_cta(bar_addr + 8u * buf, (unsigned)dst));
             }
         }
         // 3. every warp waits (bounded) for the records of all CTAs of this step
@@ -272,60 +299,89 @@ __global__ void __launch_bounds__(T, 1)
             if (piv == 0.f && sm.zero_piv == 0) sm.zero_piv = j + k + 1;
         }
         // 5. interchange of positions k and ppos: labels only
-        if (cand && pos == ppos) {
-            pos = k;
-            kp = k;
-        } else if (pos == k) {
-            pos = ppos;
+        if (c0 && pos0 == ppos) {
+            pos0 = k;
+            kp0 = k;
+        } else if (pos0 == k) {
+            pos0 = ppos;
+        }
+        if (c1 && pos1 == ppos) {
+            pos1 = k;
+            kp1 = k;
+        } else if (pos1 == k) {
+            pos1 = ppos;
         }
         if (warp == 1) {
             Us[k * NB + lane] = u[3 + lane];
             Us[k * NB + lane + 32] = u[35 + lane];
         }
         // 6. scale column k (getf2: by the reciprocal, divide below the smallest
-        //    normal), update and shift the live part of the window
-        if (valid && kp == nbp) {
-            float l = a[0];
-            if (piv != 0.f) l = (fabsf(piv) >= FLT_MIN) ? l * r : l / piv;
-            Ls[k * T + t] = l;
-            const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
-            const int live = nbp - k;                                        // a[0..live-1] nonzero
+        //    normal) and update the live part of both windows.  A window that is
+        //    not updated any more (pivot row, or past the matrix) is shifted with
+        //    l = 0; its contents are never used again.
+        const bool u0 = valid0 && kp0 == nbp, u1 = valid1 && kp1 == nbp;
+        float l0 = 0.f, l1 = 0.f;
+        if (u0) {
+            l0 = a0[0];
+            if (piv != 0.f) l0 = (fabsf(piv) >= FLT_MIN) ? l0 * r : l0 / piv;
+            Ls[k * RPC + t] = l0;
+        }
+        if (u1) {
+            l1 = a1[0];
+            if (piv != 0.f) l1 = (fabsf(piv) >= FLT_MIN) ? l1 * r : l1 / piv;
+            Ls[k * RPC + T + t] = l1;
+        }
+        // No branches on the live width: past it, the windows and the staged
+        // record hold zeros (a value shifts left only from inside the live
+        // width), so the extra fmas change nothing that is used, and the 16
+        // loads of the pivot row can all be issued ahead of the fmas.
+        const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
 #pragma unroll
-            for (int q = 0; q < NB / 4; ++q) {
-                if (4 * q < live) {
-                    const float4 w = us[q];
-                    a[4 * q + 0] = fmaf(-l, w.x, a[4 * q + 1]);
-                    a[4 * q + 1] = fmaf(-l, w.y, a[4 * q + 2]);
-                    a[4 * q + 2] = fmaf(-l, w.z, a[4 * q + 3]);
-                    a[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l, w.w, a[4 * q + 4]) : 0.f;
-                }
-            }
+        for (int q = 0; q < NB / 4; ++q) {
+            const float4 w = us[q];
+            a0[4 * q + 0] = fmaf(-l0, w.x, a0[4 * q + 1]);
+            a0[4 * q + 1] = fmaf(-l0, w.y, a0[4 * q + 2]);
+            a0[4 * q + 2] = fmaf(-l0, w.z, a0[4 * q + 3]);
+            a0[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l0, w.w, a0[4 * q + 4]) : 0.f;
+            a1[4 * q + 0] = fmaf(-l1, w.x, a1[4 * q + 1]);
+            a1[4 * q + 1] = fmaf(-l1, w.y, a1[4 * q + 2]);
+            a1[4 * q + 2] = fmaf(-l1, w.z, a1[4 * q + 3]);
+            a1[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l1, w.w, a1[4 * q + 4]) : 0.f;
         }
     }
     // net permutation of the panel: position j + pos now holds the row that started at j + home
-    int porg = 0;
-    const bool moved = valid && pos != home;
-    if (moved) {
-        int e = atomicAdd(&swap_list[0], 1);
-        swap_list[1 + 2 * e] = j + pos;
-        swap_list[2 + 2 * e] = j + home;
-        porg = perm[j + home];
+    int porg0 = 0, porg1 = 0;
+    const bool moved0 = valid0 && pos0 != home0, moved1 = valid1 && pos1 != home1;
+    if (moved0) {
+        const int e = atomicAdd(&swap_list[0], 1);
+        swap_list[1 + 2 * e] = j + pos0;
+        swap_list[2 + 2 * e] = j + home0;
+        porg0 = perm[j + home0];
+    }
+    if (moved1) {
+        const int e = atomicAdd(&swap_list[0], 1);
+        swap_list[1 + 2 * e] = j + pos1;
+        swap_list[2 + 2 * e] = j + home1;
+        porg1 = perm[j + home1];
     }
     if (crank == 0) {
         for (int k = t; k < nbp; k += T) ipiv[j + k] = sm.piv_log[k];
         if (t == 0 && sm.zero_piv) atomicMin(&dev->info, sm.zero_piv);
     }
     cluster_sync_all();   // every perm read of the cluster is done
-    if (moved) perm[j + pos] = porg;
-    if (valid) {
-        // the row at its final position: multipliers of steps < kp, then the U part staged at step kp
+    if (moved0) perm[j + pos0] = porg0;
+    if (moved1) perm[j + pos1] = porg1;
 #pragma unroll
-        for (int c = 0; c < NB; ++c) a[c] = (c < kp) ? Ls[c * T + t] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
+    for (int h = 0; h < 2; ++h) {
+        const bool valid = h ? valid1 : valid0;
+        if (!valid) continue;
+        const int pos = h ? pos1 : pos0, kp = h ? kp1 : kp0;
+        final_row(a0, Ls, t + h * T, Us, kp, nbp);
         float4 *dst = reinterpret_cast<float4 *>(AF + (int64_t)(j + pos) * ldf + j);
 #pragma unroll
         for (int c = 0; c < NB; c += 4)
-            if (c < nbp) dst[c / 4] = make_float4(a[c], a[c + 1], a[c + 2], a[c + 3]);
-        if (has_trailing && Aop != nullptr && pos >= NB) store_op_row(Aop, pos - NB, a, tf);
+            if (c < nbp) dst[c / 4] = make_float4(a0[c], a0[c + 1], a0[c + 2], a0[c + 3]);
+        if (has_trailing && Aop != nullptr && pos >= NB) store_op_row(Aop, pos - NB, a0, tf);
     }
     cluster_sync_all();   // no CTA leaves while its shared memory may be written
 }
@@ -396,7 +452,7 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
         attr_done = true;
     }
     int M = n - j;
-    int C = (M + T - 1) / T;
+    int C = (M + RPC - 1) / RPC;
     if (C > kPanelMaxCluster) return cudaErrorInvalidValue;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
