@@ -489,6 +489,48 @@ def main():
     roof["share_of_step"] = dom_ms / total_prof
     roof["avg_launch_ms"] = avg_ms
 
+    # --- a roofline line for every kernel kind of the step (the dominant one is the latency-bound panel)
+    def dgemm_rate():
+        G = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+        torch.matmul(G, G)
+        torch.cuda.synchronize()
+        best = None
+        for _ in range(3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            torch.matmul(G, G)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            t_ = e0.elapsed_time(e1)
+            best = t_ if best is None else min(best, t_)
+        return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+    fp64_tflops = dgemm_rate()
+    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
+    n_iter = rep32.iters
+    kr = {}
+
+    def line(kind, prof, steps, bound, work, peak, unit, note):
+        if kind not in prof:
+            return
+        ms_, calls = prof[kind]
+        rate = work / (ms_ / steps * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        kr[kind] = {"bound": bound, "achieved": rate, "peak": peak, "unit": unit, "frac": rate / peak,
+                    "ms_per_step": ms_ / steps, "calls_per_step": calls / steps, "work": note}
+
+    gemm_flops = sum(2 * (n - j - nb) ** 2 * nb for j in range(0, n - nb, nb))
+    line("gemm_simt", prof32, args.steps, "alu", gemm_flops, fp32_peak_tflops, "TFLOP/s",
+         "2 m^2 nb flops per block step, binary32 FMA pipe (unit counts x 2070 MHz)")
+    tc_steps = max(3, args.steps // 2)
+    line("gemm_tc", prof_tc, tc_steps, "tensor", gemm_flops, tf32_peak, "TFLOP/s",
+         "2 m^2 nb flops per block step, TF32 peak = measured bf16 x 1.1/2.25")
+    line("residual", prof32, args.steps, "alu", 2.0 * n * n * n_iter, fp64_tflops, "TFLOP/s",
+         "2 N^2 flops per residual on the binary64 pipe; peak = measured binary64 GEMM rate")
+    line("trsv_pair", prof32, args.steps, "hbm", 4.0 * n * n * n_iter, peaks["hbm_gbs"], "GB/s",
+         "N^2 x 4 B of factors (L and U) per correction solve")
+    line("cast", prof32, args.steps, "hbm", 12.0 * n * n, peaks["hbm_gbs"], "GB/s",
+         "N^2 x (8 B read + 4 B written)")
+
     # --- LU rate of the headline path (2 N^3 / 3 flops over factor time = cast + LU kernels)
     lu_kinds = ("cast", "iota", "panel", "laswp", "trsm", "gemm_simt", "diag_inv")
     lu_ms = sum(prof32[k][0] for k in lu_kinds if k in prof32) / args.steps
@@ -550,6 +592,8 @@ def main():
                                                     for k, v in sorted(prof_tc.items())}},
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof32.items())},
         "roofline": roof,
+        "kernel_rooflines": kr,
+        "fp64_gemm_tflops": fp64_tflops,
         "e2e": e2e,
         "cpu_baseline": cpu,
         "gpu_launches": launches,
