@@ -88,6 +88,55 @@ __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n
     }
 }
 
+// The same update for a narrow column range (<= 64 columns: the next block
+// column of the lookahead, on the critical path): 64 x 64 tiles, so twice the
+// CTAs of the wide kernel for the same rows; thread (ty, tx) owns rows
+// 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3, fmaf chains from C in
+// ascending k.
+constexpr int NT = 64;
+__global__ void __launch_bounds__(256) k_gemm_simt_narrow(float *AF, int64_t ldf, int n, int j, int cb, int ce) {
+    __shared__ __align__(16) float As[NB][NT + 4];   // As[k][i] = L21[i][k]
+    __shared__ __align__(16) float Bs[NB][NT + 4];   // Bs[k][c] = U12[k][c]
+    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
+    const int i0 = j + NB + blockIdx.x * NT;
+    for (int e = t; e < NT * NB / 4; e += 256) {
+        const int row = e >> 4, kq = (e & 15) * 4;
+        const int i = i0 + row;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + kq);
+        As[kq + 0][row] = v.x; As[kq + 1][row] = v.y; As[kq + 2][row] = v.z; As[kq + 3][row] = v.w;
+        const int m = e >> 4, cq = (e & 15) * 4, c = cb + cq;
+        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (c < ce) w = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + m) * ldf + c);
+        *reinterpret_cast<float4 *>(&Bs[m][cq]) = w;
+    }
+    float acc[4][4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r, c = cb + tx * 4;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n && c < ce) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c);
+        acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
+    }
+    __syncthreads();
+#pragma unroll 8
+    for (int k = 0; k < NB; ++k) {
+        const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
+        const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
+        const float ar[4] = {a.x, a.y, a.z, a.w}, br[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+        for (int r = 0; r < 4; ++r)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(-ar[r], br[q], acc[r][q]);
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r, c = cb + tx * 4;
+        if (i < n && c < ce)
+            *reinterpret_cast<float4 *>(AF + (int64_t)i * ldf + c) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
+    }
+}
+
 }  // namespace
 
 // max_ctas > 0: share the GPU with a concurrent panel -- the update runs as
@@ -99,6 +148,10 @@ cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int c
     if (m <= 0 || ce <= cb) return cudaSuccess;
     const int tiles = ((m + BM - 1) / BM) * ((ce - cb + BN - 1) / BN);
     count_launch();
+    if (max_ctas <= 0 && ce - cb <= NT) {
+        k_gemm_simt_narrow<<<(m + NT - 1) / NT, 256, 0, s>>>(AF, ldf, n, j, cb, ce);
+        return cudaGetLastError();
+    }
     if (max_ctas <= 0) {
         k_gemm_simt<<<tiles, 256, 0, s>>>(AF, ldf, n, j, cb, ce);
         return cudaGetLastError();

@@ -408,30 +408,73 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int c
     for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
 }
 
-// U12 = L11^{-1} A12 for the block row j..j+NB and columns j+NB..n.  One
-// thread per column, its NB values in registers, L11 in shared memory; each
-// u_kc is the fmaf chain over m < k in ascending order.  For tensor-core
+// U12 = L11^{-1} A12 for the block row j..j+NB and the columns [cb, ce).  The
+// solve is a 63-step dependency chain per column, so it is spread thin for
+// latency: four threads per column, each holding 16 rows; column-oriented:
+// for m ascending the owner of row m broadcasts the final u_m (shuffle) and
+// the rows below take fmaf(-l_km, u_m, u_k), so every entry is the fmaf chain
+// over m < k in ascending order, as in the unblocked LU.  For tensor-core
 // updates the rounded values rTF(u_mc) are also written to Bop (row c).
-__global__ void __launch_bounds__(128) k_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
-                                              void *Bop) {
-    __shared__ float L[NB][NB + 1];
+constexpr int kNarrowCols = 64;   // columns per CTA (4 threads each)
+__global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
+                                                     void *Bop) {
+    __shared__ __align__(16) float Lt[NB][NB + 4];    // Lt[m][k] = L11[k][m]
     for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        int r = e / NB, m = e % NB;
-        L[r][m] = AF[(int64_t)(j + r) * ldf + j + m];
+        const int k = e / NB, m = e % NB;
+        Lt[m][k] = AF[(int64_t)(j + k) * ldf + j + m];
     }
     __syncthreads();
-    const int c = cb + blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= ce) return;
-    float u[NB];
+    const int t = threadIdx.x, lane = t & 31, q = t & 3;
+    const int c = cb + blockIdx.x * kNarrowCols + (t >> 2);
+    const bool on = c < ce;
+    float u[16];
 #pragma unroll
-    for (int m = 0; m < NB; ++m) u[m] = AF[(int64_t)(j + m) * ldf + c];
+    for (int r = 0; r < 16; ++r) u[r] = on ? AF[(int64_t)(j + q * 16 + r) * ldf + c] : 0.f;
 #pragma unroll
-    for (int k = 1; k < NB; ++k)
+    for (int m = 0; m < NB - 1; ++m) {
+        const float um = __shfl_sync(0xffffffffu, u[m % 16], (lane & ~3) | (m / 16));
+        const float4 *l4 = reinterpret_cast<const float4 *>(&Lt[m][q * 16]);
 #pragma unroll
-        for (int m = 0; m < k; ++m) u[k] = fmaf(-L[k][m], u[m], u[k]);
+        for (int r4 = 0; r4 < 4; ++r4) {
+            const float4 l = l4[r4];
+            const int k = q * 16 + 4 * r4;
+            if (k + 0 > m) u[4 * r4 + 0] = fmaf(-l.x, um, u[4 * r4 + 0]);
+            if (k + 1 > m) u[4 * r4 + 1] = fmaf(-l.y, um, u[4 * r4 + 1]);
+            if (k + 2 > m) u[4 * r4 + 2] = fmaf(-l.z, um, u[4 * r4 + 2]);
+            if (k + 3 > m) u[4 * r4 + 3] = fmaf(-l.w, um, u[4 * r4 + 3]);
+        }
+    }
+    if (!on) return;
 #pragma unroll
-    for (int m = 1; m < NB; ++m) AF[(int64_t)(j + m) * ldf + c] = u[m];
-    if (Bop != nullptr) store_op_row(Bop, c - (j + NB), u, tf);
+    for (int r = 0; r < 16; ++r)
+        if (q * 16 + r > 0) AF[(int64_t)(j + q * 16 + r) * ldf + c] = u[r];
+    if (Bop == nullptr) return;
+    const int64_t row = c - (j + NB);
+    if (tf == IR_TF32) {
+        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(Bop) + row * NB + q * 16);
+#pragma unroll
+        for (int r = 0; r < 16; r += 4)
+            dst[r / 4] = make_float4(round_tf(u[r], tf), round_tf(u[r + 1], tf), round_tf(u[r + 2], tf),
+                                     round_tf(u[r + 3], tf));
+    } else if (tf == IR_BF16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Bop) + row * NB + q * 16);
+#pragma unroll
+        for (int r = 0; r < 16; r += 8) {
+            __nv_bfloat162 p2[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) p2[h] = __floats2bfloat162_rn(u[r + 2 * h], u[r + 2 * h + 1]);
+            dst[r / 8] = *reinterpret_cast<uint4 *>(p2);
+        }
+    } else if (tf == IR_F16) {
+        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__half *>(Bop) + row * NB + q * 16);
+#pragma unroll
+        for (int r = 0; r < 16; r += 8) {
+            __half2 p2[4];
+#pragma unroll
+            for (int h = 0; h < 4; ++h) p2[h] = __floats2half2_rn(u[r + 2 * h], u[r + 2 * h + 1]);
+            dst[r / 8] = *reinterpret_cast<uint4 *>(p2);
+        }
+    }
 }
 
 __global__ void k_iota(int n, int32_t *perm) {
@@ -486,7 +529,8 @@ cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype 
     const int ncols = ce - cb;
     if (ncols <= 0) return cudaSuccess;
     count_launch();
-    k_trsm<<<(ncols + 127) / 128, 128, 0, s>>>(AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
+    k_trsm_narrow<<<(ncols + kNarrowCols - 1) / kNarrowCols, 4 * kNarrowCols, 0, s>>>(
+        AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
     return cudaGetLastError();
 }
 
