@@ -130,6 +130,7 @@ void free_fact(ir_fact *f) {
     cudaFree(f->Linv);
     cudaFree(f->Uinv);
     cudaFree(f->tags);
+    cudaFree(f->blk_subst);
     cudaFree(f->x);
     cudaFree(f->r);
     cudaFree(f->dev);
@@ -172,6 +173,7 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     AL(f->Linv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
     AL(f->Uinv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
     AL(f->tags, (size_t)2 * nblk * kTrsvB * sizeof(unsigned long long));
+    AL(f->blk_subst, (size_t)2 * nblk * sizeof(int32_t));
     AL(f->x, nn * sizeof(double));
     AL(f->r, nn * sizeof(double));
     AL(f->dev, sizeof(DevScalars));
@@ -308,7 +310,7 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
         }
     }
     if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
-    RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, s));
+    RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, f->blk_subst, s));
     return IR_OK;
 }
 
@@ -603,8 +605,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     while (status < 0) {
         f->epoch += 1;
         CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, sizeof(unsigned long long), s));
-        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->perm, f->r, nullptr, nullptr,
-                            f->x, f->tags, f->epoch, f->dev, s));
+        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
+                                         nullptr, nullptr, f->x, f->tags, f->epoch, f->dev, s));
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
                            f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
         st = read_dev(f, s);
@@ -633,7 +635,7 @@ ir_status ir_lu_solve(ir_fact *f, const float *v, float *d, void *stream) {
     if (f->n == 0) return IR_OK;
     CK(cudaSetDevice(f->ctx->device));
     f->epoch += 1;
-    CK(launch_trsv_pair(f->AF, f->ldf, (int)f->n, f->Linv, f->Uinv, f->perm, nullptr, v, d, nullptr,
+    CK(launch_trsv_pair(f->AF, f->ldf, (int)f->n, f->Linv, f->Uinv, f->blk_subst, f->perm, nullptr, v, d, nullptr,
                         f->tags, f->epoch, f->dev, (cudaStream_t)stream));
     return IR_OK;
 }

@@ -6,7 +6,7 @@
 //          (row interchanges move contiguous rows; a panel row is contiguous)
 //   Aop    rTF(L21) of the current block step, row-major (K contiguous), TF dtype
 //   Bop    rTF(U12)^T of the current block step, row-major (K contiguous)
-//   Linv/Uinv  inverses of the 64x64 diagonal blocks of L and U (row-major)
+//   Linv/Uinv  inverses of the 128x128 diagonal blocks of L and U (row-major)
 //   x      binary64 iterate (TR), r binary64 residual, y binary32 solve vector
 //   dev    small block of device scalars (norms as ordered bit patterns, flags)
 #pragma once
@@ -17,7 +17,7 @@
 
 namespace ir {
 
-constexpr int kTrsvB = 64;        // row block of the triangular solves
+constexpr int kTrsvB = 128;       // row block of the triangular solves
 constexpr int kPanelNB = 64;      // panel width = outer block size
 constexpr int kPanelRows = 512;   // panel rows per CTA (two per thread)
 constexpr int kPanelThreads = 256;
@@ -66,7 +66,8 @@ struct ir_fact {
     cudaStream_t la_stream;  // low-priority stream of the lookahead schedule
     cudaEvent_t *la_events;  // fork/join events of the lookahead schedule
     int la_nevents;
-    float *Linv, *Uinv;      // diagonal-block inverses, nblk x 64 x 64
+    float *Linv, *Uinv;      // diagonal-block inverses, nblk x B x B (B = kTrsvB)
+    int32_t *blk_subst;      // 2 x nblk: 1 = solve this diagonal block by substitution (ill-conditioned)
     unsigned long long *tags;  // 2 x nblk*64 tagged solve values (epoch << 32 | bits)
     unsigned epoch;            // tag of the latest solve
     double *x, *r;           // binary64 iterate and residual
@@ -111,9 +112,9 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb,
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
-                            cudaStream_t s);
+                            int32_t *blk_subst, cudaStream_t s);
 cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *Linv,
-                             const float *Uinv, const int32_t *perm, const double *r,
+                             const float *Uinv, const int32_t *blk_subst, const int32_t *perm, const double *r,
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
                              cudaStream_t s);

@@ -2,28 +2,39 @@
 // vdlow/promotevd of Sec. 5.3 for the scaling by ||r||).
 //
 // Blocked, synchronisation-free triangular solves: the rows are cut into
-// blocks of B = 64; CTA b (taken in order through a ticket counter, so every
+// blocks of B = 128; CTA b (taken in order through a ticket counter, so every
 // block it waits on has already started) accumulates the products of its
 // off-diagonal blocks with the solution blocks as they appear, then applies
-// the inverse of its diagonal block (computed once after the factorization)
-// and publishes its 64 values.  A published value is a 64-bit word
+// its diagonal block -- by the inverse computed once after the factorization,
+// or by substitution (one warp, column sweep) when the block's condition
+// number ||T|| ||T^{-1}|| exceeds kSubstKappa, where an explicit inverse would
+// lose too much accuracy -- and publishes its 128 values.  The off-diagonal
+// sums are compensated (see acc_pair).  A published value is a 64-bit word
 // (epoch << 32 | binary32 bits), so a reader learns "ready" and the value in
-// one load; waits are bounded and a timeout is reported, never hung.
+// one load; waits are bounded and a timeout is reported, never hung.  The
+// solve is a chain of N / B dependent block steps, so the block is large:
+// 512 threads, warp w owns rows 8w .. 8w+7 of the block and lane l columns
+// l, l+32, l+64, l+96 of every 128-column tile.
 #include "ir_internal.cuh"
 
 namespace ir {
 namespace {
 
 constexpr int B = kTrsvB;
-constexpr int TT = 256;          // threads per solve CTA (8 warps x 8 rows)
+constexpr int TT = 512;          // threads per solve CTA (16 warps x 8 rows)
+constexpr int CPL = B / 32;      // columns of a tile per lane
+static_assert(B == 128 && TT == 32 * (B / 8), "warp w owns rows 8w..8w+7 of the block");
 
 // Inverse of the diagonal blocks: blockIdx.y = 0 -> L (unit lower), 1 -> U.
 // Thread t computes column t of the inverse by substitution (binary32).
 // Rows/columns beyond n are treated as identity.
+constexpr size_t kDiagSmem = 2 * sizeof(float) * B * (B + 1);
+constexpr float kSubstKappa = 1e5f;   // blocks above this condition number are solved by substitution
 __global__ void __launch_bounds__(B) k_diag_inv(const float *AF, int64_t ldf, int n, float *Linv,
-                                                 float *Uinv) {
-    __shared__ float Tb[B][B + 1];
-    __shared__ float X[B][B + 1];
+                                                 float *Uinv, int32_t *blk_subst) {
+    extern __shared__ float dsm[];
+    float(*Tb)[B + 1] = reinterpret_cast<float(*)[B + 1]>(dsm);
+    float(*X)[B + 1] = reinterpret_cast<float(*)[B + 1]>(dsm + B * (B + 1));
     const int b = blockIdx.x, upper = blockIdx.y, t = threadIdx.x;
     const int r0 = b * B;
     for (int i = 0; i < B; ++i) {
@@ -60,6 +71,33 @@ __global__ void __launch_bounds__(B) k_diag_inv(const float *AF, int64_t ldf, in
     __syncthreads();
     float *dst = (upper ? Uinv : Linv) + (int64_t)b * B * B;
     for (int i = 0; i < B; ++i) dst[i * B + t] = X[i][t];
+    // kappa_inf of the triangle: max row sum of |T| times max row sum of |T^{-1}|
+    float tr = 0.f, xr = 0.f;
+    for (int m = 0; m < B; ++m) {
+        const float tv = upper ? (m >= t ? Tb[t][m] : 0.f) : (m < t ? Tb[t][m] : (m == t ? 1.f : 0.f));
+        tr += fabsf(tv);
+        xr += fabsf(X[t][m]);
+    }
+    __shared__ float red[2][B / 32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        tr = fmaxf(tr, __shfl_xor_sync(0xffffffffu, tr, o));
+        xr = fmaxf(xr, __shfl_xor_sync(0xffffffffu, xr, o));
+    }
+    if ((t & 31) == 0) {
+        red[0][t >> 5] = tr;
+        red[1][t >> 5] = xr;
+    }
+    __syncthreads();
+    if (t == 0) {
+        float tm = 0.f, xm = 0.f;
+        for (int w = 0; w < B / 32; ++w) {
+            tm = fmaxf(tm, red[0][w]);
+            xm = fmaxf(xm, red[1][w]);
+        }
+        const float kappa = tm * xm;
+        blk_subst[upper * gridDim.x + b] = !(kappa <= kSubstKappa);   // NaN: substitution too
+    }
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
@@ -71,16 +109,16 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Wait (bounded, with back-off) until the word carries `tag`; return its value.
+// Wait (bounded, with a short back-off) until the word carries `tag`; return its value.
 __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsigned tag,
                                              int *timeout) {
     unsigned long long v = ld_relaxed_u64(p);
     if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
     const unsigned long long t0 = globaltimer();
-    unsigned ns = 32;
+    unsigned ns = 16;
     while (true) {
         __nanosleep(ns);
-        if (ns < 256) ns <<= 1;
+        if (ns < 64) ns <<= 1;
         v = ld_relaxed_u64(p);
         if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
         if (*reinterpret_cast<volatile int *>(timeout) || globaltimer() - t0 > kWaitLimitNs) {
@@ -88,6 +126,27 @@ __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsign
             return 0.f;
         }
     }
+}
+
+// The 128 published values of one block, read by one warp: the four words of
+// a lane are loaded together, and only the ones not yet carrying `tag` are
+// polled again (bounded, with a short back-off).
+__device__ __forceinline__ void poll_block(const unsigned long long *p, unsigned tag, float *ys, int lane,
+                                           int *timeout) {
+    unsigned long long v[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) v[c] = ld_relaxed_u64(p + lane + 32 * c);
+    bool ready = true;
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) ready &= ((unsigned)(v[c] >> 32) == tag);
+    if (!ready) {
+#pragma unroll
+        for (int c = 0; c < CPL; ++c)
+            if ((unsigned)(v[c] >> 32) != tag)
+                v[c] = ((unsigned long long)tag << 32) | __float_as_uint(poll_tagged(p + lane + 32 * c, tag, timeout));
+    }
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) ys[lane + 32 * c] = __uint_as_float((unsigned)v[c]);
 }
 
 // Sum of 8 per-lane values over the 32 lanes of a warp in 9 shuffles
@@ -123,73 +182,212 @@ __device__ __forceinline__ int reduce8_row(int lane) {
     return ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
 }
 
-// Prefetch of one 64x64 off-diagonal tile slice: warp w rows 8w..8w+7,
-// lane l columns l and l+32 of block column bj.
+// Compensated (double-binary32) accumulation of the off-diagonal products.
+// A triangular solve of an ill-conditioned factor cancels heavily, and a row
+// sum rounded at every step relative to its partial magnitude would carry an
+// error proportional to |sum| into the (much smaller) result.  Each lane adds
+// the sum of its 4 products of a tile to a pair (hi, lo) with TwoSum (Knuth),
+// the pairs of a row are reduced the same way, and the right-hand side is
+// subtracted before the single final rounding.
+// (The _rn intrinsics keep the compiler from contracting these steps into fmas.)
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void acc_pair(float &hi, float &lo, float h2, float l2) {
+    float s, e;
+    two_sum(hi, h2, s, e);
+    hi = s;
+    lo = __fadd_rn(lo, __fadd_rn(e, l2));
+}
+
+// reduce8 for (hi, lo) pairs: the same recursive halving, each addition compensated.
+__device__ __forceinline__ void reduce8_pair(float (&h)[8], float (&l)[8], int lane, float &ho, float &lo_out) {
+    const bool h16 = lane & 16, h8 = lane & 8, h4 = lane & 4;
+    float ah[4], al[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float sh = h16 ? h[q] : h[q + 4], sl = h16 ? l[q] : l[q + 4];
+        ah[q] = h16 ? h[q + 4] : h[q];
+        al[q] = h16 ? l[q + 4] : l[q];
+        acc_pair(ah[q], al[q], __shfl_xor_sync(0xffffffffu, sh, 16), __shfl_xor_sync(0xffffffffu, sl, 16));
+    }
+    float bh[2], bl[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float sh = h8 ? ah[q] : ah[q + 2], sl = h8 ? al[q] : al[q + 2];
+        bh[q] = h8 ? ah[q + 2] : ah[q];
+        bl[q] = h8 ? al[q + 2] : al[q];
+        acc_pair(bh[q], bl[q], __shfl_xor_sync(0xffffffffu, sh, 8), __shfl_xor_sync(0xffffffffu, sl, 8));
+    }
+    float ch, cl;
+    {
+        const float sh = h4 ? bh[0] : bh[1], sl = h4 ? bl[0] : bl[1];
+        ch = h4 ? bh[1] : bh[0];
+        cl = h4 ? bl[1] : bl[0];
+        acc_pair(ch, cl, __shfl_xor_sync(0xffffffffu, sh, 4), __shfl_xor_sync(0xffffffffu, sl, 4));
+    }
+    acc_pair(ch, cl, __shfl_xor_sync(0xffffffffu, ch, 2), __shfl_xor_sync(0xffffffffu, cl, 2));
+    acc_pair(ch, cl, __shfl_xor_sync(0xffffffffu, ch, 1), __shfl_xor_sync(0xffffffffu, cl, 1));
+    ho = ch;
+    lo_out = cl;
+}
+
+// sv_i <- fl32(sv_i - (hi + lo)), the subtraction itself compensated.
+__device__ __forceinline__ float sub_pair(float v, float hi, float lo) {
+    float s, e;
+    two_sum(v, -hi, s, e);
+    return __fadd_rn(s, __fsub_rn(e, lo));
+}
+
+// One 128x128 off-diagonal tile slice: warp w rows 8w..8w+7, lane l columns
+// l + 32c (c < 4) of block column bj.
 __device__ __forceinline__ void load_tile(const float *AF, int64_t ldf, int n, int row0, int bj,
-                                          int lane, float (&la)[8], float (&lb)[8]) {
-    const int c = bj * B + lane;
+                                          int lane, float (&a)[8][CPL]) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const int i = row0 + q;
-        la[q] = (i < n && c < n) ? __ldg(AF + (int64_t)i * ldf + c) : 0.f;
-        lb[q] = (i < n && c + 32 < n) ? __ldg(AF + (int64_t)i * ldf + c + 32) : 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) {
+            const int col = bj * B + lane + 32 * c;
+            a[q][c] = (i < n && col < n) ? __ldg(AF + (int64_t)i * ldf + col) : 0.f;
+        }
     }
 }
 
-// Accumulate the off-diagonal products of block bi: p[q] += sum_j A[row0+q][j] y_j
-// over the predecessor blocks, in order; the next tile is in flight while the
-// current one waits for its published values.
+// Accumulate the off-diagonal products of block bi: (p[q], pl[q]) += sum_j
+// A[row0+q][j] y_j over the predecessor blocks, in order (compensated); the
+// next tile is in flight while the current one waits for its published values.
 template <bool LOWER>
 __device__ __forceinline__ void offdiag(const float *AF, int64_t ldf, int n, int nblk, int bi,
                                         const unsigned long long *tags, unsigned tag, float *ys,
-                                        int *timeout, float (&p)[8]) {
+                                        int *timeout, float (&p)[8], float (&pl)[8]) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int row0 = bi * B + warp * 8;
     const int npred = LOWER ? bi : (nblk - 1 - bi);
-    float la[8], lb[8], na[8], nb2[8];
-    if (npred > 0) load_tile(AF, ldf, n, row0, LOWER ? 0 : nblk - 1, lane, la, lb);
+    float la[8][CPL], na[8][CPL];
+    if (npred > 0) load_tile(AF, ldf, n, row0, LOWER ? 0 : nblk - 1, lane, la);
     for (int it = 0; it < npred; ++it) {
         const int bj = LOWER ? it : (nblk - 1 - it);
-        if (it + 1 < npred) load_tile(AF, ldf, n, row0, LOWER ? bj + 1 : bj - 1, lane, na, nb2);
-        if (warp == 0) {
-            ys[lane] = poll_tagged(tags + bj * B + lane, tag, timeout);
-            ys[lane + 32] = poll_tagged(tags + bj * B + lane + 32, tag, timeout);
-        }
+        if (it + 1 < npred) load_tile(AF, ldf, n, row0, LOWER ? bj + 1 : bj - 1, lane, na);
+        if (warp == 0) poll_block(tags + bj * B, tag, ys, lane, timeout);
         __syncthreads();
-        const float y0 = ys[lane], y1 = ys[lane + 32];
+        float y[CPL];
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) y[c] = ys[lane + 32 * c];
+        // the tile's 4 products of a lane in binary32, their sum added compensated
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
-            p[q] = fmaf(la[q], y0, p[q]);
-            p[q] = fmaf(lb[q], y1, p[q]);
+            float tp = __fmul_rn(la[q][0], y[0]);
+#pragma unroll
+            for (int c = 1; c < CPL; ++c) tp = fmaf(la[q][c], y[c], tp);
+            acc_pair(p[q], pl[q], tp, 0.f);
         }
         __syncthreads();                       // ys consumed before the next fetch
 #pragma unroll
-        for (int q = 0; q < 8; ++q) { la[q] = na[q]; lb[q] = nb2[q]; }
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) la[q][c] = na[q][c];
+    }
+}
+
+// Rows 8w..8w+7 of the diagonal-block inverse times sv: lane l takes columns
+// l + 32c; the 8 row sums end in lanes with (l & 3) == 0 (reduce8).
+__device__ __forceinline__ float diag_apply(const float *Ds, const float *sv, int warp, int lane) {
+    float acc[8];
+    float s[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) s[c] = sv[lane + 32 * c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        float a = 0.f;
+#pragma unroll
+        for (int c = 0; c < CPL; ++c) a = fmaf(Ds[(warp * 8 + q) * B + lane + 32 * c], s[c], a);
+        acc[q] = a;
+    }
+    return reduce8(acc, lane);
+}
+
+// The diagonal block solved by substitution in place on sv (one warp, lane l
+// rows l + 32r): Dt[j][i] = T[i][j] (row stride B + 1).  Lower: unit
+// diagonal, columns ascending; upper: columns descending, each diagonal
+// entry divided before its column is applied.
+template <bool LOWER>
+__device__ __forceinline__ void diag_subst(const float *Dt, float *sv, int lane) {
+    float v[CPL];
+#pragma unroll
+    for (int r = 0; r < CPL; ++r) v[r] = sv[lane + 32 * r];
+    // j = 32 jr + jl: jr is unrolled, so v[jr] stays a register
+    if (LOWER) {
+#pragma unroll
+        for (int jr = 0; jr < CPL; ++jr) {
+#pragma unroll 4
+            for (int jl = 0; jl < 32; ++jl) {
+                const int j = 32 * jr + jl;
+                const float vj = __shfl_sync(0xffffffffu, v[jr], jl);
+#pragma unroll
+                for (int r = 0; r < CPL; ++r)
+                    if (r >= jr && lane + 32 * r > j) v[r] = fmaf(-Dt[j * (B + 1) + lane + 32 * r], vj, v[r]);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int jr = CPL - 1; jr >= 0; --jr) {
+#pragma unroll 4
+            for (int jl = 31; jl >= 0; --jl) {
+                const int j = 32 * jr + jl;
+                if (lane == jl) v[jr] = v[jr] / Dt[j * (B + 1) + j];
+                const float vj = __shfl_sync(0xffffffffu, v[jr], jl);
+#pragma unroll
+                for (int r = 0; r < CPL; ++r)
+                    if (r <= jr && lane + 32 * r < j) v[r] = fmaf(-Dt[j * (B + 1) + lane + 32 * r], vj, v[r]);
+            }
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < CPL; ++r) sv[lane + 32 * r] = v[r];
+}
+
+// Shared-memory staging of the diagonal block: the inverse (row-major, B x B)
+// or, for a block solved by substitution, the triangle transposed (stride
+// B + 1; identity past row n).
+template <bool LOWER>
+__device__ __forceinline__ void stage_diag(const float *AF, int64_t ldf, int n, int r0, const float *inv,
+                                           bool subst, float *Ds) {
+    const int t = threadIdx.x;
+    if (!subst) {
+        const float4 *src = reinterpret_cast<const float4 *>(inv);
+        for (int e = t; e < B * B / 4; e += TT) reinterpret_cast<float4 *>(Ds)[e] = __ldg(src + e);
+    } else {
+        for (int e = t; e < B * B; e += TT) {
+            const int i = e / B, j = e % B, gi = r0 + i, gj = r0 + j;
+            float v = (i == j) ? 1.f : 0.f;
+            if (gi < n && gj < n && (LOWER ? j < i : j >= i)) v = __ldg(AF + (int64_t)gi * ldf + gj);
+            Ds[j * (B + 1) + i] = v;
+        }
     }
 }
 
 // mode 0: v = fl32(r[perm[i]] / ||r||) (refinement step); mode 1: v = vin[perm[i]].
 // Publishes tagged y for the upper solve.
-__global__ void __launch_bounds__(TT) k_trsv_lower(const float *AF, int64_t ldf, int n, int nblk,
-                                                   const float *Linv, const int32_t *perm,
-                                                   const double *r, const float *vin, int mode,
-                                                   unsigned long long *ytag, unsigned tag,
-                                                   DevScalars *dev) {
+__global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t ldf, int n, int nblk,
+                                                      const float *Linv, const int32_t *blk_subst,
+                                                      const int32_t *perm, const double *r, const float *vin,
+                                                      int mode, unsigned long long *ytag, unsigned tag,
+                                                      DevScalars *dev) {
+    extern __shared__ __align__(16) float tsm[];
+    float *Ds = tsm;                 // this block's diagonal inverse, or its transposed triangle
+    float *sv = Ds + B * (B + 1);    // right-hand side of the block, then its solution
+    float *ys = sv + B;              // published values of the predecessor being applied
     __shared__ int s_bi;
-    __shared__ float sv[B], ys[B];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) s_bi = (int)atomicAdd(&dev->ticket[0], 1u);
     __syncthreads();
     const int bi = s_bi;
     const int r0 = bi * B;
-    // diagonal-block inverse rows of this warp, and this block's right-hand side
-    const float *Li = Linv + (int64_t)bi * B * B;
-    float da[8], db[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        da[q] = __ldg(Li + (warp * 8 + q) * B + lane);
-        db[q] = __ldg(Li + (warp * 8 + q) * B + lane + 32);
-    }
+    const bool subst = blk_subst[bi] != 0;
+    stage_diag<true>(AF, ldf, n, r0, Linv + (int64_t)bi * B * B, subst, Ds);
     if (t < B) {
         const int i = r0 + t;
         float v = 0.f;
@@ -204,72 +402,85 @@ __global__ void __launch_bounds__(TT) k_trsv_lower(const float *AF, int64_t ldf,
         }
         sv[t] = v;
     }
-    float p[8];
+    float p[8], pl[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) p[q] = 0.f;
-    offdiag<true>(AF, ldf, n, nblk, bi, ytag, tag, ys, &dev->timeout, p);
+    for (int q = 0; q < 8; ++q) p[q] = pl[q] = 0.f;
+    offdiag<true>(AF, ldf, n, nblk, bi, ytag, tag, ys, &dev->timeout, p, pl);
     __syncthreads();
     {
-        const float sq = reduce8(p, lane);
-        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] -= sq;
+        float sh, sl;
+        reduce8_pair(p, pl, lane, sh, sl);
+        if ((lane & 3) == 0) {
+            const int il = warp * 8 + reduce8_row(lane);
+            sv[il] = sub_pair(sv[il], sh, sl);
+        }
     }
     __syncthreads();
-    float acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = fmaf(da[q], sv[lane], db[q] * sv[lane + 32]);
-    const float y = reduce8(acc, lane);
-    if ((lane & 3) == 0) {
-        const int il = warp * 8 + reduce8_row(lane);
-        const float yv = (r0 + il < n) ? y : 0.f;
-        st_relaxed_u64(ytag + r0 + il, ((unsigned long long)tag << 32) | __float_as_uint(yv));
+    if (subst) {
+        if (warp == 0) diag_subst<true>(Ds, sv, lane);
+    } else {
+        const float y = diag_apply(Ds, sv, warp, lane);
+        __syncthreads();
+        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] = y;
+    }
+    __syncthreads();
+    if (t < B) {
+        const float yv = (r0 + t < n) ? sv[t] : 0.f;
+        st_relaxed_u64(ytag + r0 + t, ((unsigned long long)tag << 32) | __float_as_uint(yv));
     }
 }
 
 // Back substitution with U, reading the tagged y of the lower solve.
 // mode 0: d = (||r|| s) fl64(z); x += d; ||d|| into dev; mode 1: dout = z.
-__global__ void __launch_bounds__(TT) k_trsv_upper(const float *AF, int64_t ldf, int n, int nblk,
-                                                   const float *Uinv,
-                                                   const unsigned long long *ytag,
-                                                   unsigned long long *ztag, unsigned tag,
-                                                   int mode, double *x, float *dout,
-                                                   DevScalars *dev) {
+__global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t ldf, int n, int nblk,
+                                                      const float *Uinv, const int32_t *blk_subst,
+                                                      const unsigned long long *ytag,
+                                                      unsigned long long *ztag, unsigned tag,
+                                                      int mode, double *x, float *dout,
+                                                      DevScalars *dev) {
+    extern __shared__ __align__(16) float tsm[];
+    float *Ds = tsm;
+    float *sv = Ds + B * (B + 1);
+    float *ys = sv + B;
     __shared__ int s_bi;
-    __shared__ float sv[B], ys[B];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (t == 0) s_bi = nblk - 1 - (int)atomicAdd(&dev->ticket[1], 1u);
     __syncthreads();
     const int bi = s_bi;
     const int r0 = bi * B;
-    const float *Ui = Uinv + (int64_t)bi * B * B;
-    float da[8], db[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        da[q] = __ldg(Ui + (warp * 8 + q) * B + lane);
-        db[q] = __ldg(Ui + (warp * 8 + q) * B + lane + 32);
-    }
+    const bool subst = blk_subst[nblk + bi] != 0;
+    stage_diag<false>(AF, ldf, n, r0, Uinv + (int64_t)bi * B * B, subst, Ds);
     if (t < B) {
         // the lower solve of this launch sequence has written every y word already
         const int i = r0 + t;
         sv[t] = (i < n) ? __uint_as_float((unsigned)ld_relaxed_u64(ytag + i)) : 0.f;
     }
-    float p[8];
+    float p[8], pl[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) p[q] = 0.f;
-    offdiag<false>(AF, ldf, n, nblk, bi, ztag, tag, ys, &dev->timeout, p);
+    for (int q = 0; q < 8; ++q) p[q] = pl[q] = 0.f;
+    offdiag<false>(AF, ldf, n, nblk, bi, ztag, tag, ys, &dev->timeout, p, pl);
     __syncthreads();
     {
-        const float sq = reduce8(p, lane);
-        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] -= sq;
+        float sh, sl;
+        reduce8_pair(p, pl, lane, sh, sl);
+        if ((lane & 3) == 0) {
+            const int il = warp * 8 + reduce8_row(lane);
+            sv[il] = sub_pair(sv[il], sh, sl);
+        }
     }
     __syncthreads();
-    float acc[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) acc[q] = fmaf(da[q], sv[lane], db[q] * sv[lane + 32]);
-    const float z = reduce8(acc, lane);
+    if (subst) {
+        if (warp == 0) diag_subst<false>(Ds, sv, lane);
+    } else {
+        const float z = diag_apply(Ds, sv, warp, lane);
+        __syncthreads();
+        if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] = z;
+    }
+    __syncthreads();
     double dmax = 0.0;
-    if ((lane & 3) == 0) {
-        const int i = r0 + warp * 8 + reduce8_row(lane);
-        const float zv = (i < n) ? z : 0.f;
+    if (t < B) {
+        const int i = r0 + t;
+        const float zv = (i < n) ? sv[t] : 0.f;
         st_relaxed_u64(ztag + i, ((unsigned long long)tag << 32) | __float_as_uint(zv));
         if (i < n) {
             if (mode == 0) {
@@ -282,42 +493,60 @@ __global__ void __launch_bounds__(TT) k_trsv_upper(const float *AF, int64_t ldf,
             }
         }
     }
-    if (mode == 0) {
+    if (mode == 0 && t < B) {
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
         if (lane == 0) atomic_max_nonneg(&dev->dnorm_bits, dmax);
     }
 }
 
+constexpr size_t kSolveSmem = sizeof(float) * (B * (B + 1) + 2 * B);
+
 }  // namespace
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
-                            cudaStream_t s) {
+                            int32_t *blk_subst, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_diag_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kDiagSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     const int nblk = (n + B - 1) / B;
     count_launch();
-    k_diag_inv<<<dim3(nblk, 2), B, 0, s>>>(AF, ldf, n, Linv, Uinv);
+    k_diag_inv<<<dim3(nblk, 2), B, kDiagSmem, s>>>(AF, ldf, n, Linv, Uinv, blk_subst);
     return cudaGetLastError();
 }
 
 // ytag/ztag: 2 arrays of nblk*B tagged words (flags buffer).  Tickets are reset here.
 cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *Linv,
-                             const float *Uinv, const int32_t *perm, const double *r,
+                             const float *Uinv, const int32_t *blk_subst, const int32_t *perm, const double *r,
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
                              cudaStream_t s) {
     if (n == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_trsv_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_trsv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
     const int nblk = (n + B - 1) / B;
     cudaError_t e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     const int mode = vin ? 1 : 0;
     unsigned long long *ytag = tags, *ztag = tags + (int64_t)nblk * B;
     count_launch();
-    k_trsv_lower<<<nblk, TT, 0, s>>>(AF, ldf, n, nblk, Linv, perm, r, vin, mode, ytag, epoch, dev);
+    k_trsv_lower<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode, ytag, epoch,
+                                              dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_trsv_upper<<<nblk, TT, 0, s>>>(AF, ldf, n, nblk, Uinv, ytag, ztag, epoch, mode, x, dout, dev);
+    k_trsv_upper<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, epoch, mode, x, dout,
+                                              dev);
     return cudaGetLastError();
 }
 

@@ -79,3 +79,26 @@ def test_gauss8192_low_precision(ctx, tf):
     assert eta <= 3 * _gamma(n, 2.0 ** -53), eta
     if tf == "f16":
         assert rep.scale == 1024.0 / np.max(np.abs(A))
+
+
+def test_svd8192_promoted_problem(ctx):
+    """TW = TF = binary32, TR = binary64 (the promoted problem, Sec. 2.2.2),
+    A = U diag(s) V^T with s geometric from 1 to 1e-6, b = fl32(A 1) at
+    N = 8192.  IR converges to the solution of the promoted problem: the
+    binary32 result is within the bound of Thm. irterm (4 (N+1) kappa eps64 +
+    eps32, relative) of a binary64 solve of (fl64 A) x = fl64 b, and the loop
+    ends by the correction-stagnation rule of eq. (wilkterm), never by the
+    residual test."""
+    n = 8192
+    A, b = irgen.case_svd(n, 1003)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    x, rep = f.solve(dev_vec(b), term=ir.default_term(litmax=30))
+    x = x.cpu().numpy().astype(np.float64)
+    assert rep.status in ("stagnated", "converged")
+    A64 = A.astype(np.float64)
+    xr = np.linalg.solve(A64, b.astype(np.float64))
+    kappa = np.linalg.cond(A64, np.inf)
+    bound = 4 * (n + 1) * kappa * 2.0 ** -52 + 2.0 ** -23
+    assert np.max(np.abs(x - xr)) / np.max(np.abs(xr)) <= bound
+    # the solution is fl32-accurate in the sense of the paper's example (Sec. 2.2.2)
+    assert np.max(np.abs(x - xr)) / np.max(np.abs(xr)) <= 1e-4

@@ -155,3 +155,25 @@ def test_solve_host_end_to_end(ctx):
     xr = O.reference_solution(A, b)
     assert not xh.is_cuda
     assert O.rel_err_inf(xh.numpy(), xr) <= O.parity_tol(O.cond_inf(A), O.F64)
+
+
+def test_lu_solve_backward_stable_with_ill_conditioned_diagonal_blocks(ctx):
+    """U = D W with D graded from 1 to 1e-12 and W unit upper triangular close
+    to I: no interchanges, U = A, and two of its three 128-row diagonal blocks
+    have condition numbers above 1e5 (3e5), far too high for an explicit
+    inverse, so the solve takes them by substitution; the correction solve
+    must stay backward stable (componentwise, gamma_n |U| |d|), as the LU
+    solve of Algorithm IR assumes (Sec. 5.4.1)."""
+    n = 300
+    g = np.random.default_rng(5)
+    dg = np.logspace(0, -12, n) * np.where(g.random(n) < 0.5, -1.0, 1.0)
+    W = np.eye(n) + np.triu(g.standard_normal((n, n)), 1) * (0.3 / np.sqrt(n))
+    A = np.asfortranarray((dg[:, None] * W).astype(np.float32))
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    assert np.array_equal(f.pivots(), np.arange(n, dtype=np.int32))
+    v = g.standard_normal(n).astype(np.float32)
+    d = f.lu_solve(dev_vec(v)).cpu().numpy().astype(np.float64)
+    U = A.astype(np.float64)
+    r = U @ d - v.astype(np.float64)
+    bound = 2 * n * 2.0 ** -24 * (np.abs(U) @ np.abs(d) + np.abs(v))
+    assert np.all(np.abs(r) <= bound), float(np.max(np.abs(r) / bound))
