@@ -99,16 +99,26 @@ __global__ void __launch_bounds__(256) k_gemm_simt_narrow(float *AF, int64_t ldf
     __shared__ __align__(16) float Bs[NB][NT + 4];   // Bs[k][c] = U12[k][c]
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
     const int i0 = j + NB + blockIdx.x * NT;
-    for (int e = t; e < NT * NB / 4; e += 256) {
-        const int row = e >> 4, kq = (e & 15) * 4;
-        const int i = i0 + row;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < n) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + kq);
-        As[kq + 0][row] = v.x; As[kq + 1][row] = v.y; As[kq + 2][row] = v.z; As[kq + 3][row] = v.w;
-        const int m = e >> 4, cq = (e & 15) * 4, c = cb + cq;
-        float4 w = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (c < ce) w = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + m) * ldf + c);
-        *reinterpret_cast<float4 *>(&Bs[m][cq]) = w;
+    {
+        // all eight 16-byte loads of a thread in flight before the stores; for L21 the
+        // row runs fastest over the lanes so that the transposed stores hit 32 banks
+        constexpr int R = NT * NB / 4 / 256;
+        float4 va[R], vb[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int e = t + q * 256, ra = e % NT, ka = (e / NT) * 4, i = i0 + ra;
+            const int rb = e >> 4, cq = (e & 15) * 4, c = cb + cq;
+            va[q] = (i < n) ? *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + ka)
+                            : make_float4(0.f, 0.f, 0.f, 0.f);
+            vb[q] = (c < ce) ? *reinterpret_cast<const float4 *>(AF + (int64_t)(j + rb) * ldf + c)
+                             : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int e = t + q * 256, ra = e % NT, ka = (e / NT) * 4, rb = e >> 4, cq = (e & 15) * 4;
+            As[ka + 0][ra] = va[q].x; As[ka + 1][ra] = va[q].y; As[ka + 2][ra] = va[q].z; As[ka + 3][ra] = va[q].w;
+            *reinterpret_cast<float4 *>(&Bs[rb][cq]) = vb[q];
+        }
     }
     float acc[4][4];
 #pragma unroll

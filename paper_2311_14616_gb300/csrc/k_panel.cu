@@ -419,9 +419,23 @@ constexpr int kNarrowCols = 64;   // columns per CTA (4 threads each)
 __global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
                                                      void *Bop) {
     __shared__ __align__(16) float Lt[NB][NB + 4];    // Lt[m][k] = L11[k][m]
-    for (int e = threadIdx.x; e < NB * NB; e += blockDim.x) {
-        const int k = e / NB, m = e % NB;
-        Lt[m][k] = AF[(int64_t)(j + k) * ldf + j + m];
+    {
+        // all loads in flight before the (transposing) stores: row k, columns 4 m4 .. 4 m4 + 3;
+        // k runs fastest over the lanes so that the transposed stores hit 32 banks
+        float4 v[NB * NB / 4 / (4 * kNarrowCols)];
+#pragma unroll
+        for (int i = 0; i < NB * NB / 4 / (4 * kNarrowCols); ++i) {
+            const int e = threadIdx.x + i * 4 * kNarrowCols, k = e % NB, m4 = e / NB;
+            v[i] = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + k) * ldf + j + 4 * m4);
+        }
+#pragma unroll
+        for (int i = 0; i < NB * NB / 4 / (4 * kNarrowCols); ++i) {
+            const int e = threadIdx.x + i * 4 * kNarrowCols, k = e % NB, m4 = e / NB;
+            Lt[4 * m4 + 0][k] = v[i].x;
+            Lt[4 * m4 + 1][k] = v[i].y;
+            Lt[4 * m4 + 2][k] = v[i].z;
+            Lt[4 * m4 + 3][k] = v[i].w;
+        }
     }
     __syncthreads();
     const int t = threadIdx.x, lane = t & 31, q = t & 3;
