@@ -15,6 +15,9 @@ A plain, slow, obviously-correct implementation of the paper's method
                        shrinking.
 * ``term_decide``   -- the termination test of Sec. 5.1, a pure function that
                        the tests replay the paper's printed histories through.
+* ``gmres_ir_solve`` -- GMRES-IR (Sec. 4.3): the correction equation solved by
+                       left-preconditioned GMRES with P = U^{-1} L^{-1}
+                       (eq. pdef), ``gmres_correction``.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package.  It shares
@@ -249,10 +252,13 @@ class IRResult:
         return len(self.rhist) - 1
 
 
-def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: bool):
+def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: bool,
+                rmax_r: Optional[float] = None):
     """Termination test of Sec. 5.1, applied after each residual computation.
 
     rhist = [||r_0||, ..., ||r_k||] (r_0 = b), dhist = [||d_0||, ..., ||d_{k-1}||].
+    rmax_r replaces R_max in the residual-stagnation test (eq. stag) when
+    given (GMRES-IR); the correction test (eq. wilkterm) keeps term.Rmax.
     Returns a status code, or None to continue.
     """
     k = len(rhist) - 1
@@ -271,7 +277,8 @@ def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: 
         tol = term.abs_rel_tol if term.abs_rel_tol > 0 else term.Cr * eps_w
         if rn <= tol * bnorm:             # eq. (residterm)
             return CONVERGED
-        if k >= 1 and rn >= term.Rmax * rhist[-2]:   # eq. (stag)
+        rm = term.Rmax if rmax_r is None else rmax_r
+        if k >= 1 and rn >= rm * rhist[-2]:   # eq. (stag)
             return STAGNATED
     if k >= term.litmax:
         return MAXIT
@@ -321,6 +328,178 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
         r = residual(A, b64, x)
         res.rhist.append(float(np.max(np.abs(r))))
         st = term_decide(res.rhist, res.dhist, bnorm, eps_w, term, tr_wider)
+        if st is not None:
+            res.status = st
+            break
+    res.x = x
+    res.sol = x.astype(A.dtype)
+    return res
+
+
+# --------------------------------------------------------------------------
+# GMRES-IR (Sec. 4.2-4.3; Sec. 2.3 IR-Krylov)
+# --------------------------------------------------------------------------
+
+@dataclass
+class KrylovOpts:
+    """Options of the Krylov correction solve.
+
+    basissize: the Krylov basis size, i.e. the most GMRES iterations per
+               refinement step (default 10, Sec. 4.3).
+    eta:       GMRES stops early when its residual estimate falls to
+               eta ||P r||_2 (the paper leaves this tolerance unstated).
+    Rmax_r:    residual-stagnation factor of the outer loop (eq. stag) when TR
+               is not wider than TW; 1 stops when the residual no longer
+               decreases (the N = 8102 half-precision GMRES-IR history of
+               Sec. 4.5 continues past a ratio of 0.69).
+    """
+    basissize: int = 10
+    eta: float = 1e-8
+    Rmax_r: float = 1.0
+
+
+def precondition(LU: np.ndarray, ipiv: np.ndarray, s: float, w: np.ndarray) -> np.ndarray:
+    """P w with P = U^{-1} L^{-1} (eq. pdef) applied as the refinement solve is.
+
+    rho = ||w||_inf; v = fl32(Pi w / rho); v = U^{-1} L^{-1} v in binary32;
+    P w = (rho s) fl64(v) (eqs. vdlow, promotevd; s is the binary16 scale of
+    A_F = s A, since (s A)^{-1} = A^{-1} / s).  P 0 = 0.
+    """
+    rho = float(np.max(np.abs(w))) if w.size else 0.0
+    if rho == 0.0:
+        return np.zeros_like(w, dtype=np.float64)
+    v = getrs_f32(LU, ipiv, (w / rho).astype(np.float32))
+    return (rho * s) * v.astype(np.float64)
+
+
+def matvec(A: np.ndarray, v: np.ndarray) -> np.ndarray:
+    """A v in TR = binary64 with A promoted exactly: the residual of b = 0, negated."""
+    return -residual(A, np.zeros(A.shape[0]), v)
+
+
+def gmres(op, z: np.ndarray, m: int, eta: float):
+    """GMRES (Saad and Schultz) for op(d) = z from d_0 = 0, in binary64.
+
+    Minimises ||z - op(d)||_2 over d in the Krylov space K_k(op, z):
+      beta = ||z||_2, v_0 = z / beta, g = beta e_1;
+      for j = 0..m-1: w = op(v_j); classical Gram-Schmidt against v_0..v_j,
+        done twice (h = h' + h''); h_{j+1,j} = ||w||_2; v_{j+1} = w / h_{j+1,j};
+        the Givens rotations of the earlier columns are applied to column j of
+        H, a new rotation (c, s) = (h_jj, h_{j+1,j}) / hypot(h_jj, h_{j+1,j})
+        zeroes h_{j+1,j}, and g_{j+1} = -s g_j, g_j = c g_j;
+        stop when |g_{j+1}| <= eta beta, on breakdown (h_{j+1,j} = 0) or at m;
+      y = R^{-1} g (back substitution, R the rotated H), d = V_k y.
+    Returns (d, k, est): k iterations, est[j] = |g_{j+1}| (the residual norm
+    after iteration j as the rotations give it).
+    """
+    n = z.shape[0]
+    beta = float(np.sqrt(np.dot(z, z)))
+    if beta == 0.0 or m < 1:
+        return np.zeros(n), 0, []
+    V = np.zeros((n, m + 1))
+    H = np.zeros((m + 1, m))
+    cs = np.zeros(m)
+    sn = np.zeros(m)
+    g = np.zeros(m + 1)
+    V[:, 0] = z / beta
+    g[0] = beta
+    k = 0
+    est = []
+    for j in range(m):
+        w = op(V[:, j])
+        Vj = V[:, :j + 1]
+        h1 = Vj.T @ w
+        w = w - Vj @ h1
+        h2 = Vj.T @ w
+        w = w - Vj @ h2
+        H[:j + 1, j] = h1 + h2
+        hn = float(np.sqrt(np.dot(w, w)))
+        H[j + 1, j] = hn
+        if hn > 0.0:
+            V[:, j + 1] = w / hn
+        for i in range(j):
+            a, b_ = H[i, j], H[i + 1, j]
+            H[i, j] = cs[i] * a + sn[i] * b_
+            H[i + 1, j] = -sn[i] * a + cs[i] * b_
+        nu = float(np.hypot(H[j, j], H[j + 1, j]))
+        if nu == 0.0:
+            cs[j], sn[j] = 1.0, 0.0
+        else:
+            cs[j], sn[j] = H[j, j] / nu, H[j + 1, j] / nu
+        H[j, j] = nu
+        H[j + 1, j] = 0.0
+        g[j + 1] = -sn[j] * g[j]
+        g[j] = cs[j] * g[j]
+        k = j + 1
+        est.append(abs(g[j + 1]))
+        if abs(g[j + 1]) <= eta * beta or hn == 0.0:
+            break
+    y = np.zeros(k)
+    for i in range(k - 1, -1, -1):
+        acc = g[i]
+        for l in range(i + 1, k):
+            acc -= H[i, l] * y[l]
+        y[i] = acc / H[i, i] if H[i, i] != 0.0 else 0.0
+    return V[:, :k] @ y, k, est
+
+
+def gmres_correction(A: np.ndarray, LU: np.ndarray, ipiv: np.ndarray, s: float, r: np.ndarray,
+                     m: int, eta: float):
+    """Left-preconditioned GMRES for the correction equation A d = r (Sec. 4.3):
+    ``gmres`` on P A d = P r, with P (eq. pdef) applied by ``precondition``
+    and A v in binary64 (the high-precision matrix-vector product).
+    Returns (d, k)."""
+    d, k, _ = gmres(lambda v: precondition(LU, ipiv, s, matvec(A, v)),
+                    precondition(LU, ipiv, s, r), m, eta)
+    return d, k
+
+
+@dataclass
+class GMRESIRResult(IRResult):
+    khist: list = field(default_factory=list)
+
+
+def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
+                   kopts: Optional[KrylovOpts] = None, nb: int = 0, fp16_scaling: bool = True,
+                   tr_wider: Optional[bool] = None) -> GMRESIRResult:
+    """GMRES-IR (Sec. 4.3): Algorithm IR with the correction d from
+    ``gmres_correction`` instead of one low-precision solve.  Factorization,
+    residual (TR = binary64) and the termination tests of Sec. 5.1 are those of
+    ``ir_solve``, except that the residual-stagnation factor is kopts.Rmax_r;
+    khist[i] is the number of GMRES iterations of refinement step i.
+    """
+    term = term or Term()
+    kopts = kopts or KrylovOpts()
+    A = np.asfortranarray(A)
+    tw = _tw_of(A)
+    n = A.shape[0]
+    if tr_wider is None:
+        tr_wider = tw == F32
+    b64 = np.ascontiguousarray(b, dtype=np.float64)
+    eps_w = EPS[tw]
+    s = fp16_scale(A) if (tf == F16 and fp16_scaling) else 1.0
+    AF = cast(A, tf, s)
+    LU, ipiv, info = getrf_tf(AF, tf, nb)
+    x = np.zeros(n)
+    res = GMRESIRResult(x=x, sol=x.astype(A.dtype), ipiv=ipiv, LU=LU, scale=s, info=info)
+    bnorm = float(np.max(np.abs(b64))) if n else 0.0
+    res.rhist.append(bnorm)
+    if info != 0:
+        res.status = FAILED
+        return res
+    if bnorm == 0.0:
+        res.status = CONVERGED
+        return res
+    tterm = Term(Cr=term.Cr, Ce=term.Ce, Rmax=term.Rmax, litmax=term.litmax, abs_rel_tol=term.abs_rel_tol)
+    r = b64.copy()
+    while True:
+        d, k = gmres_correction(A, LU, ipiv, s, r, kopts.basissize, kopts.eta)
+        res.khist.append(k)
+        x += d
+        res.dhist.append(float(np.max(np.abs(d))))
+        r = residual(A, b64, x)
+        res.rhist.append(float(np.max(np.abs(r))))
+        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, tterm, tr_wider, rmax_r=kopts.Rmax_r)
         if st is not None:
             res.status = st
             break

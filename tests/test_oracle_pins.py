@@ -312,7 +312,8 @@ def test_termination_replays_printed_histories(golden):
         stop = None
         for k in range(1, len(rh)):
             d = dh[:k] if dh is not None else [1.0] * k
-            st = O.term_decide(rh[:k + 1], d, case["bnorm"], case["eps_w"], term, case["tr_wider"])
+            st = O.term_decide(rh[:k + 1], d, case["bnorm"], case["eps_w"], term, case["tr_wider"],
+                               rmax_r=case.get("Rmax_r"))
             if st is not None:
                 stop = (k, O.STATUS_NAMES[st])
                 break
