@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the binary64 cuSOLVER comparators (e.g. under a profiler)")
     ap.add_argument("--batch-count", type=int, default=2000)
+    ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES-IR line")
     return ap.parse_args()
 
 
@@ -572,6 +573,37 @@ def main():
 
     batched = None if args.no_batch else run_batched(args, ctx, dev, stream, flush, ws, rank)
 
+    # --- GMRES-IR (Sec. 4.3) with binary16 factors on the same system, where plain IR
+    # with the same factors does not converge
+    gmres = None
+    if not args.no_gmres:
+        fact16 = ctx.factor(A_d, tf="f16")
+        fact16.gmres_reserve(10)
+        xg16 = torch.empty_like(b_d)
+        x16 = torch.empty_like(b_d)
+        kopts = ir.krylov_opts()
+
+        def step_gm():
+            fact16.refactor(A_d)
+            return fact16.solve_gmres(b_d, xg16, term, kopts)[1]
+
+        gsteps = max(3, args.steps // 2)
+        _, _, prof_gm, l_gm = timed_steps(step_gm, gsteps, 1, profile=True)
+        ms_gm, rep_gm, _, _ = timed_steps(step_gm, gsteps, 1)
+        _, rep_ir16 = fact16.solve(b_d, x16, term)
+        rel = lambda v: float(np.max(np.abs(v.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
+        gm_kinds = {k: v[0] / gsteps for k, v in sorted(prof_gm.items())}
+        gmres = {
+            "workload": f"green_sine_N{n}_alpha800_TWf64_TFf16_TRf64_basis10",
+            "ms": max_over_ranks(statistics.mean(ms_gm), ws), "unit": "ms (refactor + GMRES-IR solve)",
+            "iters": rep_gm.iters, "status": rep_gm.status, "khist": rep_gm.khist,
+            "rhist": rep_gm.rhist, "rel_err_vs_closed_form": rel(xg16),
+            "ir_same_factors": {"iters": rep_ir16.iters, "status": rep_ir16.status,
+                                "rel_err_vs_closed_form": rel(x16)},
+            "kernel_ms_per_step": gm_kinds,
+            "gpu_launches_per_step": l_gm / gsteps,
+        }
+
     value = t32 / ws if ws > 1 else t32
     out = {
         "metric": "ir_solve_ms", "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
@@ -600,6 +632,7 @@ def main():
         "gpu_launches_per_step": launches / args.steps,
         "clocks": clk,
         "batched": batched,
+        "gmres_ir": gmres,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -230,6 +230,45 @@ ir_status ir_factor_solve_batched(ir_ctx *ctx, int64_t count, const int64_t *n_h
                                   const ir_opts *opts, const ir_term *term, void *stream,
                                   ir_batch_result *results_dev);
 
+/* ---- GMRES-IR (Sec. 4.2-4.3) ---------------------------------------------
+ * Each refinement step solves its correction equation A d = r by GMRES on the
+ * left-preconditioned system P A d = P r, with P = U^{-1} L^{-1} (eq. pdef),
+ * instead of applying P once.  Within GMRES everything is binary64: the
+ * product A v (A promoted exactly), the Krylov basis (classical Gram-Schmidt,
+ * done twice), the Hessenberg matrix and its Givens rotations.  P w is applied
+ * as the refinement solve is: rho = ||w||_inf, binary32 solves of
+ * fl32(w / rho), scaled back by rho (and by the binary16 scale s).
+ * GMRES starts from d = 0 and stops after basissize iterations, when its
+ * residual estimate |g_{k+1}| <= eta ||P r||_2, or on breakdown.
+ * The outer loop and its termination are those of ir_solve, except that the
+ * residual-stagnation test (eq. stag) uses Rmax_r in place of term->Rmax. */
+#define IR_MAX_BASIS 64
+
+typedef struct {
+    int basissize;        /* default 10 (Sec. 4.3); 1 .. IR_MAX_BASIS */
+    double eta;           /* default 1e-8 */
+    double Rmax_r;        /* default 1.0: stop when the residual no longer decreases */
+} ir_krylov_opts;
+
+void ir_default_krylov_opts(ir_krylov_opts *kopts);
+
+/* mpglu (Sec. 4.4): reserve the GMRES storage of a factorization -- the
+ * Krylov basis, (basissize + 2) n binary64 values, and O(basissize^2)
+ * scalars -- so that ir_solve_gmres allocates nothing.  ir_solve_gmres
+ * reserves on first use (synchronously) when this was not called or was
+ * called with a smaller basissize.  Freed by ir_fact_destroy. */
+ir_status ir_gmres_reserve(ir_fact *fact, int basissize);
+
+/* Backslash on the GMRES-IR factorization: solve A x = b.
+ *   b, x: n values in TW (device).  term, kopts may be NULL (defaults).
+ *   rep may be NULL; khist (host, may be NULL) receives IR_MAX_HIST ints,
+ *   khist[k] = GMRES iterations of refinement step k (Sec. 4.5), for
+ *   k < rep->iters.
+ * Errors as ir_solve; IR_EINVAL for basissize outside 1 .. IR_MAX_BASIS or
+ * eta < 0.  Synchronizes `stream` once per refinement step. */
+ir_status ir_solve_gmres(ir_fact *fact, const void *b, void *x, const ir_term *term,
+                         const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist);
+
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */
 ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);
 

@@ -461,12 +461,14 @@ class GMRESIRResult(IRResult):
 
 def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
                    kopts: Optional[KrylovOpts] = None, nb: int = 0, fp16_scaling: bool = True,
-                   tr_wider: Optional[bool] = None) -> GMRESIRResult:
+                   tr_wider: Optional[bool] = None, factors=None) -> GMRESIRResult:
     """GMRES-IR (Sec. 4.3): Algorithm IR with the correction d from
     ``gmres_correction`` instead of one low-precision solve.  Factorization,
     residual (TR = binary64) and the termination tests of Sec. 5.1 are those of
     ``ir_solve``, except that the residual-stagnation factor is kopts.Rmax_r;
     khist[i] is the number of GMRES iterations of refinement step i.
+    factors = (LU, ipiv): use these factors of A_F = s A instead of computing
+    them (to compare the refinement alone with another implementation's).
     """
     term = term or Term()
     kopts = kopts or KrylovOpts()
@@ -478,8 +480,11 @@ def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] =
     b64 = np.ascontiguousarray(b, dtype=np.float64)
     eps_w = EPS[tw]
     s = fp16_scale(A) if (tf == F16 and fp16_scaling) else 1.0
-    AF = cast(A, tf, s)
-    LU, ipiv, info = getrf_tf(AF, tf, nb)
+    if factors is None:
+        LU, ipiv, info = getrf_tf(cast(A, tf, s), tf, nb)
+    else:
+        LU, ipiv = np.asfortranarray(factors[0], dtype=np.float32), np.asarray(factors[1], dtype=np.int32)
+        info = 0
     x = np.zeros(n)
     res = GMRESIRResult(x=x, sol=x.astype(A.dtype), ipiv=ipiv, LU=LU, scale=s, info=info)
     bnorm = float(np.max(np.abs(b64))) if n else 0.0

@@ -28,11 +28,11 @@ namespace {
 // call on the launching stream, summed per kind when profiling stops.
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
-    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_N
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
-                                "batched"};
+                                "batched", "gm_orth", "gm_update"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -135,6 +135,10 @@ void free_fact(ir_fact *f) {
     cudaFree(f->r);
     cudaFree(f->dev);
     if (f->host_dev) cudaFreeHost(f->host_dev);
+    cudaFree(f->gm_V);
+    cudaFree(f->gm_W);
+    cudaFree(f->gm_st);
+    if (f->gm_host_k) cudaFreeHost(f->gm_host_k);
     if (f->graph) cudaGraphExecDestroy(f->graph);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
     if (f->la_stream) cudaStreamDestroy(f->la_stream);
@@ -364,8 +368,9 @@ ir_status read_dev(ir_fact *f, cudaStream_t s) {
 
 // Termination test of Sec. 5.1 after the k-th residual (rh[0..k], dh[0..k-1]).
 // Returns -1 to continue, else an ir_solve_status.
+// rmax_r: the factor of the residual-stagnation test (t->Rmax for IR).
 int term_decide(const double *rh, const double *dh, int k, double bnorm, double eps_w,
-                const ir_term *t, bool tr_wider) {
+                const ir_term *t, bool tr_wider, double rmax_r) {
     const double rn = rh[k];
     if (!std::isfinite(rn)) return IR_DIVERGED;
     if (rn == 0.0) return IR_CONVERGED;    // exact solution: r / ||r|| (eq. vdlow) is undefined next
@@ -374,7 +379,7 @@ int term_decide(const double *rh, const double *dh, int k, double bnorm, double 
     } else {
         const double tol = t->abs_rel_tol > 0 ? t->abs_rel_tol : t->Cr * eps_w;
         if (rn <= tol * bnorm) return IR_CONVERGED;                           // eq. (residterm)
-        if (k >= 1 && rn >= t->Rmax * rh[k - 1]) return IR_STAGNATED;         // eq. (stag)
+        if (k >= 1 && rn >= rmax_r * rh[k - 1]) return IR_STAGNATED;          // eq. (stag)
     }
     if (k >= t->litmax) return IR_MAXIT;
     return -1;
@@ -618,7 +623,149 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
         ++k;
         R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
         R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
-        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider);
+        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, t.Rmax);
+    }
+    RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
+    R.iters = k;
+    R.status = (ir_solve_status)status;
+    if (rep) {
+        CK(cudaStreamSynchronize(s));
+        *rep = R;
+    }
+    return IR_OK;
+}
+
+void ir_default_krylov_opts(ir_krylov_opts *o) {
+    if (!o) return;
+    o->basissize = 10;
+    o->eta = 1e-8;
+    o->Rmax_r = 1.0;
+}
+
+ir_status ir_gmres_reserve(ir_fact *f, int m) {
+    if (!f || m < 1 || m > IR_MAX_BASIS) return IR_EINVAL;
+    if (f->gm_st && f->gm_m >= m) return IR_OK;
+    CK(cudaSetDevice(f->ctx->device));
+    CK(cudaDeviceSynchronize());     // the old buffers may be in use
+    cudaFree(f->gm_V);
+    cudaFree(f->gm_W);
+    cudaFree(f->gm_st);
+    f->gm_V = f->gm_W = nullptr;
+    f->gm_st = nullptr;
+    f->gm_m = 0;
+    const int64_t n = f->n > 0 ? f->n : 1;
+    const int64_t ldv = (n + 31) / 32 * 32;
+    CK(cudaMalloc(&f->gm_V, (size_t)(m + 1) * ldv * sizeof(double)));
+    CK(cudaMalloc(&f->gm_W, (size_t)ldv * sizeof(double)));
+    CK(cudaMalloc(&f->gm_st, sizeof(GmState)));
+    CK(cudaMemset(f->gm_st, 0, sizeof(GmState)));
+    if (!f->gm_host_k) CK(cudaMallocHost((void **)&f->gm_host_k, sizeof(int)));
+    f->gm_ldv = ldv;
+    f->gm_m = m;
+    return IR_OK;
+}
+
+ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term,
+                         const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist) {
+    if (!f || (f->n > 0 && (!b || !x))) return IR_EINVAL;
+    ir_term t;
+    if (term) t = *term;
+    else ir_default_term(&t);
+    ir_krylov_opts ko;
+    if (kopts) ko = *kopts;
+    else ir_default_krylov_opts(&ko);
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    if (ko.basissize < 1 || ko.basissize > IR_MAX_BASIS || !(ko.eta >= 0) || !(ko.Rmax_r > 0)) return IR_EINVAL;
+    if (khist) std::memset(khist, 0, IR_MAX_HIST * sizeof(int));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n = f->n;
+    ir_report R;
+    std::memset(&R, 0, sizeof R);
+    R.scale = 1.0;
+    if (n == 0) {
+        R.status = IR_CONVERGED;
+        if (rep) *rep = R;
+        return IR_OK;
+    }
+    CK(cudaSetDevice(f->ctx->device));
+    ir_status st = ir_gmres_reserve(f, ko.basissize);
+    if (st != IR_OK) return st;
+    st = read_dev(f, s);
+    if (st != IR_OK) return st;
+    R.scale = f->host_dev->scale;
+    if (f->host_dev->timeout) {
+        snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the factorization timed out");
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ETIMEOUT;
+    }
+    if (f->host_dev->nonfinite) {
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ENONFINITE;
+    }
+    if (f->host_dev->info != kInfoNone) {
+        R.info = f->host_dev->info;
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ESINGULAR;
+    }
+    CK(cudaMemsetAsync(&f->dev->bnorm_bits, 0, sizeof(unsigned long long), s));
+    RUN(KC_INIT, s, launch_init_rb(n, f->TW, b, f->r, f->x, f->dev, s));
+    CK(cudaMemcpyAsync(&f->dev->rnorm_bits, &f->dev->bnorm_bits, sizeof(unsigned long long),
+                       cudaMemcpyDeviceToDevice, s));
+    st = read_dev(f, s);
+    if (st != IR_OK) return st;
+    if (f->host_dev->nonfinite) {
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ENONFINITE;
+    }
+    const double bnorm = bits_to_double(f->host_dev->bnorm_bits);
+    R.rhist[0] = bnorm;
+    const bool tr_wider = (f->TW == IR_F32);
+    const double eps_w = eps_of(f->TW);
+    const int m = ko.basissize;
+    const int nn = (int)n;
+    double *V = f->gm_V, *W = f->gm_W;
+    const int64_t ldv = f->gm_ldv;
+    GmState *gs = f->gm_st;
+    int k = 0;
+    int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
+    while (status < 0) {
+        // v_0 = P r / ||P r||_2
+        f->epoch += 1;
+        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
+                                         nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s,
+                                         &f->dev->rnorm_bits, V, nullptr));
+        RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, -1, m, ko.eta, gs, s));
+        for (int j = 0; j < m; ++j) {
+            // V_{j+1} = P (A v_j), then orthogonalize; skipped once GMRES has stopped
+            RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, nullptr, V + (int64_t)j * ldv, W,
+                                             f->ctx->partials, f->ctx->partials_cap, &gs->wnorm_bits,
+                                             f->ctx->sms, s, &gs->done));
+            f->epoch += 1;
+            RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, W,
+                                             nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s,
+                                             &gs->wnorm_bits, V + (int64_t)(j + 1) * ldv, &gs->done));
+            RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, j, m, ko.eta, gs, s));
+        }
+        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, sizeof(unsigned long long), s));
+        RUN(KC_GM_UPDATE, s, launch_gm_update(nn, V, ldv, gs, f->x, &f->dev->dnorm_bits, s));
+        RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
+                                         f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
+        CK(cudaMemcpyAsync(f->gm_host_k, &gs->k, sizeof(int), cudaMemcpyDeviceToHost, s));
+        st = read_dev(f, s);
+        if (st != IR_OK) return st;
+        if (f->host_dev->timeout) {
+            snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the triangular solve timed out");
+            return IR_ETIMEOUT;
+        }
+        if (khist) khist[k] = *f->gm_host_k;
+        ++k;
+        R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
+        R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
+        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, ko.Rmax_r);
     }
     RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
     R.iters = k;

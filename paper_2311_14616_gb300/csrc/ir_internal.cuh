@@ -39,6 +39,21 @@ struct DevScalars {
     unsigned int ticket[2];          // CTA ticket counters of the two solves
 };
 
+// GMRES state of one correction solve (device memory, written by the
+// orthogonalization kernel's first CTA).  R is the Hessenberg matrix after the
+// Givens rotations (upper triangular, column-major with leading dimension
+// kMaxBasis), g the rotated right-hand side beta e_1.
+constexpr int kMaxBasis = 64;
+struct GmState {
+    double beta;                        // ||P r||_2
+    double g[kMaxBasis + 1];
+    double cs[kMaxBasis], sn[kMaxBasis];
+    double R[kMaxBasis * kMaxBasis];
+    unsigned long long wnorm_bits;      // ||A v_j||_inf of the latest product
+    int k;                              // GMRES iterations taken
+    int done;                           // 1: the remaining iterations are skipped
+};
+
 }  // namespace ir
 
 struct ir_ctx {
@@ -79,6 +94,13 @@ struct ir_fact {
     const void *graph_A;
     int64_t graph_lda;
     unsigned long long graph_launches;  // kernels in the graph
+    // GMRES-IR workspace (reserved on demand): Krylov basis V (gm_m + 1
+    // columns of gm_ldv binary64), the product buffer W, the GMRES state
+    int gm_m;
+    int64_t gm_ldv;
+    double *gm_V, *gm_W;
+    ir::GmState *gm_st;
+    int *gm_host_k;          // pinned mirror of gm_st->k
 };
 
 namespace ir {
@@ -113,14 +135,31 @@ cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
                             int32_t *blk_subst, cudaStream_t s);
+// Solve pair in one of three modes:
+//   refinement (vin = pw = NULL): x += (||r|| s) fl64(U^{-1} L^{-1} fl32(P r / ||r||)), ||d|| into dev;
+//   raw (vin != NULL): dout = U^{-1} L^{-1} P vin in binary32;
+//   preconditioner (pw != NULL): pw = (rho s) fl64(U^{-1} L^{-1} fl32(P r / rho)), rho from rho_bits.
+// skip != NULL: every CTA returns at once while *skip != 0.
 cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *Linv,
                              const float *Uinv, const int32_t *blk_subst, const int32_t *perm, const double *r,
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
-                             cudaStream_t s);
+                             cudaStream_t s, const unsigned long long *rho_bits = nullptr,
+                             double *pw = nullptr, const int *skip = nullptr);
+// r = b - A x (b == NULL: r = A x) and ||r||_inf into rnorm_bits; skip as above.
 cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *b,
                             const double *x, double *r, double *partials, int64_t partials_cap,
-                            unsigned long long *rnorm_bits, int sms, cudaStream_t s);
+                            unsigned long long *rnorm_bits, int sms, cudaStream_t s,
+                            const int *skip = nullptr);
+
+// GMRES (k_gmres.cu).  j = -1: v_0 = V_0 / ||V_0||_2, beta, g = beta e_1.
+// j >= 0: orthogonalize V_{j+1} = P A v_j against v_0..v_j (classical
+// Gram-Schmidt twice), normalize, rotate column j of H, set done.
+cudaError_t launch_gm_orth(int n, double *V, int64_t ldv, int j, int m, double eta, GmState *st,
+                           cudaStream_t s);
+// d = V_k R^{-1} g; x += d; ||d||_inf into dnorm_bits.
+cudaError_t launch_gm_update(int n, const double *V, int64_t ldv, const GmState *st, double *x,
+                             unsigned long long *dnorm_bits, cudaStream_t s);
 int64_t residual_partials_needed(int64_t n, int sms);
 
 // batched driver (many systems with n <= IR_BATCH_MAX_N, one persistent launch)

@@ -1,5 +1,7 @@
 // Residual r = b - A x in binary64 (Algorithm IR, residual in TR; eq. xferrule:
-// A and b in TW are promoted exactly) and ||r||_inf.
+// A and b in TW are promoted exactly) and ||r||_inf; with b = NULL the same
+// kernels form the product A x (the high-precision matrix-vector product of
+// GMRES-IR, Sec. 4.3).
 //
 // Pass 1: CTA (row block, column split) forms the partial sums of 256 rows over
 // a range of columns -- each thread two adjacent rows, loaded as one 16-byte
@@ -26,7 +28,8 @@ struct Vec2<float> { using T = float2; };
 template <typename TW>
 __global__ void __launch_bounds__(RT) k_resid_partial(int64_t n, const TW *A, int64_t lda,
                                                       const double *x, int64_t cols_per_split,
-                                                      double *partials, int vec_ok) {
+                                                      double *partials, int vec_ok, const int *skip) {
+    if (skip && *skip) return;
     __shared__ double xs[XCH];
     const int64_t i = (int64_t)blockIdx.x * RB + 2 * threadIdx.x;
     const int64_t c0 = (int64_t)blockIdx.y * cols_per_split;
@@ -73,13 +76,14 @@ __global__ void __launch_bounds__(RT) k_resid_partial(int64_t n, const TW *A, in
 
 template <typename TW>
 __global__ void k_resid_final(int64_t n, const TW *b, const double *partials, int nsplit,
-                              double *r, unsigned long long *rnorm_bits) {
+                              double *r, unsigned long long *rnorm_bits, const int *skip) {
+    if (skip && *skip) return;
     double m = 0.0;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double s = partials[i];
         for (int k = 1; k < nsplit; ++k) s += partials[(int64_t)k * n + i];
-        const double ri = (double)b[i] - s;
+        const double ri = b ? (double)b[i] - s : s;
         r[i] = ri;
         m = fmax(m, fabs(ri));
         if (ri != ri) m = ri;   // keep a NaN visible to the norm
@@ -107,7 +111,7 @@ int64_t residual_partials_needed(int64_t n, int sms) { return (int64_t)nsplit_fo
 
 cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *b,
                             const double *x, double *r, double *partials, int64_t partials_cap,
-                            unsigned long long *rnorm_bits, int sms, cudaStream_t s) {
+                            unsigned long long *rnorm_bits, int sms, cudaStream_t s, const int *skip) {
     if (n == 0) return cudaSuccess;
     const int ns = nsplit_for(n, sms);
     if ((int64_t)ns * n > partials_cap) return cudaErrorInvalidValue;
@@ -121,14 +125,14 @@ cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, 
     const int fg = (int)((n + 255) / 256 < 1024 ? (n + 255) / 256 : 1024);
     if (tw == IR_F64) {
         count_launch();
-        k_resid_partial<double><<<grid, RT, 0, s>>>(n, (const double *)A, lda, x, cps, partials, vec_ok);
+        k_resid_partial<double><<<grid, RT, 0, s>>>(n, (const double *)A, lda, x, cps, partials, vec_ok, skip);
         count_launch();
-        k_resid_final<double><<<fg, 256, 0, s>>>(n, (const double *)b, partials, ns, r, rnorm_bits);
+        k_resid_final<double><<<fg, 256, 0, s>>>(n, (const double *)b, partials, ns, r, rnorm_bits, skip);
     } else {
         count_launch();
-        k_resid_partial<float><<<grid, RT, 0, s>>>(n, (const float *)A, lda, x, cps, partials, vec_ok);
+        k_resid_partial<float><<<grid, RT, 0, s>>>(n, (const float *)A, lda, x, cps, partials, vec_ok, skip);
         count_launch();
-        k_resid_final<float><<<fg, 256, 0, s>>>(n, (const float *)b, partials, ns, r, rnorm_bits);
+        k_resid_final<float><<<fg, 256, 0, s>>>(n, (const float *)b, partials, ns, r, rnorm_bits, skip);
     }
     return cudaGetLastError();
 }

@@ -369,13 +369,15 @@ __device__ __forceinline__ void stage_diag(const float *AF, int64_t ldf, int n, 
     }
 }
 
-// mode 0: v = fl32(r[perm[i]] / ||r||) (refinement step); mode 1: v = vin[perm[i]].
-// Publishes tagged y for the upper solve.
+// mode 0 / 2: v = fl32(r[perm[i]] / rho), rho = *rho_bits (||r||; v = 0 when
+// rho = 0); mode 1: v = vin[perm[i]].  Publishes tagged y for the upper solve.
 __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t ldf, int n, int nblk,
                                                       const float *Linv, const int32_t *blk_subst,
                                                       const int32_t *perm, const double *r, const float *vin,
-                                                      int mode, unsigned long long *ytag, unsigned tag,
+                                                      int mode, const unsigned long long *rho_bits,
+                                                      const int *skip, unsigned long long *ytag, unsigned tag,
                                                       DevScalars *dev) {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) float tsm[];
     float *Ds = tsm;                 // this block's diagonal inverse, or its transposed triangle
     float *sv = Ds + B * (B + 1);    // right-hand side of the block, then its solution
@@ -393,9 +395,9 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t l
         float v = 0.f;
         if (i < n) {
             const int src = perm[i];
-            if (mode == 0) {
-                const double rn = __longlong_as_double((long long)dev->rnorm_bits);
-                v = __double2float_rn(r[src] / rn);
+            if (mode != 1) {
+                const double rn = __longlong_as_double((long long)*rho_bits);
+                v = (rn == 0.0) ? 0.f : __double2float_rn(r[src] / rn);
             } else {
                 v = vin[src];
             }
@@ -431,13 +433,16 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t l
 }
 
 // Back substitution with U, reading the tagged y of the lower solve.
-// mode 0: d = (||r|| s) fl64(z); x += d; ||d|| into dev; mode 1: dout = z.
+// mode 0: d = (rho s) fl64(z); x += d; ||d|| into dev; mode 1: dout = z;
+// mode 2: x = (rho s) fl64(z).
 __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t ldf, int n, int nblk,
                                                       const float *Uinv, const int32_t *blk_subst,
                                                       const unsigned long long *ytag,
                                                       unsigned long long *ztag, unsigned tag,
-                                                      int mode, double *x, float *dout,
+                                                      int mode, const unsigned long long *rho_bits,
+                                                      const int *skip, double *x, float *dout,
                                                       DevScalars *dev) {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) float tsm[];
     float *Ds = tsm;
     float *sv = Ds + B * (B + 1);
@@ -483,11 +488,15 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
         const float zv = (i < n) ? sv[t] : 0.f;
         st_relaxed_u64(ztag + i, ((unsigned long long)tag << 32) | __float_as_uint(zv));
         if (i < n) {
-            if (mode == 0) {
-                const double scale = __longlong_as_double((long long)dev->rnorm_bits) * dev->scale;
+            if (mode != 1) {
+                const double scale = __longlong_as_double((long long)*rho_bits) * dev->scale;
                 const double d = scale * (double)zv;
-                x[i] += d;
-                dmax = fabs(d);
+                if (mode == 0) {
+                    x[i] += d;
+                    dmax = fabs(d);
+                } else {
+                    x[i] = d;
+                }
             } else {
                 dout[i] = zv;
             }
@@ -524,7 +533,8 @@ cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *L
                              const float *Uinv, const int32_t *blk_subst, const int32_t *perm, const double *r,
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
-                             cudaStream_t s) {
+                             cudaStream_t s, const unsigned long long *rho_bits, double *pw,
+                             const int *skip) {
     if (n == 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
@@ -537,16 +547,18 @@ cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *L
     const int nblk = (n + B - 1) / B;
     cudaError_t e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
-    const int mode = vin ? 1 : 0;
+    const int mode = vin ? 1 : (pw ? 2 : 0);
+    if (mode != 2) rho_bits = &dev->rnorm_bits;
+    double *xo = (mode == 2) ? pw : x;
     unsigned long long *ytag = tags, *ztag = tags + (int64_t)nblk * B;
     count_launch();
-    k_trsv_lower<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode, ytag, epoch,
-                                              dev);
+    k_trsv_lower<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode, rho_bits, skip,
+                                              ytag, epoch, dev);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_trsv_upper<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, epoch, mode, x, dout,
-                                              dev);
+    k_trsv_upper<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, epoch, mode, rho_bits,
+                                              skip, xo, dout, dev);
     return cudaGetLastError();
 }
 

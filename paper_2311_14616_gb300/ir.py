@@ -59,6 +59,12 @@ class BatchResult(ctypes.Structure):
 
 
 BATCH_MAX_N = 512
+MAX_BASIS = 64
+
+
+class KrylovOpts(ctypes.Structure):
+    """ir_krylov_opts: GMRES basis size, its stopping tolerance, the residual-stagnation factor."""
+    _fields_ = [("basissize", ctypes.c_int), ("eta", ctypes.c_double), ("Rmax_r", ctypes.c_double)]
 
 
 @dataclass
@@ -69,6 +75,7 @@ class Report:
     dhist: List[float] = field(default_factory=list)
     info: int = 0
     scale: float = 1.0
+    khist: List[int] = field(default_factory=list)   # GMRES iterations per step (GMRES-IR)
 
 
 _lib = None
@@ -94,6 +101,9 @@ def lib():
             "ir_solve": (i32, [vp, vp, vp, P(Term), vp, P(_Report)]),
             "ir_solve_host": (i32, [vp, i64, vp, i64, vp, vp, P(Opts), P(Term), vp, P(_Report)]),
             "ir_lu_solve": (i32, [vp, vp, vp, vp]),
+            "ir_default_krylov_opts": (None, [P(KrylovOpts)]),
+            "ir_gmres_reserve": (i32, [vp, i32]),
+            "ir_solve_gmres": (i32, [vp, vp, vp, P(Term), P(KrylovOpts), vp, P(_Report), vp]),
             "ir_residual": (i32, [vp, i64, i32, vp, i64, vp, vp, vp, vp, vp]),
             "ir_batch_create": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), P(vp)]),
             "ir_batch_run": (i32, [vp, vp, vp]),
@@ -155,6 +165,15 @@ def default_term(**kw) -> Term:
     for k, v in kw.items():
         setattr(t, k, v)
     return t
+
+
+def krylov_opts(**kw) -> KrylovOpts:
+    """ir_krylov_opts with the defaults (basissize 10, eta 1e-8, Rmax_r 1) and overrides."""
+    k = KrylovOpts()
+    lib().ir_default_krylov_opts(ctypes.byref(k))
+    for name, v in kw.items():
+        setattr(k, name, v)
+    return k
 
 
 def make_opts(TW: int, TF: int, fp16_scale: bool = True, nb: int = 0) -> Opts:
@@ -359,6 +378,33 @@ class Factorization:
         code = lib().ir_solve(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(x.data_ptr()),
                               ctypes.byref(t), _stream_ptr(stream), ctypes.byref(rep) if report else None)
         R = _report(rep) if report else None
+        if code != 0:
+            L = lib()
+            err = IRError(code, f"{L.ir_strerror(code).decode()} ({L.ir_last_error().decode()})")
+            err.report = R
+            raise err
+        return x, R
+
+    def gmres_reserve(self, basissize: int = 10):
+        """Reserve the Krylov basis (mpglu's allocation, Sec. 4.4)."""
+        _check(lib().ir_gmres_reserve(self._h, int(basissize)))
+
+    def solve_gmres(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, term: Optional[Term] = None,
+                    kopts: Optional[KrylovOpts] = None, stream=None, report: bool = True):
+        """GMRES-IR (Sec. 4.3): returns (x, Report with khist)."""
+        bb = b.to(self.A.dtype).contiguous()
+        if x is None:
+            x = torch.empty_like(bb)
+        rep = _Report()
+        kh = (ctypes.c_int * MAX_HIST)()
+        t = term if term is not None else default_term()
+        ko = kopts if kopts is not None else krylov_opts()
+        code = lib().ir_solve_gmres(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.byref(t), ctypes.byref(ko), _stream_ptr(stream),
+                                    ctypes.byref(rep) if report else None, kh)
+        R = _report(rep) if report else None
+        if R is not None:
+            R.khist = list(kh[: R.iters])
         if code != 0:
             L = lib()
             err = IRError(code, f"{L.ir_strerror(code).decode()} ({L.ir_last_error().decode()})")

@@ -17,7 +17,8 @@ def _declared():
 def test_header_declares_the_boundary():
     names = _declared()
     for must in ("ir_init", "ir_factor", "ir_refactor", "ir_solve", "ir_solve_host", "ir_lu_solve",
-                 "ir_residual", "ir_fact_pivots", "ir_fact_factors", "ir_fact_destroy", "ir_finalize"):
+                 "ir_residual", "ir_fact_pivots", "ir_fact_factors", "ir_fact_destroy", "ir_finalize",
+                 "ir_gmres_reserve", "ir_solve_gmres", "ir_default_krylov_opts"):
         assert must in names
 
 
@@ -36,6 +37,9 @@ def test_defaults_and_strerror_without_gpu():
     o = ir.make_opts(ir.F64, ir.F32)
     assert (o.TW, o.TF, o.TR, o.fp16_scale) == (ir.F64, ir.F32, ir.F64, 1)
     assert ir.lib().ir_strerror(4) == b"zero pivot in the factorization"
+    k = ir.krylov_opts()
+    assert (k.basissize, k.eta, k.Rmax_r) == (10, 1e-8, 1.0)
+    assert ctypes.sizeof(ir.KrylovOpts) == 24
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):
