@@ -233,6 +233,7 @@ class Term:
     Rmax: float = 0.5
     litmax: int = 10
     abs_rel_tol: float = 0.0  # > 0: converged iff ||r|| <= abs_rel_tol ||b||
+    mode: int = 0             # 0: small residual (eq. residterm); 1: small backward error (eq. term)
 
 
 @dataclass
@@ -253,12 +254,15 @@ class IRResult:
 
 
 def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: bool,
-                rmax_r: Optional[float] = None):
+                rmax_r: Optional[float] = None, anorm: float = 0.0, xnorm: float = 0.0):
     """Termination test of Sec. 5.1, applied after each residual computation.
 
     rhist = [||r_0||, ..., ||r_k||] (r_0 = b), dhist = [||d_0||, ..., ||d_{k-1}||].
     rmax_r replaces R_max in the residual-stagnation test (eq. stag) when
     given (GMRES-IR); the correction test (eq. wilkterm) keeps term.Rmax.
+    term.mode = 1 replaces eq. (residterm) by the backward-error test eq. (term),
+    ||r|| <= C_e u_W (||b|| + ||A|| ||x||), with anorm = ||A||_1 and xnorm =
+    ||x||_inf of the current iterate.
     Returns a status code, or None to continue.
     """
     k = len(rhist) - 1
@@ -274,9 +278,13 @@ def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: 
         if len(dhist) >= 2 and dhist[-1] >= term.Rmax * dhist[-2]:
             return STAGNATED
     else:
-        tol = term.abs_rel_tol if term.abs_rel_tol > 0 else term.Cr * eps_w
-        if rn <= tol * bnorm:             # eq. (residterm)
-            return CONVERGED
+        if term.mode == 1:
+            if rn <= term.Ce * eps_w * (bnorm + anorm * xnorm):    # eq. (term)
+                return CONVERGED
+        else:
+            tol = term.abs_rel_tol if term.abs_rel_tol > 0 else term.Cr * eps_w
+            if rn <= tol * bnorm:             # eq. (residterm)
+                return CONVERGED
         rm = term.Rmax if rmax_r is None else rmax_r
         if k >= 1 and rn >= rm * rhist[-2]:   # eq. (stag)
             return STAGNATED
@@ -318,6 +326,7 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
     if bnorm == 0.0:
         res.status = CONVERGED
         return res
+    anorm = norm1(A) if term.mode == 1 else 0.0
     r = b64.copy()
     while True:
         rho = float(np.max(np.abs(r)))
@@ -327,7 +336,8 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
         res.dhist.append(float(np.max(np.abs(d))))
         r = residual(A, b64, x)
         res.rhist.append(float(np.max(np.abs(r))))
-        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, term, tr_wider)
+        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, term, tr_wider,
+                         anorm=anorm, xnorm=float(np.max(np.abs(x))))
         if st is not None:
             res.status = st
             break
@@ -495,7 +505,7 @@ def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] =
     if bnorm == 0.0:
         res.status = CONVERGED
         return res
-    tterm = Term(Cr=term.Cr, Ce=term.Ce, Rmax=term.Rmax, litmax=term.litmax, abs_rel_tol=term.abs_rel_tol)
+    anorm = norm1(A) if term.mode == 1 else 0.0
     r = b64.copy()
     while True:
         d, k = gmres_correction(A, LU, ipiv, s, r, kopts.basissize, kopts.eta)
@@ -504,7 +514,8 @@ def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] =
         res.dhist.append(float(np.max(np.abs(d))))
         r = residual(A, b64, x)
         res.rhist.append(float(np.max(np.abs(r))))
-        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, tterm, tr_wider, rmax_r=kopts.Rmax_r)
+        st = term_decide(res.rhist, res.dhist, bnorm, eps_w, term, tr_wider, rmax_r=kopts.Rmax_r,
+                         anorm=anorm, xnorm=float(np.max(np.abs(x))))
         if st is not None:
             res.status = st
             break
@@ -539,6 +550,15 @@ def reference_solution(A: np.ndarray, b: np.ndarray, maxit: int = 10) -> np.ndar
             break
         dold = dn
     return x
+
+
+def norm1(A: np.ndarray) -> float:
+    """||A||_1 = max_j sum_i |a_ij| in binary64 (the operator norm of the
+    backward-error test eq. (term); Sec. 5.1.1 and the OPNORM column of Sec. 5.2)."""
+    A64 = np.asarray(A, dtype=np.float64)
+    if A64.size == 0:
+        return 0.0
+    return float(np.max(np.sum(np.abs(A64), axis=0)))
 
 
 def inverse_f64(A: np.ndarray) -> np.ndarray:

@@ -456,3 +456,46 @@ def test_scalar_promoted_problem_stops_at_exact_solution(a, b):
     exact = np.float64(bb[0]) / np.float64(A[0, 0])
     assert res.sol[0] == np.float32(exact)
     assert abs(res.x[0] - exact) <= 2 * np.spacing(abs(exact))
+
+
+# ---------------------------------------------------------------------------
+# backward-error termination (Sec. 5.1.1, eq. term) and ||A||_1
+# ---------------------------------------------------------------------------
+
+def test_norm1_is_the_column_sum_norm():
+    # nonsymmetric: ||A||_1 (columns) = 9 differs from ||A||_inf (rows) = 7, so a
+    # transposed operand fails
+    A = np.asfortranarray(np.array([[1.0, -4.0, 0.0], [2.0, 0.0, 3.0], [0.0, 5.0, -1.0]]))
+    assert O.norm1(A) == 9.0
+    assert O.norm1(A.astype(np.float32)) == 9.0
+    assert O.norm1(np.zeros((0, 0))) == 0.0
+
+
+def test_backward_error_test_replaces_the_residual_test():
+    t = O.Term(mode=1)
+    eps = 2.0 ** -52
+    # ||r|| = 1e-14: far above eps ||b|| (residterm fails) but below eps (||b|| + ||A|| ||x||)
+    rh = [1.0, 1e-3, 1e-14]
+    assert O.term_decide(rh, [1, 1], 1.0, eps, O.Term(), False) is None
+    assert O.term_decide(rh, [1, 1], 1.0, eps, t, False, anorm=100.0, xnorm=1000.0) == O.CONVERGED
+    assert O.term_decide(rh, [1, 1], 1.0, eps, t, False, anorm=1.0, xnorm=1.0) is None
+    # C_e scales the bound
+    assert O.term_decide(rh, [1, 1], 1.0, eps, O.Term(mode=1, Ce=100.0), False, anorm=1.0, xnorm=1.0) \
+        == O.CONVERGED
+    # TR wider than TW: only the correction test stops the loop, whatever the mode
+    assert O.term_decide(rh, [1.0, 0.9], 1.0, 2.0 ** -23, t, True, anorm=1e9, xnorm=1e9) == O.STAGNATED
+
+
+def test_ir_backward_error_termination_on_ill_conditioned_system():
+    """I - 799 G at N = 512 (the system of Sec. 5.1.3): the residual floor is far
+    above eps ||b||, so eq. (residterm) never holds and the loop ends on
+    stagnation; ||A|| ||x|| ~ 5e4 makes eq. (term) hold at that floor, one
+    step earlier and with the same iterate."""
+    A = np.asfortranarray(np.eye(512) - 799.0 * irgen.gmat_trapezoid(512))
+    b = np.ones(512)
+    r0 = O.ir_solve(A, b, O.F32)
+    r1 = O.ir_solve(A, b, O.F32, O.Term(mode=1))
+    assert r0.status == O.STAGNATED and r1.status == O.CONVERGED
+    assert r1.iters == r0.iters - 1
+    assert r1.rhist == r0.rhist[:-1]
+    assert r1.rhist[-1] <= 2.0 ** -52 * (1.0 + O.norm1(A) * np.max(np.abs(r1.x)))
