@@ -56,18 +56,22 @@ typedef enum {
 
 /* Termination parameters: the TERM structure of Sec. 5.1.3.
  *   converged   if ||r|| == 0 (x is exact; r / ||r|| would be undefined)
- *               or ||r|| <= Cr * eps(TW) * ||b||         (eq. residterm)
- *               or, when abs_rel_tol > 0, ||r|| <= abs_rel_tol * ||b||
+ *               or, mode 0, ||r|| <= Cr * eps(TW) * ||b||  (eq. residterm)
+ *                  (when abs_rel_tol > 0: ||r|| <= abs_rel_tol * ||b||)
+ *               or, mode 1, ||r|| <= Ce * eps(TW) * (||b|| + ||A||_1 ||x||)
+ *                  (eq. term, the normwise backward error; ||A||_1 is computed
+ *                  in binary64 from A once per factorization, on first use)
  *   stagnated   if ||r_new|| >= Rmax ||r_old||           (eq. stag), TR == TW
  *               if ||d_new|| >= Rmax ||d_old||           (eq. wilkterm), TR wider than TW
  *   stop        after litmax residual computations.
  * Norms are infinity norms; eps(T) is 2^-52 (FP64) or 2^-23 (FP32). */
 typedef struct {
     double Cr;            /* default 1.0 */
-    double Ce;            /* default 1.0 (backward-error test, not used by this build) */
+    double Ce;            /* default 1.0 (backward-error test, mode 1) */
     double Rmax;          /* default 0.5 */
     int litmax;           /* default 10, at most IR_MAX_HIST - 1 */
-    int mode;             /* 0: residual test (the only mode of this build) */
+    int mode;             /* 0: small residual (default); 1: small backward error.
+                             The batched driver supports mode 0 only (IR_EUNSUPPORTED). */
     double abs_rel_tol;   /* > 0 overrides Cr * eps(TW) */
 } ir_term;
 

@@ -28,11 +28,11 @@ namespace {
 // call on the launching stream, summed per kind when profiling stops.
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
-    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_N
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
-                                "batched", "gm_orth", "gm_update"};
+                                "batched", "gm_orth", "gm_update", "norm1"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -368,17 +368,23 @@ ir_status read_dev(ir_fact *f, cudaStream_t s) {
 
 // Termination test of Sec. 5.1 after the k-th residual (rh[0..k], dh[0..k-1]).
 // Returns -1 to continue, else an ir_solve_status.
-// rmax_r: the factor of the residual-stagnation test (t->Rmax for IR).
+// rmax_r: the factor of the residual-stagnation test (t->Rmax for IR).  With
+// t->mode = 1 the small-residual test is the backward-error test (eq. term),
+// anorm = ||A||_1, xnorm = ||x||_inf of the current iterate.
 int term_decide(const double *rh, const double *dh, int k, double bnorm, double eps_w,
-                const ir_term *t, bool tr_wider, double rmax_r) {
+                const ir_term *t, bool tr_wider, double rmax_r, double anorm, double xnorm) {
     const double rn = rh[k];
     if (!std::isfinite(rn)) return IR_DIVERGED;
     if (rn == 0.0) return IR_CONVERGED;    // exact solution: r / ||r|| (eq. vdlow) is undefined next
     if (tr_wider) {
         if (k >= 2 && dh[k - 1] >= t->Rmax * dh[k - 2]) return IR_STAGNATED;   // eq. (wilkterm)
     } else {
-        const double tol = t->abs_rel_tol > 0 ? t->abs_rel_tol : t->Cr * eps_w;
-        if (rn <= tol * bnorm) return IR_CONVERGED;                           // eq. (residterm)
+        if (t->mode == 1) {
+            if (rn <= t->Ce * eps_w * (bnorm + anorm * xnorm)) return IR_CONVERGED;   // eq. (term)
+        } else {
+            const double tol = t->abs_rel_tol > 0 ? t->abs_rel_tol : t->Cr * eps_w;
+            if (rn <= tol * bnorm) return IR_CONVERGED;                       // eq. (residterm)
+        }
         if (k >= 1 && rn >= rmax_r * rh[k - 1]) return IR_STAGNATED;          // eq. (stag)
     }
     if (k >= t->litmax) return IR_MAXIT;
@@ -524,6 +530,7 @@ ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda, const ir
     if (st != IR_OK) return st;
     f->A = A;
     f->lda = lda;
+    f->anorm_valid = 0;
     st = run_factor(f, (cudaStream_t)stream);
     if (st != IR_OK) {
         free_fact(f);
@@ -537,6 +544,7 @@ ir_status ir_refactor(ir_fact *f, const void *B, int64_t ldb, void *stream) {
     if (!f || (f->n > 0 && !B) || ldb < (f->n > 1 ? f->n : 1)) return IR_EINVAL;
     f->A = B;
     f->lda = ldb;
+    f->anorm_valid = 0;
     return run_factor(f, (cudaStream_t)stream);
 }
 
@@ -556,7 +564,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     ir_term t;
     if (term) t = *term;
     else ir_default_term(&t);
-    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0) || (t.mode != 0 && t.mode != 1))
+        return IR_EINVAL;
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t n = f->n;
     ir_report R;
@@ -594,6 +603,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     RUN(KC_INIT, s, launch_init_rb(n, f->TW, b, f->r, f->x, f->dev, s));
     CK(cudaMemcpyAsync(&f->dev->rnorm_bits, &f->dev->bnorm_bits, sizeof(unsigned long long),
                        cudaMemcpyDeviceToDevice, s));
+    if (t.mode == 1 && !f->anorm_valid)
+        RUN(KC_NORM1, s, launch_norm1(n, f->TW, f->A, f->lda, &f->dev->anorm_bits, s));
     st = read_dev(f, s);
     if (st != IR_OK) return st;
     if (f->host_dev->nonfinite) {
@@ -601,6 +612,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
         if (rep) *rep = R;
         return IR_ENONFINITE;
     }
+    if (t.mode == 1) f->anorm_valid = 1;
+    const double anorm = bits_to_double(f->host_dev->anorm_bits);
     const double bnorm = bits_to_double(f->host_dev->bnorm_bits);
     R.rhist[0] = bnorm;
     const bool tr_wider = (f->TW == IR_F32);
@@ -609,7 +622,7 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
     while (status < 0) {
         f->epoch += 1;
-        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, sizeof(unsigned long long), s));
+        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
         RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
                                          nullptr, nullptr, f->x, f->tags, f->epoch, f->dev, s));
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
@@ -623,7 +636,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
         ++k;
         R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
         R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
-        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, t.Rmax);
+        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, t.Rmax, anorm,
+                             bits_to_double(f->host_dev->xnorm_bits));
     }
     RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
     R.iters = k;
@@ -674,7 +688,8 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
     ir_krylov_opts ko;
     if (kopts) ko = *kopts;
     else ir_default_krylov_opts(&ko);
-    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0) || (t.mode != 0 && t.mode != 1))
+        return IR_EINVAL;
     if (ko.basissize < 1 || ko.basissize > IR_MAX_BASIS || !(ko.eta >= 0) || !(ko.Rmax_r > 0)) return IR_EINVAL;
     if (khist) std::memset(khist, 0, IR_MAX_HIST * sizeof(int));
     cudaStream_t s = (cudaStream_t)stream;
@@ -714,6 +729,8 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
     RUN(KC_INIT, s, launch_init_rb(n, f->TW, b, f->r, f->x, f->dev, s));
     CK(cudaMemcpyAsync(&f->dev->rnorm_bits, &f->dev->bnorm_bits, sizeof(unsigned long long),
                        cudaMemcpyDeviceToDevice, s));
+    if (t.mode == 1 && !f->anorm_valid)
+        RUN(KC_NORM1, s, launch_norm1(n, f->TW, f->A, f->lda, &f->dev->anorm_bits, s));
     st = read_dev(f, s);
     if (st != IR_OK) return st;
     if (f->host_dev->nonfinite) {
@@ -721,6 +738,8 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
         if (rep) *rep = R;
         return IR_ENONFINITE;
     }
+    if (t.mode == 1) f->anorm_valid = 1;
+    const double anorm = bits_to_double(f->host_dev->anorm_bits);
     const double bnorm = bits_to_double(f->host_dev->bnorm_bits);
     R.rhist[0] = bnorm;
     const bool tr_wider = (f->TW == IR_F32);
@@ -750,8 +769,8 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
                                              &gs->wnorm_bits, V + (int64_t)(j + 1) * ldv, &gs->done));
             RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, j, m, ko.eta, gs, s));
         }
-        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, sizeof(unsigned long long), s));
-        RUN(KC_GM_UPDATE, s, launch_gm_update(nn, V, ldv, gs, f->x, &f->dev->dnorm_bits, s));
+        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
+        RUN(KC_GM_UPDATE, s, launch_gm_update(nn, V, ldv, gs, f->x, &f->dev->dnorm_bits, &f->dev->xnorm_bits, s));
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
                                          f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
         CK(cudaMemcpyAsync(f->gm_host_k, &gs->k, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -765,7 +784,8 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
         ++k;
         R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
         R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
-        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, ko.Rmax_r);
+        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, ko.Rmax_r, anorm,
+                             bits_to_double(f->host_dev->xnorm_bits));
     }
     RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
     R.iters = k;
@@ -818,7 +838,9 @@ ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host, con
     ir_term t;
     if (term) t = *term;
     else ir_default_term(&t);
-    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0)) return IR_EINVAL;
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0) || (t.mode != 0 && t.mode != 1))
+        return IR_EINVAL;
+    if (t.mode != 0) return IR_EUNSUPPORTED;    // the batched driver tests small residuals (eq. residterm)
     int64_t maxn = 0;
     for (int64_t i = 0; i < count; ++i) {
         const int64_t n = n_host[i];

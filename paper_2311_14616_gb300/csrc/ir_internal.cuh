@@ -29,8 +29,10 @@ constexpr int kMaxN = kPanelRows * kPanelMaxCluster;  // 8192 rows per panel clu
 struct DevScalars {
     unsigned long long rnorm_bits;   // ||r||_inf of the latest residual
     unsigned long long dnorm_bits;   // ||d||_inf of the latest correction
+    unsigned long long xnorm_bits;   // ||x||_inf after the latest update (cleared with dnorm_bits)
     unsigned long long bnorm_bits;   // ||b||_inf
     unsigned long long amax_bits;    // max |a_ij| (binary16 scaling)
+    unsigned long long anorm_bits;   // ||A||_1 (backward-error termination)
     double scale;                    // s of the factorization copy
     int info;                        // first zero pivot, 1-based (INT_MAX = none)
     int nonfinite;                   // 1: NaN/Inf met in A, b or the rounded copy
@@ -87,6 +89,7 @@ struct ir_fact {
     unsigned epoch;            // tag of the latest solve
     double *x, *r;           // binary64 iterate and residual
     ir::DevScalars *dev;
+    int anorm_valid;         // dev->anorm_bits holds ||A||_1 of the current A
     ir::DevScalars *host_dev;  // pinned mirror
     // the factorization's launch sequence as a CUDA graph (captured for one A)
     cudaStream_t cap_stream;
@@ -115,6 +118,8 @@ cudaError_t launch_maxabs(int64_t n, ir_dtype tw, const void *A, int64_t lda, De
                           int sms, cudaStream_t s);
 cudaError_t launch_cast(int64_t n, ir_dtype tw, const void *A, int64_t lda, ir_dtype tf,
                         int use_scale, float *AF, int64_t ldf, DevScalars *dev, cudaStream_t s);
+cudaError_t launch_norm1(int64_t n, ir_dtype tw, const void *A, int64_t lda, unsigned long long *out_bits,
+                         cudaStream_t s);
 cudaError_t launch_init_rb(int64_t n, ir_dtype tw, const void *b, double *r, double *x,
                            DevScalars *dev, cudaStream_t s);
 cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s);
@@ -136,7 +141,7 @@ cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
                             int32_t *blk_subst, cudaStream_t s);
 // Solve pair in one of three modes:
-//   refinement (vin = pw = NULL): x += (||r|| s) fl64(U^{-1} L^{-1} fl32(P r / ||r||)), ||d|| into dev;
+//   refinement (vin = pw = NULL): x += (||r|| s) fl64(U^{-1} L^{-1} fl32(P r / ||r||)), ||d||, ||x|| into dev;
 //   raw (vin != NULL): dout = U^{-1} L^{-1} P vin in binary32;
 //   preconditioner (pw != NULL): pw = (rho s) fl64(U^{-1} L^{-1} fl32(P r / rho)), rho from rho_bits.
 // skip != NULL: every CTA returns at once while *skip != 0.
@@ -157,9 +162,9 @@ cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, 
 // Gram-Schmidt twice), normalize, rotate column j of H, set done.
 cudaError_t launch_gm_orth(int n, double *V, int64_t ldv, int j, int m, double eta, GmState *st,
                            cudaStream_t s);
-// d = V_k R^{-1} g; x += d; ||d||_inf into dnorm_bits.
+// d = V_k R^{-1} g; x += d; ||d||_inf into dnorm_bits, ||x||_inf into xnorm_bits.
 cudaError_t launch_gm_update(int n, const double *V, int64_t ldv, const GmState *st, double *x,
-                             unsigned long long *dnorm_bits, cudaStream_t s);
+                             unsigned long long *dnorm_bits, unsigned long long *xnorm_bits, cudaStream_t s);
 int64_t residual_partials_needed(int64_t n, int sms);
 
 // batched driver (many systems with n <= IR_BATCH_MAX_N, one persistent launch)

@@ -133,6 +133,41 @@ int grid_for(int64_t work, int threads, int cap) {
 
 }  // namespace
 
+// ||A||_1 = max_j sum_i |a_ij| in binary64 (Sec. 5.1.1, eq. term; the OPNORM of
+// Sec. 5.2): one warp per column (coalesced over the column-major rows), lane
+// partial sums in row order, then a butterfly; the maximum over columns by an
+// atomic maximum on ordered bit patterns, so the result is deterministic.
+template <typename TW>
+__global__ void __launch_bounds__(256) k_norm1(int64_t n, const TW *A, int64_t lda, unsigned long long *out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    double m = 0.0;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n; j += warps) {
+        const TW *col = A + j * lda;
+        double s = 0.0;
+        for (int64_t i = lane; i < n; i += 32) s += fabs(ld_w(col + i));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        m = fmax(m, s);
+        if (s != s) m = s;
+    }
+    if (lane == 0) atomic_max_nonneg(out, m);
+}
+
+cudaError_t launch_norm1(int64_t n, ir_dtype tw, const void *A, int64_t lda, unsigned long long *out_bits,
+                         cudaStream_t s) {
+    cudaError_t e = cudaMemsetAsync(out_bits, 0, sizeof(unsigned long long), s);
+    if (e != cudaSuccess || n == 0) return e;
+    int64_t g = (n + 7) / 8;
+    if (g > 1216) g = 1216;
+    count_launch();
+    if (tw == IR_F64)
+        k_norm1<double><<<(unsigned)g, 256, 0, s>>>(n, (const double *)A, lda, out_bits);
+    else
+        k_norm1<float><<<(unsigned)g, 256, 0, s>>>(n, (const float *)A, lda, out_bits);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_maxabs(int64_t n, ir_dtype tw, const void *A, int64_t lda, DevScalars *dev,
                           int sms, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

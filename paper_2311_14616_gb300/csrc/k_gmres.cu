@@ -3,8 +3,8 @@
 // residual kernels with b = NULL and the solve pair with P = U^{-1} L^{-1},
 // eq. pdef).
 //
-// k_gm_orth: one thread-block cluster, one basis row per thread (512 rows per
-// CTA, up to 16 CTAs = 8192 rows).  Classical Gram-Schmidt run twice against
+// k_gm_orth: one thread-block cluster of up to 16 CTAs x 256 threads, one or
+// two basis rows per thread (8192 rows at most).  Classical Gram-Schmidt run twice against
 // v_0..v_j, the 2-norm, the normalization of v_{j+1}, then the Givens step on
 // column j of the Hessenberg matrix and the stopping test.  Every dot product
 // is summed lane-butterfly -> warps in order -> CTAs in rank order through
@@ -20,90 +20,181 @@ namespace cg = cooperative_groups;
 namespace ir {
 namespace {
 
-constexpr int OT = 512;               // threads per CTA = basis rows per CTA
+constexpr int OT = 256;               // threads per CTA
 constexpr int OW = OT / 32;
 constexpr int kOrthMaxCluster = 16;
-constexpr int kChunk = 8;             // basis columns loaded together
+constexpr int kChunk = 4;             // dot products reduced together
 
-__device__ __forceinline__ double warp_sum(double v) {
+// Butterfly sum of one value over the warp (every lane ends with the total).
+__device__ __forceinline__ double warp_sum1(double v) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     return v;
 }
 
-// res[l] = sum_i V_il w_i for l < cnt, or (V == NULL, cnt = 1) res[0] = sum_i w_i^2,
-// over the rows of the whole cluster.  mine: this CTA's slot of the exchange,
-// a different one per call so that no CTA overwrites a slot another still reads.
-__device__ void cluster_dots(const cg::cluster_group &cl, const double *V, int64_t ldv, int i, bool on,
-                             double w, int cnt, double (*wsum)[kMaxBasis + 1], double *mine, double *res) {
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    for (int l0 = 0; l0 < cnt; l0 += kChunk) {
-        double v[kChunk];
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q)
-            v[q] = (on && l0 + q < cnt) ? (V ? V[(int64_t)(l0 + q) * ldv + i] : w) : 0.0;
-#pragma unroll
-        for (int q = 0; q < kChunk; ++q) {
-            if (l0 + q >= cnt) break;
-            const double p = warp_sum(v[q] * w);
-            if (lane == 0) wsum[warp][l0 + q] = p;
-        }
-    }
+// Warp sums of four values by recursive halving: 6 binary64 additions per lane
+// instead of 20 (binary64 throughput is the scarce resource on this part).
+// Lane l ends with the total of value q(l) = 2 * bit4(l) + bit3(l).
+__device__ __forceinline__ double warp_sum4(const double (&p)[4], int lane) {
+    const bool h16 = lane & 16, h8 = lane & 8;
+    double k0 = h16 ? p[2] : p[0], k1 = h16 ? p[3] : p[1];
+    k0 += __shfl_xor_sync(0xffffffffu, h16 ? p[0] : p[2], 16);
+    k1 += __shfl_xor_sync(0xffffffffu, h16 ? p[1] : p[3], 16);
+    double k = h8 ? k1 : k0;
+    k += __shfl_xor_sync(0xffffffffu, h8 ? k0 : k1, 8);
+    k += __shfl_xor_sync(0xffffffffu, k, 4);
+    k += __shfl_xor_sync(0xffffffffu, k, 2);
+    k += __shfl_xor_sync(0xffffffffu, k, 1);
+    return k;
+}
+
+// Sum the per-warp partials of wsum[.][0..cnt) in warp order into this CTA's
+// exchange slot, then the slots of all CTAs in rank order into res (every CTA
+// gets bitwise the same totals).  mine is a different slot per call so that no
+// CTA overwrites a slot another still reads.
+__device__ __forceinline__ void cluster_total(const cg::cluster_group &cl, int cnt, double (*wsum)[kMaxBasis + 1],
+                                              double *mine, double *res) {
+    const int t = threadIdx.x;
     __syncthreads();
     if (t < cnt) {
+        double v[OW];
+#pragma unroll
+        for (int q = 0; q < OW; ++q) v[q] = wsum[q][t];
         double s = 0.0;
-        for (int q = 0; q < OW; ++q) s += wsum[q][t];
+#pragma unroll
+        for (int q = 0; q < OW; ++q) s += v[q];
         mine[t] = s;
     }
     cl.sync();
     if (t < cnt) {
+        const unsigned C = cl.num_blocks();
+        double v[kOrthMaxCluster];
+#pragma unroll
+        for (unsigned r = 0; r < kOrthMaxCluster; ++r) v[r] = (r < C) ? cl.map_shared_rank(mine, r)[t] : 0.0;
         double s = 0.0;
-        for (unsigned r = 0; r < cl.num_blocks(); ++r) s += cl.map_shared_rank(mine, r)[t];
+#pragma unroll
+        for (unsigned r = 0; r < kOrthMaxCluster; ++r)
+            if (r < C) s += v[r];
         res[t] = s;
     }
     __syncthreads();
 }
 
-// w -= V_{0..cnt-1} h (fma chain over ascending l).
-__device__ __forceinline__ double subtract_projection(const double *V, int64_t ldv, int i, bool on, double w,
-                                                      int cnt, const double *h) {
-    if (!on) return w;
+// res[l] = sum over the cluster's rows of V_il w_i, l < cnt.  A thread's RPT
+// rows are combined first (fma in row order), then warps, CTAs, the cluster.
+template <int RPT>
+__device__ void cluster_dots(const cg::cluster_group &cl, const double *V, int64_t ldv, const int (&i)[RPT],
+                             const bool (&on)[RPT], const double (&w)[RPT], int cnt,
+                             double (*wsum)[kMaxBasis + 1], double *mine, double *res) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int l0 = 0; l0 < cnt; l0 += kChunk) {
-        double v[kChunk];
+        double p[kChunk];
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q) v[q] = (l0 + q < cnt) ? V[(int64_t)(l0 + q) * ldv + i] : 0.0;
+        for (int q = 0; q < kChunk; ++q) {
+            double acc = 0.0;
 #pragma unroll
-        for (int q = 0; q < kChunk; ++q)
-            if (l0 + q < cnt) w = fma(-v[q], h[l0 + q], w);
+            for (int r = 0; r < RPT; ++r)
+                if (on[r] && l0 + q < cnt) acc = fma(V[(int64_t)(l0 + q) * ldv + i[r]], w[r], acc);
+            p[q] = acc;
+        }
+        const double sum = warp_sum4(p, lane);
+        const int q = 2 * ((lane >> 4) & 1) + ((lane >> 3) & 1);
+        if ((lane & 7) == 0 && l0 + q < cnt) wsum[warp][l0 + q] = sum;
     }
-    return w;
+    cluster_total(cl, cnt, wsum, mine, res);
+}
+
+// res[0] = sum over the cluster's rows of w_i^2.
+template <int RPT>
+__device__ void cluster_norm2(const cg::cluster_group &cl, const bool (&on)[RPT], const double (&w)[RPT],
+                              double (*wsum)[kMaxBasis + 1], double *mine, double *res) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double acc = 0.0;
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+        if (on[r]) acc = fma(w[r], w[r], acc);
+    acc = warp_sum1(acc);
+    if (lane == 0) wsum[warp][0] = acc;
+    cluster_total(cl, 1, wsum, mine, res);
+}
+
+// w -= V_{0..cnt-1} h for each row (fma chain over ascending l).
+template <int RPT>
+__device__ __forceinline__ void subtract_projection(const double *V, int64_t ldv, const int (&i)[RPT],
+                                                    const bool (&on)[RPT], double (&w)[RPT], int cnt,
+                                                    const double *h) {
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        if (!on[r]) continue;
+        for (int l0 = 0; l0 < cnt; l0 += kChunk) {
+            double v[kChunk];
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q) v[q] = (l0 + q < cnt) ? V[(int64_t)(l0 + q) * ldv + i[r]] : 0.0;
+#pragma unroll
+            for (int q = 0; q < kChunk; ++q)
+                if (l0 + q < cnt) w[r] = fma(-v[q], h[l0 + q], w[r]);
+        }
+    }
 }
 
 // j = -1: column 0 holds P r; beta = ||P r||_2, v_0 = P r / beta, g_0 = beta.
 // j >= 0: column j + 1 holds P A v_j; orthogonalize, normalize and rotate.
+// CTA c of the cluster owns rows c RPT OT .. (c + 1) RPT OT - 1, thread t rows
+// c RPT OT + t + r OT (coalesced).
+template <int RPT>
 __global__ void __launch_bounds__(OT, 1) k_gm_orth(int n, double *V, int64_t ldv, int j, int m, double eta,
                                                     GmState *st) {
     cg::cluster_group cl = cg::this_cluster();
     __shared__ double wsum[OW][kMaxBasis + 1];
     __shared__ double part[3][kMaxBasis + 1];
     __shared__ double h[3][kMaxBasis + 1];
+    __shared__ double rot[2][kMaxBasis];   // the earlier rotations (c, s), read while the dots run
+    __shared__ double gb[2];               // g_j, beta
+    __shared__ double colj[kMaxBasis + 1]; // column j of H while it is rotated
+    __shared__ double ninv[2];             // ||w||_2 and its reciprocal
     if (j >= 0 && st->done) return;      // uniform: written by an earlier launch
     const int t = threadIdx.x;
     const unsigned rank = cl.block_rank();
-    const int i = (int)rank * OT + t;
-    const bool on = i < n;
+    if (rank == 0 && j >= 0) {
+        if (t < j) {
+            rot[0][t] = st->cs[t];
+            rot[1][t] = st->sn[t];
+        }
+        if (t == 0) {
+            gb[0] = st->g[j];
+            gb[1] = st->beta;
+        }
+    }
+    int i[RPT];
+    bool on[RPT];
+    double w[RPT];
     const int nv = j + 1;                 // vectors already in the basis
     double *col = V + (int64_t)(j + 1) * ldv;
-    double w = on ? col[i] : 0.0;
-    if (j >= 0) {
-        cluster_dots(cl, V, ldv, i, on, w, nv, wsum, part[0], h[0]);
-        w = subtract_projection(V, ldv, i, on, w, nv, h[0]);
-        cluster_dots(cl, V, ldv, i, on, w, nv, wsum, part[1], h[1]);
-        w = subtract_projection(V, ldv, i, on, w, nv, h[1]);
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) {
+        i[r] = (int)rank * RPT * OT + r * OT + t;
+        on[r] = i[r] < n;
+        w[r] = on[r] ? col[i[r]] : 0.0;
     }
-    cluster_dots(cl, nullptr, ldv, i, on, w, 1, wsum, part[2], h[2]);
-    const double hn = sqrt(h[2][0]);
-    if (on && hn > 0.0) col[i] = w / hn;
+    if (j >= 0) {
+        cluster_dots<RPT>(cl, V, ldv, i, on, w, nv, wsum, part[0], h[0]);
+        subtract_projection<RPT>(V, ldv, i, on, w, nv, h[0]);
+        cluster_dots<RPT>(cl, V, ldv, i, on, w, nv, wsum, part[1], h[1]);
+        subtract_projection<RPT>(V, ldv, i, on, w, nv, h[1]);
+    }
+    cluster_norm2<RPT>(cl, on, w, wsum, part[2], h[2]);
+    // one thread takes the square root and the reciprocal (binary64 throughput is
+    // scarce: every thread doing them costs microseconds); v_{j+1} = w * (1 / ||w||)
+    if (t == 0) {
+        const double nrm = sqrt(h[2][0]);
+        ninv[0] = nrm;
+        ninv[1] = (nrm > 0.0) ? 1.0 / nrm : 0.0;
+    }
+    __syncthreads();
+    const double hn = ninv[0], inv = ninv[1];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+        if (on[r] && hn > 0.0) col[i[r]] = w[r] * inv;
     if (rank == 0 && t == 0) {
         if (j < 0) {
             st->beta = hn;
@@ -111,10 +202,10 @@ __global__ void __launch_bounds__(OT, 1) k_gm_orth(int n, double *V, int64_t ldv
             st->k = 0;
             st->done = (hn > 0.0) ? 0 : 1;
         } else {
-            double *Rc = st->R + (int64_t)j * kMaxBasis;      // column j
+            double *Rc = colj;
             for (int l = 0; l < nv; ++l) Rc[l] = __dadd_rn(h[0][l], h[1][l]);
             for (int l = 0; l < j; ++l) {                    // earlier rotations
-                const double a = Rc[l], b = Rc[l + 1], c = st->cs[l], s = st->sn[l];
+                const double a = Rc[l], b = Rc[l + 1], c = rot[0][l], s = rot[1][l];
                 Rc[l] = __dadd_rn(__dmul_rn(c, a), __dmul_rn(s, b));
                 Rc[l + 1] = __dadd_rn(__dmul_rn(-s, a), __dmul_rn(c, b));
             }
@@ -125,45 +216,58 @@ __global__ void __launch_bounds__(OT, 1) k_gm_orth(int n, double *V, int64_t ldv
                 s = hn / nu;
             }
             Rc[j] = nu;
+            double *Rg = st->R + (int64_t)j * kMaxBasis;
+            for (int l = 0; l < nv; ++l) Rg[l] = Rc[l];
             st->cs[j] = c;
             st->sn[j] = s;
-            const double gj = st->g[j];
-            st->g[j + 1] = __dmul_rn(-s, gj);
+            const double gj = gb[0], gn = __dmul_rn(-s, gj);
+            st->g[j + 1] = gn;
             st->g[j] = __dmul_rn(c, gj);
             st->k = j + 1;
-            st->done = (fabs(st->g[j + 1]) <= eta * st->beta || hn == 0.0 || j + 1 >= m) ? 1 : 0;
+            st->done = (fabs(gn) <= eta * gb[1] || hn == 0.0 || j + 1 >= m) ? 1 : 0;
         }
     }
     cl.sync();      // no CTA leaves while another may still read its slots
 }
 
 __global__ void __launch_bounds__(256) k_gm_update(int n, const double *V, int64_t ldv, const GmState *st,
-                                                    double *x, unsigned long long *dnorm_bits) {
+                                                    double *x, unsigned long long *dnorm_bits,
+                                                    unsigned long long *xnorm_bits) {
     __shared__ double y[kMaxBasis];
+    __shared__ double Rs[kMaxBasis * kMaxBasis];
     const int k = st->k;
+    for (int e = threadIdx.x; e < k * kMaxBasis; e += blockDim.x) Rs[e] = st->R[e];   // columns 0..k-1
+    if (threadIdx.x < k) y[threadIdx.x] = st->g[threadIdx.x];
+    __syncthreads();
     if (threadIdx.x == 0) {
         for (int i = k - 1; i >= 0; --i) {
-            double acc = st->g[i];
-            for (int l = i + 1; l < k; ++l) acc = __dsub_rn(acc, __dmul_rn(st->R[(int64_t)l * kMaxBasis + i], y[l]));
-            const double rii = st->R[(int64_t)i * kMaxBasis + i];
+            double acc = y[i];
+            for (int l = i + 1; l < k; ++l) acc = __dsub_rn(acc, __dmul_rn(Rs[l * kMaxBasis + i], y[l]));
+            const double rii = Rs[i * kMaxBasis + i];
             y[i] = (rii != 0.0) ? acc / rii : 0.0;
         }
     }
     __syncthreads();
-    double m = 0.0;
+    double m = 0.0, xm = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double d = 0.0;
         for (int l = 0; l < k; ++l) d = fma(V[(int64_t)l * ldv + i], y[l], d);
-        x[i] += d;
+        const double xn = x[i] + d;
+        x[i] = xn;
         m = fmax(m, fabs(d));
         if (d != d) m = d;     // keep a NaN visible to the norm
+        xm = fmax(xm, fabs(xn));
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         const double v = __shfl_xor_sync(0xffffffffu, m, o);
         m = (v != v || v > m) ? v : m;
+        xm = fmax(xm, __shfl_xor_sync(0xffffffffu, xm, o));
     }
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(dnorm_bits, m);
+    if ((threadIdx.x & 31) == 0) {
+        atomic_max_nonneg(dnorm_bits, m);
+        atomic_max_nonneg(xnorm_bits, xm);
+    }
 }
 
 }  // namespace
@@ -171,11 +275,14 @@ __global__ void __launch_bounds__(256) k_gm_update(int n, const double *V, int64
 cudaError_t launch_gm_orth(int n, double *V, int64_t ldv, int j, int m, double eta, GmState *st,
                            cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    const int C = (n + OT - 1) / OT;
+    // one row per thread while 16 CTAs suffice, else two (n <= 8192)
+    const int rpt = (n <= kOrthMaxCluster * OT) ? 1 : 2;
+    const int C = (n + rpt * OT - 1) / (rpt * OT);
     if (C > kOrthMaxCluster || j >= kMaxBasis || m > kMaxBasis) return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
-        const cudaError_t e = cudaFuncSetAttribute(k_gm_orth, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        cudaError_t e = cudaFuncSetAttribute(k_gm_orth<1>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_gm_orth<2>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
         if (e != cudaSuccess) return e;
         attr = true;
     }
@@ -191,16 +298,17 @@ cudaError_t launch_gm_orth(int n, double *V, int64_t ldv, int j, int m, double e
     cfg.attrs = a;
     cfg.numAttrs = 1;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, k_gm_orth, n, V, ldv, j, m, eta, st);
+    if (rpt == 1) return cudaLaunchKernelEx(&cfg, k_gm_orth<1>, n, V, ldv, j, m, eta, st);
+    return cudaLaunchKernelEx(&cfg, k_gm_orth<2>, n, V, ldv, j, m, eta, st);
 }
 
 cudaError_t launch_gm_update(int n, const double *V, int64_t ldv, const GmState *st, double *x,
-                             unsigned long long *dnorm_bits, cudaStream_t s) {
+                             unsigned long long *dnorm_bits, unsigned long long *xnorm_bits, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     int grid = (n + 255) / 256;
     if (grid > 64) grid = 64;
     count_launch();
-    k_gm_update<<<grid, 256, 0, s>>>(n, V, ldv, st, x, dnorm_bits);
+    k_gm_update<<<grid, 256, 0, s>>>(n, V, ldv, st, x, dnorm_bits, xnorm_bits);
     return cudaGetLastError();
 }
 

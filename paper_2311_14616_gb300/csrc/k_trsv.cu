@@ -433,7 +433,7 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t l
 }
 
 // Back substitution with U, reading the tagged y of the lower solve.
-// mode 0: d = (rho s) fl64(z); x += d; ||d|| into dev; mode 1: dout = z;
+// mode 0: d = (rho s) fl64(z); x += d; ||d||, ||x|| into dev; mode 1: dout = z;
 // mode 2: x = (rho s) fl64(z).
 __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t ldf, int n, int nblk,
                                                       const float *Uinv, const int32_t *blk_subst,
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
         if ((lane & 3) == 0) sv[warp * 8 + reduce8_row(lane)] = z;
     }
     __syncthreads();
-    double dmax = 0.0;
+    double dmax = 0.0, xmax = 0.0;
     if (t < B) {
         const int i = r0 + t;
         const float zv = (i < n) ? sv[t] : 0.f;
@@ -492,8 +492,10 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
                 const double scale = __longlong_as_double((long long)*rho_bits) * dev->scale;
                 const double d = scale * (double)zv;
                 if (mode == 0) {
-                    x[i] += d;
+                    const double xn = x[i] + d;
+                    x[i] = xn;
                     dmax = fabs(d);
+                    xmax = fabs(xn);
                 } else {
                     x[i] = d;
                 }
@@ -504,8 +506,14 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
     }
     if (mode == 0 && t < B) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        if (lane == 0) atomic_max_nonneg(&dev->dnorm_bits, dmax);
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        }
+        if (lane == 0) {
+            atomic_max_nonneg(&dev->dnorm_bits, dmax);
+            atomic_max_nonneg(&dev->xnorm_bits, xmax);
+        }
     }
 }
 

@@ -177,3 +177,53 @@ def test_lu_solve_backward_stable_with_ill_conditioned_diagonal_blocks(ctx):
     r = U @ d - v.astype(np.float64)
     bound = 2 * n * 2.0 ** -24 * (np.abs(U) @ np.abs(d) + np.abs(v))
     assert np.all(np.abs(r) <= bound), float(np.max(np.abs(r) / bound))
+
+
+@pytest.mark.parametrize("tw", [np.float64, np.float32])
+def test_backward_error_termination_matches_oracle(ctx, tw):
+    """eq. (term) with ||A||_1: on I - 799 G (Sec. 5.1.3's system) the residual floor
+    is far above eps ||b||; the backward-error test stops there as converged, where
+    the residual test stops on stagnation one step later."""
+    A64 = np.asfortranarray(np.eye(512) - 799.0 * irgen.gmat_trapezoid(512))
+    A = np.asfortranarray(A64.astype(tw))
+    b = np.ones(512, dtype=tw)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    for mode in (0, 1):
+        x, rep = f.solve(dev_vec(b), term=ir.default_term(mode=mode))
+        ref = O.ir_solve(A, b, O.F32, O.Term(mode=mode))
+        assert rep.status == O.STATUS_NAMES[ref.status], (mode, rep.rhist, ref.rhist)
+        # TW = binary32: the correction test (eq. wilkterm) decides, one step of slack
+        assert abs(rep.iters - ref.iters) <= (0 if tw == np.float64 else 1)
+        xr = O.reference_solution(A, b)
+        tol = O.parity_tol(O.cond_inf(A), O.F64) if tw == np.float64 else 2.0 ** -23
+        assert O.rel_err_inf(x.cpu().numpy(), xr) <= tol
+    if tw == np.float64:
+        assert ref.status == O.CONVERGED
+    # the norm is cached per factorization and recomputed after a refactor
+    B = np.asfortranarray(2.0 * A)
+    f.refactor(dev_colmajor(B))
+    x, rep = f.solve(dev_vec(b), term=ir.default_term(mode=1))
+    ref = O.ir_solve(B, b, O.F32, O.Term(mode=1))
+    assert rep.status == O.STATUS_NAMES[ref.status]
+    assert abs(rep.iters - ref.iters) <= (0 if tw == np.float64 else 1)
+
+
+def test_gmres_ir_backward_error_termination(ctx):
+    A = np.asfortranarray(np.eye(512) - 799.0 * irgen.gmat_trapezoid(512))
+    b = np.ones(512)
+    f = ctx.factor(dev_colmajor(A), tf="f16")
+    x, rep = f.solve_gmres(dev_vec(b), term=ir.default_term(mode=1))
+    ref = O.gmres_ir_solve(A, b, O.F16, O.Term(mode=1), nb=64)
+    assert rep.status == O.STATUS_NAMES[ref.status] == "converged"
+    assert abs(rep.iters - ref.iters) <= 1
+    assert O.rel_err_inf(x.cpu().numpy(), O.reference_solution(A, b)) <= O.parity_tol(O.cond_inf(A), O.F64)
+
+
+def test_term_mode_validation(ctx):
+    A, b = irgen.case_gaussian(40, 1)
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    with pytest.raises(ir.IRError, match="IR_EINVAL"):
+        f.solve(dev_vec(b), term=ir.default_term(mode=2))
+    As = [dev_colmajor(A)]
+    with pytest.raises(ir.IRError, match="IR_EUNSUPPORTED"):
+        ctx.solve_batched(As, [dev_vec(b)], tf="f32", term=ir.default_term(mode=1))
