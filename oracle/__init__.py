@@ -18,6 +18,7 @@ A plain, slow, obviously-correct implementation of the paper's method
 * ``gmres_ir_solve`` -- GMRES-IR (Sec. 4.3): the correction equation solved by
                        left-preconditioned GMRES with P = U^{-1} L^{-1}
                        (eq. pdef), ``gmres_correction``.
+* ``bicgstab_ir_solve`` -- BiCGSTAB-IR (Sec. 2.3, 4.2): the same with BiCGSTAB.
 
 Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
 ``--impl reference`` legs of ``bench.py`` may import this package.  It shares
@@ -464,14 +465,83 @@ def gmres_correction(A: np.ndarray, LU: np.ndarray, ipiv: np.ndarray, s: float, 
     return d, k
 
 
+def bicgstab(op, z: np.ndarray, kmax: int, eta: float):
+    """BiCGSTAB (van der Vorst) for op(d) = z from d_0 = 0, in binary64.
+
+    r = z, r^ = r, rho_old = alpha = omega = 1, v = p = 0; for i = 1..kmax:
+      rho = <r^, r>;  beta = (rho / rho_old)(alpha / omega);
+      p = r + beta (p - omega v);  v = op(p);  alpha = rho / <r^, v>;
+      s = r - alpha v;  if ||s||_2 <= eta ||z||_2: d += alpha p, stop;
+      t = op(s);  omega = <t, s> / <t, t>;  d += alpha p + omega s;
+      r = s - omega t;  stop if ||r||_2 <= eta ||z||_2;  rho_old = rho.
+    A zero rho, <r^, v> or <t, t> (breakdown) stops the iteration with the
+    current d.  Returns (d, k, est): k iterations (two op applications each,
+    one for a stop at s), est[i] = the recurrence's ||r||_2 after iteration i.
+    """
+    n = z.shape[0]
+    d = np.zeros(n)
+    r = z.astype(np.float64).copy()
+    z0 = float(np.sqrt(np.dot(r, r)))
+    if z0 == 0.0 or kmax < 1:
+        return d, 0, []
+    rh = r.copy()
+    rho_old = alpha = omega = 1.0
+    v = np.zeros(n)
+    p = np.zeros(n)
+    est = []
+    k = 0
+    for _ in range(kmax):
+        rho = float(np.dot(rh, r))
+        if rho == 0.0:
+            break
+        beta = (rho / rho_old) * (alpha / omega)
+        p = r + beta * (p - omega * v)
+        v = op(p)
+        sig = float(np.dot(rh, v))
+        if sig == 0.0:
+            break
+        alpha = rho / sig
+        s = r - alpha * v
+        k += 1
+        sn = float(np.sqrt(np.dot(s, s)))
+        if sn <= eta * z0:
+            d = d + alpha * p
+            est.append(sn)
+            break
+        t = op(s)
+        tt = float(np.dot(t, t))
+        if tt == 0.0:
+            d = d + alpha * p
+            est.append(sn)
+            break
+        omega = float(np.dot(t, s)) / tt
+        d = d + alpha * p + omega * s
+        r = s - omega * t
+        rn = float(np.sqrt(np.dot(r, r)))
+        est.append(rn)
+        if rn <= eta * z0 or omega == 0.0:
+            break
+        rho_old = rho
+    return d, k, est
+
+
 @dataclass
 class GMRESIRResult(IRResult):
     khist: list = field(default_factory=list)
 
 
+def bicgstab_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
+                      kopts: Optional[KrylovOpts] = None, nb: int = 0, fp16_scaling: bool = True,
+                      tr_wider: Optional[bool] = None, factors=None) -> GMRESIRResult:
+    """BiCGSTAB-IR (Sec. 2.3, 4.2): ``gmres_ir_solve`` with the correction equation
+    P A d = P r solved by ``bicgstab`` (at most kopts.basissize iterations);
+    khist[i] counts BiCGSTAB iterations of refinement step i."""
+    return gmres_ir_solve(A, b, tf, term, kopts, nb, fp16_scaling, tr_wider, factors, method="bicgstab")
+
+
 def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
                    kopts: Optional[KrylovOpts] = None, nb: int = 0, fp16_scaling: bool = True,
-                   tr_wider: Optional[bool] = None, factors=None) -> GMRESIRResult:
+                   tr_wider: Optional[bool] = None, factors=None, method: str = "gmres") -> GMRESIRResult:
     """GMRES-IR (Sec. 4.3): Algorithm IR with the correction d from
     ``gmres_correction`` instead of one low-precision solve.  Factorization,
     residual (TR = binary64) and the termination tests of Sec. 5.1 are those of
@@ -508,7 +578,11 @@ def gmres_ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] =
     anorm = norm1(A) if term.mode == 1 else 0.0
     r = b64.copy()
     while True:
-        d, k = gmres_correction(A, LU, ipiv, s, r, kopts.basissize, kopts.eta)
+        if method == "gmres":
+            d, k = gmres_correction(A, LU, ipiv, s, r, kopts.basissize, kopts.eta)
+        else:
+            d, k, _ = bicgstab(lambda v: precondition(LU, ipiv, s, matvec(A, v)),
+                               precondition(LU, ipiv, s, r), kopts.basissize, kopts.eta)
         res.khist.append(k)
         x += d
         res.dhist.append(float(np.max(np.abs(d))))

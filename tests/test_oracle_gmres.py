@@ -167,3 +167,66 @@ def test_gmres_ir_edge_cases():
     A = np.asfortranarray(np.array([[1.0, 2.0], [2.0, 4.0]]))
     res = O.gmres_ir_solve(A, np.ones(2), O.F32)
     assert res.status == O.FAILED and res.info == 2
+
+
+# ---------------------------------------------------------------------------
+# BiCGSTAB (Sec. 2.3, 4.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_bicgstab_finite_termination_and_true_residual(seed):
+    """In exact arithmetic BiCGSTAB ends within n iterations; in binary64 on a small,
+    well-conditioned nonsymmetric system it reaches the solution, and the residual its
+    recurrence carries equals the true residual z - M d."""
+    rng = np.random.default_rng(720 + seed)
+    n = 8
+    M = rng.standard_normal((n, n)) + 4.0 * np.eye(n)
+    z = rng.standard_normal(n)
+    d, k, est = O.bicgstab(lambda v: M @ v, z, 3 * n, 1e-14)
+    assert k <= n + 2
+    np.testing.assert_allclose(d, np.linalg.solve(M, z), rtol=1e-11, atol=1e-12)
+    for kk in range(1, k + 1):
+        dk, _, ek = O.bicgstab(lambda v: M @ v, z, kk, 0.0)
+        assert abs(np.linalg.norm(z - M @ dk) - ek[-1]) <= 1e-10 * np.linalg.norm(z)
+
+
+def test_bicgstab_omega_minimises_the_step_residual():
+    """omega = <t, s>/<t, t> is the one-dimensional least-squares choice: the
+    first iterate's residual s - omega t is no larger than with a perturbed omega."""
+    rng = np.random.default_rng(722)
+    n = 12
+    M = rng.standard_normal((n, n)) + 3.0 * np.eye(n)
+    z = rng.standard_normal(n)
+    d, k, est = O.bicgstab(lambda v: M @ v, z, 1, 0.0)
+    assert k == 1
+    alpha = (z @ z) / (z @ (M @ z))
+    s = z - alpha * (M @ z)
+    t = M @ s
+    for dw in (-1e-3, 1e-3, 0.1):
+        om = (t @ s) / (t @ t) + dw
+        assert est[-1] <= np.linalg.norm(s - om * t) + 1e-15
+    # and the iterate is alpha z + omega s (the two search directions of step one)
+    coef, *_ = np.linalg.lstsq(np.stack([z, s], 1), d, rcond=None)
+    np.testing.assert_allclose(np.stack([z, s], 1) @ coef, d, rtol=1e-12, atol=1e-14)
+    assert abs(coef[0] - alpha) <= 1e-12 * abs(alpha)
+
+
+def test_bicgstab_identity_one_iteration_and_zero_rhs():
+    z = np.array([1.0, -2.0, 3.0, 0.5])
+    d, k, est = O.bicgstab(lambda v: v, z, 10, 1e-8)
+    assert k == 1 and est[-1] == 0.0
+    np.testing.assert_array_equal(d, z)
+    d, k, est = O.bicgstab(lambda v: v, np.zeros(4), 10, 1e-8)
+    assert k == 0 and not est
+
+
+def test_bicgstab_ir_rescues_half_precision_and_agrees_with_gmres_ir():
+    A, b = irgen.case_green(256, 800.0)
+    xref = O.reference_solution(A, b)
+    tol = O.parity_tol(O.cond_inf(A), O.F64)
+    bi = O.bicgstab_ir_solve(A, b, O.F16)
+    gm = O.gmres_ir_solve(A, b, O.F16)
+    assert bi.status in (O.CONVERGED, O.STAGNATED)
+    assert O.rel_err_inf(bi.x, xref) <= tol
+    assert O.rel_err_inf(bi.x, gm.x) <= tol
+    assert all(1 <= k <= 10 for k in bi.khist)
