@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true",
                     help="skip the binary64 cuSOLVER comparators (e.g. under a profiler)")
     ap.add_argument("--batch-count", type=int, default=2000)
-    ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES-IR line")
+    ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES-IR / BiCGSTAB-IR lines")
     return ap.parse_args()
 
 
@@ -593,6 +593,24 @@ def main():
         _, rep_ir16 = fact16.solve(b_d, x16, term)
         rel = lambda v: float(np.max(np.abs(v.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
         gm_kinds = {k: v[0] / gsteps for k, v in sorted(prof_gm.items())}
+
+        # BiCGSTAB-IR (Sec. 2.3, 4.2) on the same factors and system
+        fact16.bicgstab_reserve()
+        xb16 = torch.empty_like(b_d)
+
+        def step_bi():
+            fact16.refactor(A_d)
+            return fact16.solve_bicgstab(b_d, xb16, term, kopts)[1]
+
+        _, _, prof_bi, l_bi = timed_steps(step_bi, gsteps, 1, profile=True)
+        ms_bi, rep_bi, _, _ = timed_steps(step_bi, gsteps, 1)
+        bicgstab = {
+            "ms": max_over_ranks(statistics.mean(ms_bi), ws), "unit": "ms (refactor + BiCGSTAB-IR solve)",
+            "iters": rep_bi.iters, "status": rep_bi.status, "khist": rep_bi.khist,
+            "rel_err_vs_closed_form": rel(xb16),
+            "kernel_ms_per_step": {k: v[0] / gsteps for k, v in sorted(prof_bi.items())},
+            "gpu_launches_per_step": l_bi / gsteps,
+        }
         gmres = {
             "workload": f"green_sine_N{n}_alpha800_TWf64_TFf16_TRf64_basis10",
             "ms": max_over_ranks(statistics.mean(ms_gm), ws), "unit": "ms (refactor + GMRES-IR solve)",
@@ -602,6 +620,7 @@ def main():
                                 "rel_err_vs_closed_form": rel(x16)},
             "kernel_ms_per_step": gm_kinds,
             "gpu_launches_per_step": l_gm / gsteps,
+            "bicgstab_ir": bicgstab,
         }
 
     value = t32 / ws if ws > 1 else t32

@@ -273,6 +273,17 @@ ir_status ir_gmres_reserve(ir_fact *fact, int basissize);
 ir_status ir_solve_gmres(ir_fact *fact, const void *b, void *x, const ir_term *term,
                          const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist);
 
+/* ---- BiCGSTAB-IR (Sec. 2.3, 4.2) ------------------------------------------
+ * As ir_solve_gmres, with the correction equation P A d = P r solved by
+ * BiCGSTAB (van der Vorst) in binary64 from d = 0: at most kopts->basissize
+ * iterations (two products P A u each), stopping when the recurrence's
+ * ||r||_2 (or ||s||_2 half-way) <= eta ||P r||_2 or on breakdown (a zero
+ * <r^, r>, <r^, v> or <t, t>).  khist[k] = BiCGSTAB iterations of step k.
+ * ir_bicgstab_reserve (mpblu's allocation, Sec. 4.4): 8 n binary64 values. */
+ir_status ir_bicgstab_reserve(ir_fact *fact);
+ir_status ir_solve_bicgstab(ir_fact *fact, const void *b, void *x, const ir_term *term,
+                            const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist);
+
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */
 ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);
 

@@ -28,11 +28,11 @@ namespace {
 // call on the launching stream, summed per kind when profiling stops.
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
-    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_N
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_BI_STEP, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
-                                "batched", "gm_orth", "gm_update", "norm1"};
+                                "batched", "gm_orth", "krylov_update", "norm1", "bi_step"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -138,6 +138,8 @@ void free_fact(ir_fact *f) {
     cudaFree(f->gm_V);
     cudaFree(f->gm_W);
     cudaFree(f->gm_st);
+    cudaFree(f->bi_V);
+    cudaFree(f->bi_st);
     if (f->gm_host_k) cudaFreeHost(f->gm_host_k);
     if (f->graph) cudaGraphExecDestroy(f->graph);
     if (f->cap_stream) cudaStreamDestroy(f->cap_stream);
@@ -656,31 +658,66 @@ void ir_default_krylov_opts(ir_krylov_opts *o) {
     o->Rmax_r = 1.0;
 }
 
+}  // extern "C"
+
+namespace {
+
+// The product buffer W, the pinned iteration count and the basis stride shared
+// by both Krylov solvers.
+ir_status krylov_common(ir_fact *f) {
+    if (f->gm_W) return IR_OK;
+    const int64_t n = f->n > 0 ? f->n : 1;
+    f->gm_ldv = (n + 31) / 32 * 32;
+    CK(cudaMalloc(&f->gm_W, (size_t)f->gm_ldv * sizeof(double)));
+    if (!f->gm_host_k) CK(cudaMallocHost((void **)&f->gm_host_k, sizeof(int)));
+    return IR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
 ir_status ir_gmres_reserve(ir_fact *f, int m) {
     if (!f || m < 1 || m > IR_MAX_BASIS) return IR_EINVAL;
     if (f->gm_st && f->gm_m >= m) return IR_OK;
     CK(cudaSetDevice(f->ctx->device));
     CK(cudaDeviceSynchronize());     // the old buffers may be in use
+    ir_status st = krylov_common(f);
+    if (st != IR_OK) return st;
     cudaFree(f->gm_V);
-    cudaFree(f->gm_W);
     cudaFree(f->gm_st);
-    f->gm_V = f->gm_W = nullptr;
+    f->gm_V = nullptr;
     f->gm_st = nullptr;
     f->gm_m = 0;
-    const int64_t n = f->n > 0 ? f->n : 1;
-    const int64_t ldv = (n + 31) / 32 * 32;
-    CK(cudaMalloc(&f->gm_V, (size_t)(m + 1) * ldv * sizeof(double)));
-    CK(cudaMalloc(&f->gm_W, (size_t)ldv * sizeof(double)));
+    CK(cudaMalloc(&f->gm_V, (size_t)(m + 1) * f->gm_ldv * sizeof(double)));
     CK(cudaMalloc(&f->gm_st, sizeof(GmState)));
     CK(cudaMemset(f->gm_st, 0, sizeof(GmState)));
-    if (!f->gm_host_k) CK(cudaMallocHost((void **)&f->gm_host_k, sizeof(int)));
-    f->gm_ldv = ldv;
     f->gm_m = m;
     return IR_OK;
 }
 
-ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term,
-                         const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist) {
+ir_status ir_bicgstab_reserve(ir_fact *f) {
+    if (!f) return IR_EINVAL;
+    if (f->bi_st) return IR_OK;
+    CK(cudaSetDevice(f->ctx->device));
+    ir_status st = krylov_common(f);
+    if (st != IR_OK) return st;
+    CK(cudaMalloc(&f->bi_V, (size_t)kBiCols * f->gm_ldv * sizeof(double)));
+    CK(cudaMalloc(&f->bi_st, sizeof(BiState)));
+    CK(cudaMemset(f->bi_st, 0, sizeof(BiState)));
+    return IR_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+enum { KRY_GMRES = 0, KRY_BICGSTAB = 1 };
+
+// Krylov-IR (Sec. 4.2-4.3): Algorithm IR with the correction equation solved by
+// left-preconditioned GMRES or BiCGSTAB.
+ir_status krylov_solve(int method, ir_fact *f, const void *b, void *x, const ir_term *term,
+                       const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist) {
     if (!f || (f->n > 0 && (!b || !x))) return IR_EINVAL;
     ir_term t;
     if (term) t = *term;
@@ -703,7 +740,7 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
         return IR_OK;
     }
     CK(cudaSetDevice(f->ctx->device));
-    ir_status st = ir_gmres_reserve(f, ko.basissize);
+    ir_status st = (method == KRY_GMRES) ? ir_gmres_reserve(f, ko.basissize) : ir_bicgstab_reserve(f);
     if (st != IR_OK) return st;
     st = read_dev(f, s);
     if (st != IR_OK) return st;
@@ -751,29 +788,53 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
     GmState *gs = f->gm_st;
     int k = 0;
     int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
+    double *Vb = f->bi_V;
+    BiState *bs = f->bi_st;
+    // w = P (A u) into out: the high-precision product, then the preconditioner;
+    // both skipped once the Krylov iteration has stopped (*skip != 0)
+    auto prec_matvec = [&](const double *u, double *out, unsigned long long *wbits, const int *skip) -> ir_status {
+        RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, nullptr, u, W, f->ctx->partials,
+                                         f->ctx->partials_cap, wbits, f->ctx->sms, s, skip));
+        f->epoch += 1;
+        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, W,
+                                         nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s, wbits, out,
+                                         skip));
+        return IR_OK;
+    };
     while (status < 0) {
-        // v_0 = P r / ||P r||_2
+        // z = P r
+        double *z = (method == KRY_GMRES) ? V : Vb + (int64_t)kBiR * ldv;
         f->epoch += 1;
         RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
                                          nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s,
-                                         &f->dev->rnorm_bits, V, nullptr));
-        RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, -1, m, ko.eta, gs, s));
-        for (int j = 0; j < m; ++j) {
-            // V_{j+1} = P (A v_j), then orthogonalize; skipped once GMRES has stopped
-            RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, nullptr, V + (int64_t)j * ldv, W,
-                                             f->ctx->partials, f->ctx->partials_cap, &gs->wnorm_bits,
-                                             f->ctx->sms, s, &gs->done));
-            f->epoch += 1;
-            RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, W,
-                                             nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s,
-                                             &gs->wnorm_bits, V + (int64_t)(j + 1) * ldv, &gs->done));
-            RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, j, m, ko.eta, gs, s));
-        }
+                                         &f->dev->rnorm_bits, z, nullptr));
         CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
-        RUN(KC_GM_UPDATE, s, launch_gm_update(nn, V, ldv, gs, f->x, &f->dev->dnorm_bits, &f->dev->xnorm_bits, s));
+        if (method == KRY_GMRES) {
+            RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, -1, m, ko.eta, gs, s));     // v_0 = z / ||z||_2
+            for (int j = 0; j < m; ++j) {
+                st = prec_matvec(V + (int64_t)j * ldv, V + (int64_t)(j + 1) * ldv, &gs->wnorm_bits, &gs->done);
+                if (st != IR_OK) return st;
+                RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, j, m, ko.eta, gs, s));
+            }
+            RUN(KC_GM_UPDATE, s, launch_gm_update(nn, V, ldv, gs, f->x, &f->dev->dnorm_bits, &f->dev->xnorm_bits, s));
+            CK(cudaMemcpyAsync(f->gm_host_k, &gs->k, sizeof(int), cudaMemcpyDeviceToHost, s));
+        } else {
+            RUN(KC_BI_STEP, s, launch_bi_step(0, nn, Vb, ldv, m, ko.eta, bs, s));
+            for (int j = 0; j < m; ++j) {
+                RUN(KC_BI_STEP, s, launch_bi_step(1, nn, Vb, ldv, m, ko.eta, bs, s));
+                st = prec_matvec(Vb + (int64_t)kBiP * ldv, Vb + (int64_t)kBiV * ldv, &bs->wnorm_bits, &bs->done);
+                if (st != IR_OK) return st;
+                RUN(KC_BI_STEP, s, launch_bi_step(2, nn, Vb, ldv, m, ko.eta, bs, s));
+                st = prec_matvec(Vb + (int64_t)kBiS * ldv, Vb + (int64_t)kBiT * ldv, &bs->wnorm_bits, &bs->done);
+                if (st != IR_OK) return st;
+                RUN(KC_BI_STEP, s, launch_bi_step(3, nn, Vb, ldv, m, ko.eta, bs, s));
+            }
+            RUN(KC_GM_UPDATE, s, launch_axpy_norms(nn, Vb + (int64_t)kBiD * ldv, f->x, &f->dev->dnorm_bits,
+                                                   &f->dev->xnorm_bits, s));
+            CK(cudaMemcpyAsync(f->gm_host_k, &bs->k, sizeof(int), cudaMemcpyDeviceToHost, s));
+        }
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
                                          f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
-        CK(cudaMemcpyAsync(f->gm_host_k, &gs->k, sizeof(int), cudaMemcpyDeviceToHost, s));
         st = read_dev(f, s);
         if (st != IR_OK) return st;
         if (f->host_dev->timeout) {
@@ -795,6 +856,20 @@ ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term
         *rep = R;
     }
     return IR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ir_status ir_solve_gmres(ir_fact *f, const void *b, void *x, const ir_term *term,
+                         const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist) {
+    return krylov_solve(KRY_GMRES, f, b, x, term, kopts, stream, rep, khist);
+}
+
+ir_status ir_solve_bicgstab(ir_fact *f, const void *b, void *x, const ir_term *term,
+                            const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist) {
+    return krylov_solve(KRY_BICGSTAB, f, b, x, term, kopts, stream, rep, khist);
 }
 
 ir_status ir_lu_solve(ir_fact *f, const float *v, float *d, void *stream) {

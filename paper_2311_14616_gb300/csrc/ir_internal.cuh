@@ -56,6 +56,16 @@ struct GmState {
     int done;                           // 1: the remaining iterations are skipped
 };
 
+// BiCGSTAB state of one correction solve (device memory).  The vectors live in
+// the columns of the Krylov workspace: r, r^, p, v, s, t, d.
+enum { kBiR = 0, kBiRh, kBiP, kBiV, kBiS, kBiT, kBiD, kBiCols };
+struct BiState {
+    double rho_old, rho, alpha, omega, z0;
+    unsigned long long wnorm_bits;      // ||A p||_inf or ||A s||_inf of the latest product
+    int k;                              // iterations taken
+    int done;
+};
+
 }  // namespace ir
 
 struct ir_ctx {
@@ -104,6 +114,10 @@ struct ir_fact {
     double *gm_V, *gm_W;
     ir::GmState *gm_st;
     int *gm_host_k;          // pinned mirror of gm_st->k
+    // BiCGSTAB-IR workspace (reserved on demand): kBiCols columns of gm_ldv
+    // binary64 and the state
+    double *bi_V;
+    ir::BiState *bi_st;
 };
 
 namespace ir {
@@ -157,11 +171,18 @@ cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, 
                             unsigned long long *rnorm_bits, int sms, cudaStream_t s,
                             const int *skip = nullptr);
 
-// GMRES (k_gmres.cu).  j = -1: v_0 = V_0 / ||V_0||_2, beta, g = beta e_1.
+// GMRES (k_krylov.cu).  j = -1: v_0 = V_0 / ||V_0||_2, beta, g = beta e_1.
 // j >= 0: orthogonalize V_{j+1} = P A v_j against v_0..v_j (classical
 // Gram-Schmidt twice), normalize, rotate column j of H, set done.
 cudaError_t launch_gm_orth(int n, double *V, int64_t ldv, int j, int m, double eta, GmState *st,
                            cudaStream_t s);
+// BiCGSTAB phases (k_krylov.cu): 0 start (r^ = r = z, ||z||_2), 1 rho and p,
+// 2 alpha and s (after v = M p), 3 omega, d and r (after t = M s).
+cudaError_t launch_bi_step(int phase, int n, double *Vb, int64_t ldv, int kmax, double eta, BiState *st,
+                           cudaStream_t s);
+// x += d; ||d||_inf, ||x||_inf.
+cudaError_t launch_axpy_norms(int n, const double *d, double *x, unsigned long long *dnorm_bits,
+                              unsigned long long *xnorm_bits, cudaStream_t s);
 // d = V_k R^{-1} g; x += d; ||d||_inf into dnorm_bits, ||x||_inf into xnorm_bits.
 cudaError_t launch_gm_update(int n, const double *V, int64_t ldv, const GmState *st, double *x,
                              unsigned long long *dnorm_bits, unsigned long long *xnorm_bits, cudaStream_t s);

@@ -104,6 +104,8 @@ def lib():
             "ir_default_krylov_opts": (None, [P(KrylovOpts)]),
             "ir_gmres_reserve": (i32, [vp, i32]),
             "ir_solve_gmres": (i32, [vp, vp, vp, P(Term), P(KrylovOpts), vp, P(_Report), vp]),
+            "ir_bicgstab_reserve": (i32, [vp]),
+            "ir_solve_bicgstab": (i32, [vp, vp, vp, P(Term), P(KrylovOpts), vp, P(_Report), vp]),
             "ir_residual": (i32, [vp, i64, i32, vp, i64, vp, vp, vp, vp, vp]),
             "ir_batch_create": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), P(vp)]),
             "ir_batch_run": (i32, [vp, vp, vp]),
@@ -389,9 +391,21 @@ class Factorization:
         """Reserve the Krylov basis (mpglu's allocation, Sec. 4.4)."""
         _check(lib().ir_gmres_reserve(self._h, int(basissize)))
 
+    def bicgstab_reserve(self):
+        """Reserve the BiCGSTAB vectors (mpblu's allocation, Sec. 4.4)."""
+        _check(lib().ir_bicgstab_reserve(self._h))
+
     def solve_gmres(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, term: Optional[Term] = None,
                     kopts: Optional[KrylovOpts] = None, stream=None, report: bool = True):
         """GMRES-IR (Sec. 4.3): returns (x, Report with khist)."""
+        return self._krylov(lib().ir_solve_gmres, b, x, term, kopts, stream, report)
+
+    def solve_bicgstab(self, b: torch.Tensor, x: Optional[torch.Tensor] = None, term: Optional[Term] = None,
+                       kopts: Optional[KrylovOpts] = None, stream=None, report: bool = True):
+        """BiCGSTAB-IR (Sec. 2.3, 4.2): returns (x, Report with khist)."""
+        return self._krylov(lib().ir_solve_bicgstab, b, x, term, kopts, stream, report)
+
+    def _krylov(self, fn, b, x, term, kopts, stream, report):
         bb = b.to(self.A.dtype).contiguous()
         if x is None:
             x = torch.empty_like(bb)
@@ -399,9 +413,9 @@ class Factorization:
         kh = (ctypes.c_int * MAX_HIST)()
         t = term if term is not None else default_term()
         ko = kopts if kopts is not None else krylov_opts()
-        code = lib().ir_solve_gmres(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(x.data_ptr()),
-                                    ctypes.byref(t), ctypes.byref(ko), _stream_ptr(stream),
-                                    ctypes.byref(rep) if report else None, kh)
+        code = fn(self._h, ctypes.c_void_p(bb.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                  ctypes.byref(t), ctypes.byref(ko), _stream_ptr(stream),
+                  ctypes.byref(rep) if report else None, kh)
         R = _report(rep) if report else None
         if R is not None:
             R.khist = list(kh[: R.iters])
