@@ -84,7 +84,8 @@ typedef struct {
     ir_dtype TW, TF, TR;
     int fp16_scale;       /* default 1 */
     int nb;               /* outer block size; 0 = default (64) */
-    int autotune;         /* reserved, 0 */
+    int autotune;         /* 1: tune the schedule on the caller's own input (see
+                             ir_fact_schedule / ir_batch_schedule); default 0 */
 } ir_opts;
 
 #define IR_MAX_HIST 32
@@ -283,6 +284,18 @@ ir_status ir_solve_gmres(ir_fact *fact, const void *b, void *x, const ir_term *t
 ir_status ir_bicgstab_reserve(ir_fact *fact);
 ir_status ir_solve_bicgstab(ir_fact *fact, const void *b, void *x, const ir_term *term,
                             const ir_krylov_opts *kopts, void *stream, ir_report *rep, int *khist);
+
+/* The autotuned schedule (opts.autotune = 1; not in the paper).
+ * Single system (n >= 1024): the SMs the lookahead's trailing update leaves
+ * free for the next panel's cluster, picked among 8, 12, 16, 24, 32 by timing
+ * two factorizations of the caller's A per candidate; remembered by the
+ * context per (n, TF).  nb is 64 (the tensor-core K block and the panel
+ * width).  Batch (TF = FP16/BF16): the smallest trailing block whose update
+ * goes to the tensor cores (64, 128, 192, 256 or never), picked by timing
+ * two runs of the planned batch per candidate inside ir_batch_create (x is
+ * overwritten; A, b only read).  grid = persistent CTAs (one per SM). */
+ir_status ir_fact_schedule(const ir_fact *fact, int *nb, int *panel_reserve_sms);
+ir_status ir_batch_schedule(const ir_batch *batch, int *grid, int *tc_min_trail);
 
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */
 ir_status ir_fact_pivots(const ir_fact *fact, int32_t *ipiv_host);

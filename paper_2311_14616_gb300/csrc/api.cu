@@ -159,6 +159,7 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     f->TR = o->TR;
     f->fp16_scale = o->fp16_scale;
     f->nb = kPanelNB;
+    f->reserve_sms = kPanelReserveSMs;
     f->ldf = ((n > 0 ? n : 1) + 31) / 32 * 32;
     const int64_t nn = n > 0 ? n : 1;
     const int64_t nblk = (nn + kTrsvB - 1) / kTrsvB;
@@ -296,10 +297,10 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
             if (nx1 < n) {
                 RUN(KC_TRSM, s2, launch_trsm(f->AF, ldf, nx1, n, j, f->TF, bop, s2));
                 if (f->TF == IR_F32)
-                    RUN(KC_GEMM_SIMT, s2, launch_gemm_simt(f->AF, ldf, n, j, NB, nx1, n, sms - kPanelReserveSMs, s2));
+                    RUN(KC_GEMM_SIMT, s2, launch_gemm_simt(f->AF, ldf, n, j, NB, nx1, n, sms - f->reserve_sms, s2));
                 else
                     RUN(KC_GEMM_TC, s2, launch_gemm_tc(f->AF, ldf, n, j, NB, nx1, n, f->TF, aop, bop, sms,
-                                                       sms - kPanelReserveSMs, f->dev, s2));
+                                                       sms - f->reserve_sms, f->dev, s2));
             }
             pending_rest = f->la_events[ev++];
             CK(cudaEventRecord(pending_rest, s2));
@@ -409,6 +410,7 @@ struct ir_batch {
     float *ws;           // grid slots of ws_stride floats
     int64_t ws_stride;
     int grid;
+    int tc_min_trail;    // smallest trailing block updated on the tensor cores (tuned)
 };
 
 namespace {
@@ -420,6 +422,117 @@ void free_batch(ir_batch *b) {
     cudaFree(b->ticket);
     cudaFree(b->ws);
     delete b;
+}
+
+}  // namespace
+
+namespace {
+
+// Time one replay of a planned batch (ms) on a private stream.
+ir_status time_batch(ir_batch *b, ir_batch_result *res, cudaStream_t s, cudaEvent_t e0, cudaEvent_t e1,
+                     float *ms) {
+    CK(cudaEventRecord(e0, s));
+    CK(launch_batched(b->desc, b->order, b->count, b->ticket, b->ws, b->ws_stride, b->grid, b->TW, b->TF,
+                      b->fp16_scale, &b->term, b->tc_min_trail, res, s));
+    CK(cudaEventRecord(e1, s));
+    CK(cudaEventSynchronize(e1));
+    CK(cudaEventElapsedTime(ms, e0, e1));
+    return IR_OK;
+}
+
+// Autotuner of the batched driver (opts.autotune): the smallest trailing block
+// that goes to the tensor cores -- below it the CTA's SIMT update, whose setup
+// is cheaper, does the same rounding-to-TF work.  Each candidate runs the
+// batch itself (its A and b are only read; x is rewritten by every run) twice,
+// the second timed; the fastest is kept in the plan.
+ir_status tune_batch(ir_batch *b) {
+    const int cands[] = {64, 128, 192, 256, 1 << 20};
+    cudaStream_t s = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ir_batch_result *res = nullptr;
+    ir_status st = IR_OK;
+    float best = 3.4e38f;
+    int best_c = b->tc_min_trail;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&e0);
+    if (e == cudaSuccess) e = cudaEventCreate(&e1);
+    if (e == cudaSuccess) e = cudaMalloc(&res, (size_t)b->count * sizeof(ir_batch_result));
+    if (e != cudaSuccess) st = cuda_fail(e, "tune_batch");
+    for (int c : cands) {
+        if (st != IR_OK) break;
+        b->tc_min_trail = c;
+        float ms = 0.f;
+        st = time_batch(b, res, s, e0, e1, &ms);
+        if (st == IR_OK) st = time_batch(b, res, s, e0, e1, &ms);
+        if (st == IR_OK && ms < best) {
+            best = ms;
+            best_c = c;
+        }
+    }
+    b->tc_min_trail = best_c;
+    if (res) cudaFree(res);
+    if (e1) cudaEventDestroy(e1);
+    if (e0) cudaEventDestroy(e0);
+    if (s) cudaStreamDestroy(s);
+    return st;
+}
+
+// Autotuner of the single-system factorization (opts.autotune): how many SMs
+// the lookahead's trailing update leaves free for the next panel's cluster.
+// Each candidate factors the caller's A twice (graph captured for it), the
+// second timed; the fastest is kept and remembered by the context per (n, TF).
+ir_status tune_factor(ir_fact *f, cudaStream_t s) {
+    ir_ctx *c = f->ctx;
+    for (int i = 0; i < c->ntuned && i < 16; ++i)
+        if (c->tuned[i].n == f->n && c->tuned[i].tf == (int)f->TF) {
+            f->reserve_sms = c->tuned[i].reserve_sms;
+            return IR_OK;
+        }
+    const int cands[] = {8, 12, 16, 24, 32};
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 3.4e38f;
+    int best_r = f->reserve_sms;
+    ir_status st = IR_OK;
+    for (int r : cands) {
+        if (r >= c->sms / 2) continue;
+        f->reserve_sms = r;
+        if (f->graph) {
+            cudaGraphExecDestroy(f->graph);
+            f->graph = nullptr;
+        }
+        float ms = 0.f;
+        for (int rep = 0; rep < 2 && st == IR_OK; ++rep) {
+            cudaError_t e = cudaEventRecord(e0, s);
+            if (e == cudaSuccess) {
+                st = run_factor(f, s);
+                if (st == IR_OK) e = cudaEventRecord(e1, s);
+            }
+            if (st == IR_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (st == IR_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (st == IR_OK && e != cudaSuccess) st = cuda_fail(e, "tune_factor");
+        }
+        if (st != IR_OK) break;
+        if (ms < best) {
+            best = ms;
+            best_r = r;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st != IR_OK) return st;
+    f->reserve_sms = best_r;
+    if (f->graph) {
+        cudaGraphExecDestroy(f->graph);
+        f->graph = nullptr;
+    }
+    ir_tuned &slot = c->tuned[c->ntuned % 16];
+    slot.n = f->n;
+    slot.tf = (int)f->TF;
+    slot.reserve_sms = best_r;
+    c->ntuned += 1;
+    return IR_OK;
 }
 
 }  // namespace
@@ -533,7 +646,9 @@ ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda, const ir
     f->A = A;
     f->lda = lda;
     f->anorm_valid = 0;
-    st = run_factor(f, (cudaStream_t)stream);
+    // the schedule autotuner matters once the lookahead overlaps panels with updates
+    if (o.autotune && n >= 1024) st = tune_factor(f, (cudaStream_t)stream);
+    if (st == IR_OK) st = run_factor(f, (cudaStream_t)stream);
     if (st != IR_OK) {
         free_fact(f);
         return st;
@@ -938,6 +1053,7 @@ ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host, con
     b->TF = o.TF;
     b->fp16_scale = o.fp16_scale;
     b->term = t;
+    b->tc_min_trail = kPanelNB;
     ir_status st = IR_OK;
     cudaError_t e = batch_grid(ctx->sms, count, &b->grid);
     const int64_t cnt = count > 0 ? count : 1;
@@ -965,7 +1081,28 @@ ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host, con
         free_batch(b);
         return st;
     }
+    if (o.autotune && count > 0 && (o.TF == IR_F16 || o.TF == IR_BF16)) {
+        st = tune_batch(b);
+        if (st != IR_OK) {
+            free_batch(b);
+            return st;
+        }
+    }
     *out = b;
+    return IR_OK;
+}
+
+ir_status ir_batch_schedule(const ir_batch *b, int *grid, int *tc_min_trail) {
+    if (!b) return IR_EINVAL;
+    if (grid) *grid = b->grid;
+    if (tc_min_trail) *tc_min_trail = b->tc_min_trail;
+    return IR_OK;
+}
+
+ir_status ir_fact_schedule(const ir_fact *f, int *nb, int *panel_reserve_sms) {
+    if (!f) return IR_EINVAL;
+    if (nb) *nb = f->nb;
+    if (panel_reserve_sms) *panel_reserve_sms = f->reserve_sms;
     return IR_OK;
 }
 
@@ -975,7 +1112,7 @@ ir_status ir_batch_run(ir_batch *b, ir_batch_result *results_dev, void *stream) 
     CK(cudaSetDevice(b->ctx->device));
     cudaStream_t s = (cudaStream_t)stream;
     RUN(KC_BATCHED, s, launch_batched(b->desc, b->order, b->count, b->ticket, b->ws, b->ws_stride, b->grid, b->TW,
-                                      b->TF, b->fp16_scale, &b->term, results_dev, s));
+                                      b->TF, b->fp16_scale, &b->term, b->tc_min_trail, results_dev, s));
     return IR_OK;
 }
 

@@ -68,9 +68,18 @@ struct BiState {
 
 }  // namespace ir
 
+// Tuned factorization schedules, per (n, TF), kept by the context.
+struct ir_tuned {
+    int64_t n;
+    int tf;
+    int reserve_sms;
+};
+
 struct ir_ctx {
     int device;
     int sms;
+    ir_tuned tuned[16];      // ring of tuned schedules
+    int ntuned;
     double *partials;        // residual split-K partial sums
     int64_t partials_cap;    // capacity in doubles
     double *rnorm_tmp;       // scratch scalar for ir_residual
@@ -82,6 +91,7 @@ struct ir_fact {
     ir_dtype TW, TF, TR;
     int fp16_scale;
     int nb;
+    int reserve_sms;         // SMs the trailing update leaves to the next panel's cluster (schedule)
     const void *A;
     int64_t lda;
     int64_t ldf;             // row stride of AF in floats (multiple of 32)
@@ -194,7 +204,7 @@ void batch_fill_desc(void *desc, int64_t i, const void *A, int64_t lda, const vo
 cudaError_t batch_grid(int sms, int64_t count, int *grid);
 cudaError_t launch_batched(const void *sys, const int *order, int64_t count, unsigned *ticket, float *ws,
                            int64_t ws_stride, int grid, ir_dtype tw, ir_dtype tf, int fp16_scale,
-                           const ir_term *t, ir_batch_result *results, cudaStream_t s);
+                           const ir_term *t, int tc_min_trail, ir_batch_result *results, cudaStream_t s);
 
 // ---- device helpers --------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p) {

@@ -90,6 +90,7 @@ struct BatchCfg {
     double Cr, Rmax, abs_rel_tol, eps_w;
     int litmax, tr_wider, fp16_scale, count;
     ir_dtype tw, tf;
+    int tc_min_trail;      // smallest trailing block that takes the tensor-core update (tuned)
 };
 
 __device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
@@ -713,7 +714,7 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
         b_laswp(W, n, ldw, j0, nbp, sm, big);
         if (j0 + nbp < n) {
             b_trsm(W, n, ldw, j0, big);
-            if (use_tc && n - j0 - NB > NB) {
+            if (use_tc && n - j0 - NB > cfg.tc_min_trail) {
                 if (!b_update_tc(W, n, ldw, j0, tf, reinterpret_cast<unsigned char *>(big), sm, mph)) {
                     if (t == 0) {
                         sm.abort = 1;
@@ -911,7 +912,7 @@ cudaError_t batch_grid(int sms, int64_t count, int *grid) {
 
 cudaError_t launch_batched(const void *sys, const int *order, int64_t count, unsigned *ticket, float *ws,
                            int64_t ws_stride, int grid, ir_dtype tw, ir_dtype tf, int fp16_scale, const ir_term *t,
-                           ir_batch_result *results, cudaStream_t s) {
+                           int tc_min_trail, ir_batch_result *results, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
     BatchCfg c;
     c.Cr = t->Cr;
@@ -924,6 +925,7 @@ cudaError_t launch_batched(const void *sys, const int *order, int64_t count, uns
     c.count = (int)count;
     c.tw = tw;
     c.tf = tf;
+    c.tc_min_trail = tc_min_trail;
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     count_launch();

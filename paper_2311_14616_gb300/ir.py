@@ -112,6 +112,8 @@ def lib():
             "ir_batch_destroy": (None, [vp]),
             "ir_factor_solve_batched": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), vp, vp]),
             "ir_fact_pivots": (i32, [vp, vp]),
+            "ir_fact_schedule": (i32, [vp, P(i32), P(i32)]),
+            "ir_batch_schedule": (i32, [vp, P(i32), P(i32)]),
             "ir_fact_factors": (i32, [vp, vp, i64]),
             "ir_fact_info": (i32, [vp, P(i64), P(i32)]),
             "ir_fact_destroy": (None, [vp]),
@@ -178,10 +180,10 @@ def krylov_opts(**kw) -> KrylovOpts:
     return k
 
 
-def make_opts(TW: int, TF: int, fp16_scale: bool = True, nb: int = 0) -> Opts:
+def make_opts(TW: int, TF: int, fp16_scale: bool = True, nb: int = 0, autotune: bool = False) -> Opts:
     o = Opts()
     lib().ir_default_opts(ctypes.byref(o))
-    o.TW, o.TF, o.TR, o.fp16_scale, o.nb = TW, TF, F64, int(fp16_scale), nb
+    o.TW, o.TF, o.TR, o.fp16_scale, o.nb, o.autotune = TW, TF, F64, int(fp16_scale), nb, int(autotune)
     return o
 
 
@@ -211,10 +213,10 @@ class Context:
             pass
 
     def factor(self, A: torch.Tensor, tf="f32", fp16_scale: bool = True, nb: int = 0,
-               stream=None) -> "Factorization":
+               stream=None, autotune: bool = False) -> "Factorization":
         Ac, lda = as_colmajor(A)
         tfc = DTYPES[tf] if isinstance(tf, str) else int(tf)
-        opts = make_opts(_tw_code(Ac), tfc, fp16_scale, nb)
+        opts = make_opts(_tw_code(Ac), tfc, fp16_scale, nb, autotune)
         h = ctypes.c_void_p()
         _check(lib().ir_factor(self._h, Ac.shape[0], ctypes.c_void_p(Ac.data_ptr()), lda,
                                ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h)))
@@ -254,9 +256,10 @@ class Context:
         return x, _report(rep)
 
 
-    def batch(self, As, bs, xs=None, tf="f16", term: Optional[Term] = None, fp16_scale: bool = True):
+    def batch(self, As, bs, xs=None, tf="f16", term: Optional[Term] = None, fp16_scale: bool = True,
+              autotune: bool = False):
         """Plan a batch of independent systems (ir_batch_create); see Batch."""
-        return Batch(self, As, bs, xs, tf, term, fp16_scale)
+        return Batch(self, As, bs, xs, tf, term, fp16_scale, autotune=autotune)
 
     def solve_batched(self, As, bs, tf="f16", term: Optional[Term] = None, fp16_scale: bool = True,
                       stream=None):
@@ -287,7 +290,7 @@ class Batch:
     """
 
     def __init__(self, ctx: Context, As, bs, xs=None, tf="f16", term: Optional[Term] = None,
-                 fp16_scale: bool = True, plan: bool = True):
+                 fp16_scale: bool = True, plan: bool = True, autotune: bool = False):
         if len(As) != len(bs) or (xs is not None and len(xs) != len(As)):
             raise ValueError("As, bs and xs must have the same length")
         self.ctx, self.count = ctx, len(As)
@@ -303,7 +306,7 @@ class Batch:
         self.xs = list(xs) if xs is not None else [torch.empty_like(b) for b in self.bs]
         self.ns = [A.shape[0] for A in self.As]
         tfc = DTYPES[tf] if isinstance(tf, str) else int(tf)
-        self.opts = make_opts(tw, tfc, fp16_scale)
+        self.opts = make_opts(tw, tfc, fp16_scale, autotune=autotune)
         self.term = term if term is not None else default_term()
         self._n_arr = (ctypes.c_int64 * max(self.count, 1))(*self.ns)
         self._lda_arr = (ctypes.c_int64 * max(self.count, 1))(*[c[1] for c in cols])
@@ -317,6 +320,12 @@ class Batch:
             _check(lib().ir_batch_create(ctx._h, self.count, self._n_arr, self._A_arr, self._lda_arr,
                                          self._b_arr, self._x_arr, ctypes.byref(self.opts),
                                          ctypes.byref(self.term), ctypes.byref(self._h)))
+
+    def schedule(self):
+        """(grid, tc_min_trail) of the plan (ir_batch_schedule)."""
+        g, t = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ir_batch_schedule(self._h, ctypes.byref(g), ctypes.byref(t)))
+        return g.value, t.value
 
     def run(self, stream=None):
         _check(lib().ir_batch_run(self._h, ctypes.c_void_p(self.results_dev.data_ptr()), _stream_ptr(stream)))
@@ -425,6 +434,12 @@ class Factorization:
             err.report = R
             raise err
         return x, R
+
+    def schedule(self):
+        """(nb, panel_reserve_sms) of the factorization (ir_fact_schedule)."""
+        nb, r = ctypes.c_int(), ctypes.c_int()
+        _check(lib().ir_fact_schedule(self._h, ctypes.byref(nb), ctypes.byref(r)))
+        return nb.value, r.value
 
     def lu_solve(self, v: torch.Tensor, stream=None) -> torch.Tensor:
         """d = U^{-1} L^{-1} P v in binary32."""

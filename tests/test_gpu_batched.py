@@ -226,3 +226,39 @@ def test_one_shot_entry_point_matches_plan(ctx):
     assert res == res2
     for a, b in zip(xs, xs2):
         assert np.array_equal(a.cpu().numpy(), b)
+
+
+def test_batch_autotune_picks_a_candidate_and_keeps_parity(ctx):
+    """opts.autotune: the plan times the tensor-core crossover on the batch itself;
+    the tuned plan's results still meet the oracle bar (the SIMT and tensor-core
+    updates round the same operands to TF)."""
+    _, As, bs = irgen.case_batch_sizes([48, 130, 200, 257, 384, 512, 96, 300], seed=31)
+    plan = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16", autotune=True)
+    grid, tcm = plan.schedule()
+    assert grid >= 1 and tcm in (64, 128, 192, 256, 1 << 20)
+    plan.run()
+    res = plan.results()
+    for A, b, x, r in zip(As, bs, plan.xs, res):
+        ref = O.ir_solve(A, b, O.F16, nb=64)
+        if ref.status == O.CONVERGED:
+            assert r["status"] in ("converged", "stagnated")
+            assert O.rel_err_inf(x.cpu().numpy(), O.reference_solution(A, b)) <= O.parity_tol(O.cond_inf(A), O.F64)
+    untuned = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16")
+    assert untuned.schedule()[1] == 64
+
+
+def test_factor_autotune_schedule(ctx):
+    A, b, xt = irgen.case_green_sine(2048)
+    f = ctx.factor(dev_colmajor(A), tf="f32", autotune=True)
+    nb, r = f.schedule()
+    assert nb == 64 and r in (8, 12, 16, 24, 32)
+    x, rep = f.solve(dev_vec(b))
+    assert rep.status in ("converged", "stagnated")
+    assert O.rel_err_inf(x.cpu().numpy(), xt) <= O.parity_tol(1.8e5, O.F64)
+    # the binary32 factors do not depend on the schedule (bitwise)
+    g = ctx.factor(dev_colmajor(A), tf="f32")
+    assert g.schedule() == (64, 16)
+    np.testing.assert_array_equal(f.factors(), g.factors())
+    # a second tuned factorization of the same size reuses the context's choice
+    h = ctx.factor(dev_colmajor(A), tf="f32", autotune=True)
+    assert h.schedule() == f.schedule()
