@@ -314,7 +314,7 @@ def run_batched(args, ctx, dev, stream, flush, ws, rank):
            "fp64_lu_floor": "the batch's 2N^3/3 LU flops at the measured binary64 GEMM rate "
                             "(torch.matmul 4096^3): no binary64 LU of these systems can be faster"}
     for tf in ("f16", "bf16"):
-        plan = ctx.batch(Ad, bd, tf=tf)
+        plan = ctx.batch(Ad, bd, tf=tf, autotune=True)      # the plan times its schedule candidates
         for _ in range(max(3, args.warmup)):
             plan.run()
         torch.cuda.synchronize()
@@ -337,7 +337,9 @@ def run_batched(args, ctx, dev, stream, flush, ws, rank):
         st = {}
         for r in res:
             st[r["status"]] = st.get(r["status"], 0) + 1
+        grid, tcm = plan.schedule()
         out[tf] = {"ms": t, "solves_per_s": ws * count / (t * 1e-3), "speedup_vs_fp64_lu": t64 / t,
+                   "schedule": {"grid": grid, "tc_min_trail": tcm, "autotuned": True},
                    "speedup_vs_fp64_floor": floor64 / t,
                    "gpu_launches_per_step": launches / args.steps,
                    "status": st, "mean_iters": float(np.mean([r["iters"] for r in res])),
@@ -408,7 +410,7 @@ def main():
         return ms, out, prof, launches
 
     # --- headline: TF = binary32 (bit-exact FP32 LU), default termination
-    fact32 = ctx.factor(A_d, tf="f32")
+    fact32 = ctx.factor(A_d, tf="f32", autotune=True)     # schedule timed on this A before the run
     x32 = torch.empty_like(b_d)
     term = ir.default_term()
 
@@ -425,7 +427,7 @@ def main():
     t32 = max_over_ranks(statistics.mean(ms32_plain), ws)
 
     # --- tensor-core arm: TF = TF32, litmax raised so IR reaches its limiting accuracy
-    fact_tc = ctx.factor(A_d, tf="tf32")
+    fact_tc = ctx.factor(A_d, tf="tf32", autotune=True)
     xtc = torch.empty_like(b_d)
     term_tc = ir.default_term(litmax=30)
 
@@ -631,7 +633,9 @@ def main():
         "config": {"workload": f"green_sine_N{n}_alpha800_TWf64_TFf32_TRf64", "n": n, "alpha": ALPHA,
                    "TW": "f64", "TF": "f32", "TR": "f64", "rhs": "b = A sin(pi x)",
                    "l2": "flushed by a 512 MiB write before every timed step",
-                   "parallelism": "replicas" if ws > 1 else "single"},
+                   "parallelism": "replicas" if ws > 1 else "single",
+                   "schedule": {"nb": fact32.schedule()[0], "panel_reserve_sms": fact32.schedule()[1],
+                                "autotuned": True}},
         "iters": rep32.iters, "status": rep32.status,
         "rel_err_vs_closed_form": err_true, "rel_err_vs_fp64_lu": err_vs_lu64,
         "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": (t64 / t32) if t64 else None,

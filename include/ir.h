@@ -199,6 +199,9 @@ typedef struct {
     int32_t timeout;     /* 1: a bounded device-side wait gave up (status IR_FAILED) */
     double rnorm;        /* ||r||_inf after the last residual (||b|| when none ran) */
     double scale;        /* s of the rounded copy */
+    int32_t tf;          /* ir_dtype of the factorization that produced x (see escalation) */
+    int32_t pad;
+    double bnorm;        /* ||b||_inf (rhist[0]) */
 } ir_batch_result;
 
 typedef struct ir_batch ir_batch;
@@ -226,6 +229,17 @@ ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host,
  * (they share its workspace): order them on one stream. */
 ir_status ir_batch_run(ir_batch *batch, ir_batch_result *results_dev, void *stream);
 void ir_batch_destroy(ir_batch *batch);
+
+/* Precision escalation (beyond the paper, whose Sec. 3 shows binary16 IR
+ * failing on ill-conditioned systems): ir_batch_run, then every member that
+ * neither converged nor stopped (stagnated, or litmax) with ||r|| <= rtol ||b||
+ * is solved again from scratch with TF = tf2 (IR_F32 or IR_TF32; the plan's
+ * TW, term and workspace), its result and x overwritten (results_dev[i].tf
+ * tells which TF produced x).  rtol >= 0 (0: keep only converged members).
+ * Selection and the second pass run on the device: no allocation, no host
+ * synchronisation, capturable in a CUDA graph. */
+ir_status ir_batch_run_escalate(ir_batch *batch, ir_dtype tf2, double rtol, ir_batch_result *results_dev,
+                                void *stream);
 
 /* One-shot batch: ir_batch_create + ir_batch_run + synchronisation of
  * `stream` + ir_batch_destroy. */

@@ -411,6 +411,8 @@ struct ir_batch {
     int64_t ws_stride;
     int grid;
     int tc_min_trail;    // smallest trailing block updated on the tensor cores (tuned)
+    int *order2;         // escalation: the unconverged members (device)
+    unsigned *count2;    // and their number (device)
 };
 
 namespace {
@@ -419,6 +421,8 @@ void free_batch(ir_batch *b) {
     if (!b) return;
     cudaFree(b->desc);
     cudaFree(b->order);
+    cudaFree(b->order2);
+    cudaFree(b->count2);
     cudaFree(b->ticket);
     cudaFree(b->ws);
     delete b;
@@ -1073,6 +1077,8 @@ ir_status ir_batch_create(ir_ctx *ctx, int64_t count, const int64_t *n_host, con
     if (e == cudaSuccess) e = cudaMalloc(&b->desc, desc.size());
     if (e == cudaSuccess) e = cudaMalloc(&b->order, cnt * sizeof(int));
     if (e == cudaSuccess) e = cudaMalloc(&b->ticket, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc(&b->order2, cnt * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&b->count2, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc(&b->ws, (size_t)b->grid * b->ws_stride * sizeof(float));
     if (e == cudaSuccess) e = cudaMemcpy(b->desc, desc.data(), desc.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->order, order.data(), cnt * sizeof(int), cudaMemcpyHostToDevice);
@@ -1117,6 +1123,19 @@ ir_status ir_batch_run(ir_batch *b, ir_batch_result *results_dev, void *stream) 
 }
 
 void ir_batch_destroy(ir_batch *b) { free_batch(b); }
+
+ir_status ir_batch_run_escalate(ir_batch *b, ir_dtype tf2, double rtol, ir_batch_result *results_dev,
+                                void *stream) {
+    if (!b || (b->count > 0 && !results_dev) || (tf2 != IR_F32 && tf2 != IR_TF32) || !(rtol >= 0))
+        return IR_EINVAL;
+    ir_status st = ir_batch_run(b, results_dev, stream);
+    if (st != IR_OK || b->count == 0) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    RUN(KC_BATCHED, s, launch_select_unconverged(results_dev, b->order, b->count, rtol, b->order2, b->count2, s));
+    RUN(KC_BATCHED, s, launch_batched(b->desc, b->order2, b->count, b->ticket, b->ws, b->ws_stride, b->grid, b->TW,
+                                      tf2, 0, &b->term, b->tc_min_trail, results_dev, s, b->count2));
+    return IR_OK;
+}
 
 ir_status ir_factor_solve_batched(ir_ctx *ctx, int64_t count, const int64_t *n_host, const void *const *A_dev,
                                   const int64_t *lda_host, const void *const *b_dev, void *const *x_dev,

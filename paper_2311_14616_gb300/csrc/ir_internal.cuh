@@ -204,7 +204,10 @@ void batch_fill_desc(void *desc, int64_t i, const void *A, int64_t lda, const vo
 cudaError_t batch_grid(int sms, int64_t count, int *grid);
 cudaError_t launch_batched(const void *sys, const int *order, int64_t count, unsigned *ticket, float *ws,
                            int64_t ws_stride, int grid, ir_dtype tw, ir_dtype tf, int fp16_scale,
-                           const ir_term *t, int tc_min_trail, ir_batch_result *results, cudaStream_t s);
+                           const ir_term *t, int tc_min_trail, ir_batch_result *results, cudaStream_t s,
+                           const unsigned *dcount = nullptr);
+cudaError_t launch_select_unconverged(const ir_batch_result *results, const int *order, int64_t count,
+                                      double rtol, int *order2, unsigned *count2, cudaStream_t s);
 
 // ---- device helpers --------------------------------------------------------
 __device__ __forceinline__ unsigned smem_u32(const void *p) {

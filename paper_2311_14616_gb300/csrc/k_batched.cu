@@ -611,12 +611,14 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
     if (n == 0) {
         if (t == 0) {
             res->status = IR_CONVERGED;
+            res->tf = cfg.tf;
             res->iters = 0;
             res->info = 0;
             res->nonfinite = 0;
             res->timeout = 0;
             res->rnorm = 0.0;
             res->scale = 1.0;
+            res->bnorm = 0.0;
         }
         return;
     }
@@ -719,12 +721,14 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
                     if (t == 0) {
                         sm.abort = 1;
                         res->status = IR_FAILED;
+                        res->tf = cfg.tf;
                         res->iters = 0;
                         res->info = 0;
                         res->nonfinite = 0;
                         res->timeout = 1;
                         res->rnorm = 0.0;
                         res->scale = 1.0;
+                        res->bnorm = 0.0;
                     }
                     __syncthreads();
                     return;
@@ -818,19 +822,21 @@ __device__ void b_system(const BatchSys &S, float *W, const BatchCfg &cfg, ir_ba
     }
     if (t == 0) {
         res->status = status;
+        res->tf = cfg.tf;
         res->iters = k;
         res->info = info;
         res->nonfinite = nonfinite;
         res->timeout = 0;
         res->rnorm = rprev;
         res->scale = s;
+        res->bnorm = bnorm;
     }
     __syncthreads();
 }
 
 __global__ void __launch_bounds__(BT, 1)
-    k_batched(const BatchSys *sys, const int *order, unsigned *ticket, float *ws, int64_t ws_stride, BatchCfg cfg,
-              ir_batch_result *results) {
+    k_batched(const BatchSys *sys, const int *order, const unsigned *dcount, unsigned *ticket, float *ws,
+              int64_t ws_stride, BatchCfg cfg, ir_batch_result *results) {
     extern __shared__ __align__(16) unsigned char bsm[];
     const unsigned s0 = smem_u32(bsm);
     unsigned char *base = bsm + (((s0 + 1023u) & ~1023u) - s0);
@@ -839,6 +845,7 @@ __global__ void __launch_bounds__(BT, 1)
     BSmem &sm = *reinterpret_cast<BSmem *>(Us + NB * NB);
     float *W = ws + (int64_t)blockIdx.x * ws_stride;
     const bool use_tc = (cfg.tf == IR_F16 || cfg.tf == IR_BF16);
+    const int count = dcount ? (int)*dcount : cfg.count;   // device count: the escalation pass
     if (threadIdx.x == 0) {
         sm.abort = 0;
         mbar_init(smem_u32(&sm.mma_bar), 1);
@@ -860,7 +867,7 @@ __global__ void __launch_bounds__(BT, 1)
         const int idx = sm.cur;
         const int abort = sm.abort;
         __syncthreads();
-        if (idx >= cfg.count || abort) break;
+        if (idx >= count || abort) break;
         const int id = order[idx];
         const BatchSys S = sys[id];
         if (cfg.tw == IR_F64)
@@ -884,7 +891,59 @@ __global__ void __launch_bounds__(BT, 1)
     }
 }
 
+// The members of order[0..count) to solve again, in the same (largest-first)
+// order, into order2[0..*count2): one CTA, chunked block scan.  A member is
+// kept when it converged, or stagnated / ran out of iterations with
+// ||r|| <= rtol ||b||; every other one (failed, diverged, or stopped at a
+// larger residual) is selected.
+__global__ void __launch_bounds__(1024) k_select_unconverged(const ir_batch_result *results, const int *order,
+                                                             int count, double rtol, int *order2,
+                                                             unsigned *count2) {
+    __shared__ int wsum[32];
+    __shared__ int base;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) base = 0;
+    __syncthreads();
+    for (int c0 = 0; c0 < count; c0 += 1024) {
+        const int idx = c0 + t;
+        const int id = idx < count ? order[idx] : -1;
+        int sel = 0;
+        if (id >= 0) {
+            const ir_batch_result &r = results[id];
+            const bool small = (r.status == IR_STAGNATED || r.status == IR_MAXIT) && r.rnorm <= rtol * r.bnorm;
+            sel = (r.status == IR_CONVERGED || small) ? 0 : 1;
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, sel);
+        const int before = __popc(mask & ((1u << lane) - 1u));
+        if (lane == 31) wsum[warp] = before + sel;
+        __syncthreads();
+        if (warp == 0) {
+            const int v = wsum[lane];
+            int incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            wsum[lane] = incl - v;      // exclusive prefix of the warp totals
+        }
+        __syncthreads();
+        if (sel) order2[base + wsum[warp] + before] = id;
+        __syncthreads();
+        if (t == 1023) base += wsum[31] + before + sel;
+        __syncthreads();
+    }
+    if (t == 0) *count2 = (unsigned)base;
+}
+
 }  // namespace
+
+cudaError_t launch_select_unconverged(const ir_batch_result *results, const int *order, int64_t count,
+                                      double rtol, int *order2, unsigned *count2, cudaStream_t s) {
+    count_launch();
+    k_select_unconverged<<<1, 1024, 0, s>>>(results, order, (int)count, rtol, order2, count2);
+    return cudaGetLastError();
+}
 
 size_t batch_desc_bytes() { return sizeof(BatchSys); }
 
@@ -912,7 +971,7 @@ cudaError_t batch_grid(int sms, int64_t count, int *grid) {
 
 cudaError_t launch_batched(const void *sys, const int *order, int64_t count, unsigned *ticket, float *ws,
                            int64_t ws_stride, int grid, ir_dtype tw, ir_dtype tf, int fp16_scale, const ir_term *t,
-                           int tc_min_trail, ir_batch_result *results, cudaStream_t s) {
+                           int tc_min_trail, ir_batch_result *results, cudaStream_t s, const unsigned *dcount) {
     if (count <= 0) return cudaSuccess;
     BatchCfg c;
     c.Cr = t->Cr;
@@ -929,8 +988,8 @@ cudaError_t launch_batched(const void *sys, const int *order, int64_t count, uns
     cudaError_t e = cudaMemsetAsync(ticket, 0, sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     count_launch();
-    k_batched<<<grid, BT, kBatchSmem, s>>>(static_cast<const BatchSys *>(sys), order, ticket, ws, ws_stride, c,
-                                           results);
+    k_batched<<<grid, BT, kBatchSmem, s>>>(static_cast<const BatchSys *>(sys), order, dcount, ticket, ws, ws_stride,
+                                           c, results);
     return cudaGetLastError();
 }
 

@@ -55,7 +55,8 @@ class BatchResult(ctypes.Structure):
     """ir_batch_result (one per system of a batch)."""
     _fields_ = [("status", ctypes.c_int32), ("iters", ctypes.c_int32), ("info", ctypes.c_int64),
                 ("nonfinite", ctypes.c_int32), ("timeout", ctypes.c_int32), ("rnorm", ctypes.c_double),
-                ("scale", ctypes.c_double)]
+                ("scale", ctypes.c_double), ("tf", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("bnorm", ctypes.c_double)]
 
 
 BATCH_MAX_N = 512
@@ -109,6 +110,7 @@ def lib():
             "ir_residual": (i32, [vp, i64, i32, vp, i64, vp, vp, vp, vp, vp]),
             "ir_batch_create": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), P(vp)]),
             "ir_batch_run": (i32, [vp, vp, vp]),
+            "ir_batch_run_escalate": (i32, [vp, i32, ctypes.c_double, vp, vp]),
             "ir_batch_destroy": (None, [vp]),
             "ir_factor_solve_batched": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), vp, vp]),
             "ir_fact_pivots": (i32, [vp, vp]),
@@ -330,6 +332,13 @@ class Batch:
     def run(self, stream=None):
         _check(lib().ir_batch_run(self._h, ctypes.c_void_p(self.results_dev.data_ptr()), _stream_ptr(stream)))
 
+    def run_escalate(self, tf2="f32", rtol: float = 1e-10, stream=None):
+        """run(), then the members that neither converged nor stopped with ||r|| <= rtol ||b||
+        again with TF = tf2 (ir_batch_run_escalate)."""
+        t2 = DTYPES[tf2] if isinstance(tf2, str) else int(tf2)
+        _check(lib().ir_batch_run_escalate(self._h, t2, ctypes.c_double(rtol),
+                                           ctypes.c_void_p(self.results_dev.data_ptr()), _stream_ptr(stream)))
+
     def results(self):
         """Per-system outcomes as a list of dicts (synchronises the device)."""
         raw = bytes(self.results_dev.cpu().numpy().tobytes())
@@ -339,7 +348,7 @@ class Batch:
             r = arr[i]
             out.append({"status": STATUS.get(r.status, str(r.status)), "iters": r.iters, "info": r.info,
                         "nonfinite": bool(r.nonfinite), "timeout": bool(r.timeout), "rnorm": r.rnorm,
-                        "scale": r.scale})
+                        "scale": r.scale, "tf": r.tf, "bnorm": r.bnorm})
         return out
 
     def destroy(self):

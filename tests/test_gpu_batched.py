@@ -262,3 +262,55 @@ def test_factor_autotune_schedule(ctx):
     # a second tuned factorization of the same size reuses the context's choice
     h = ctx.factor(dev_colmajor(A), tf="f32", autotune=True)
     assert h.schedule() == f.schedule()
+
+
+def test_batch_precision_escalation(ctx):
+    """ir_batch_run_escalate: the members whose binary16 IR did not converge are
+    solved again with binary32 factors on the device; those results are bitwise
+    the oracle's binary32 IR (the batch's binary32 path is the oracle's
+    arithmetic), the others are the binary16 run's.  Capturable in a graph."""
+    ns = [96, 200, 320, 448, 512, 160, 384, 256, 64, 500, 128, 300]
+    alphas, As, bs = irgen.case_batch_sizes(ns, seed=1234)
+    # two members near a singular mode (1 - alpha lambda_k ~ 0): binary16 IR fails there
+    for i, a in ((2, 88.9), (5, 157.8)):
+        n = ns[i]
+        As[i] = np.asfortranarray(np.eye(n) - a * irgen.gmat_midpoint(n))
+    rtol = 1e-10
+    Ad = [dev_colmajor(A) for A in As]
+    bd = [dev_vec(b) for b in bs]
+    plain = ctx.batch(Ad, bd, tf="f16")
+    plain.run()
+    first = plain.results()
+    plan = ctx.batch(Ad, bd, tf="f16")
+    plan.run_escalate("f32", rtol)
+    res = plan.results()
+    xs = [x.cpu().numpy() for x in plan.xs]
+    escalated = [i for i, r in enumerate(first)
+                 if not (r["status"] == "converged"
+                         or (r["status"] in ("stagnated", "maxit") and r["rnorm"] <= rtol * r["bnorm"]))]
+    assert escalated, "the near-singular members should not reach 1e-10 with binary16 factors"
+    assert len(escalated) < len(ns)
+    for i, r in enumerate(res):
+        if i in escalated:
+            o = O.ir_solve(As[i], bs[i], O.F32)
+            assert r["tf"] == ir.F32
+            assert r["status"] == O.STATUS_NAMES[o.status] and r["iters"] == o.iters
+            np.testing.assert_array_equal(xs[i], o.x)
+        else:
+            assert r["tf"] == ir.F16 and r == first[i]
+    # graph capture of the escalating run gives the same bits
+    graph = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(graph, stream=s):
+            plan.run_escalate("f32", rtol)
+    for x in plan.xs:
+        x.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    for a, x in zip(xs, plan.xs):
+        np.testing.assert_array_equal(a, x.cpu().numpy())
+    assert plan.results() == res
+    with pytest.raises(ir.IRError, match="IR_EINVAL"):
+        plan.run_escalate("f16")
