@@ -345,6 +345,30 @@ def run_batched(args, ctx, dev, stream, flush, ws, rank):
                    "status": st, "mean_iters": float(np.mean([r["iters"] for r in res])),
                    "rel_err_vs_fp64_lu": {"median": float(np.median(errs)), "max": float(np.max(errs)),
                                           "frac_le_1e-12": float(np.mean(errs <= 1e-12))}}
+        if tf == "f16":
+            # precision escalation: members that stop above 1e-10 ||b|| are solved again
+            # with binary32 factors in a second device pass (ir_batch_run_escalate)
+            ms_e = []
+            for _ in range(2):
+                plan.run_escalate("f32", 1e-10)
+            torch.cuda.synchronize()
+            for _ in range(args.steps):
+                flush.fill_(1.0)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.run_escalate("f32", 1e-10)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms_e.append(e0.elapsed_time(e1))
+            te = max_over_ranks(statistics.mean(ms_e), ws)
+            res_e = plan.results()
+            errs_e = np.array([np.max(np.abs(x.cpu().numpy() - xr)) / np.max(np.abs(xr))
+                               for x, xr in zip(plan.xs, xref)])
+            out[tf]["escalated_to_f32"] = {
+                "ms": te, "solves_per_s": ws * count / (te * 1e-3), "rtol": 1e-10,
+                "members_escalated": int(sum(1 for r in res_e if r["tf"] == ir.F32)),
+                "rel_err_vs_fp64_lu": {"median": float(np.median(errs_e)), "max": float(np.max(errs_e)),
+                                       "frac_le_1e-12": float(np.mean(errs_e <= 1e-12))}}
         plan.destroy()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         import oracle as O

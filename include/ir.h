@@ -138,6 +138,14 @@ ir_status ir_refactor(ir_fact *fact, const void *B, int64_t ldb, void *stream);
 ir_status ir_solve(ir_fact *fact, const void *b, void *x, const ir_term *term,
                    void *stream, ir_report *rep);
 
+/* Several right-hand sides on one factorization (Sec. 6.1: the factors are
+ * reused, each solve costs O(N^2)): X(:, j) = A^{-1} B(:, j) for j < nrhs,
+ * each column refined by its own IR loop and termination test (as ir_solve).
+ *   B: n x nrhs in TW, column-major, ldb >= n; X likewise with ldx.
+ *   reps: NULL or nrhs reports.  Returns the first error of any column. */
+ir_status ir_solve_many(ir_fact *fact, int64_t nrhs, const void *B, int64_t ldb, void *X, int64_t ldx,
+                        const ir_term *term, void *stream, ir_report *reps);
+
 /* End-to-end solve from HOST memory: copies A and b to the device, factors,
  * refines, copies x back and releases the device buffers.  A_host: n x n
  * column-major in TW (lda); b_host, x_host: n values in TW.  Synchronous.

@@ -991,6 +991,22 @@ ir_status ir_solve_bicgstab(ir_fact *f, const void *b, void *x, const ir_term *t
     return krylov_solve(KRY_BICGSTAB, f, b, x, term, kopts, stream, rep, khist);
 }
 
+ir_status ir_solve_many(ir_fact *f, int64_t nrhs, const void *B, int64_t ldb, void *X, int64_t ldx,
+                        const ir_term *term, void *stream, ir_report *reps) {
+    if (!f || nrhs < 0 || ldb < (f->n > 1 ? f->n : 1) || ldx < (f->n > 1 ? f->n : 1)) return IR_EINVAL;
+    if (nrhs > 0 && f->n > 0 && (!B || !X)) return IR_EINVAL;
+    const size_t esz = (f->TW == IR_F64) ? 8 : 4;
+    ir_status first = IR_OK;
+    for (int64_t j = 0; j < nrhs; ++j) {
+        const void *bj = static_cast<const char *>(B) + (size_t)j * ldb * esz;
+        void *xj = static_cast<char *>(X) + (size_t)j * ldx * esz;
+        const ir_status st = ir_solve(f, bj, xj, term, stream, reps ? reps + j : nullptr);
+        if (st != IR_OK && first == IR_OK) first = st;
+        if (st == IR_EINVAL || st == IR_ECUDA || st == IR_ENOMEM) return st;
+    }
+    return first;
+}
+
 ir_status ir_lu_solve(ir_fact *f, const float *v, float *d, void *stream) {
     if (!f || (f->n > 0 && (!v || !d))) return IR_EINVAL;
     if (f->n == 0) return IR_OK;

@@ -102,6 +102,7 @@ def lib():
             "ir_solve": (i32, [vp, vp, vp, P(Term), vp, P(_Report)]),
             "ir_solve_host": (i32, [vp, i64, vp, i64, vp, vp, P(Opts), P(Term), vp, P(_Report)]),
             "ir_lu_solve": (i32, [vp, vp, vp, vp]),
+            "ir_solve_many": (i32, [vp, i64, vp, i64, vp, i64, P(Term), vp, vp]),
             "ir_default_krylov_opts": (None, [P(KrylovOpts)]),
             "ir_gmres_reserve": (i32, [vp, i32]),
             "ir_solve_gmres": (i32, [vp, vp, vp, P(Term), P(KrylovOpts), vp, P(_Report), vp]),
@@ -404,6 +405,21 @@ class Factorization:
             err.report = R
             raise err
         return x, R
+
+    def solve_many(self, B: torch.Tensor, term: Optional[Term] = None, stream=None):
+        """X = A^{-1} B for the columns of B (n x nrhs), each refined by its own IR loop
+        (ir_solve_many); returns (X column-major, [Report])."""
+        if B.dim() != 2 or B.shape[0] != self.n:
+            raise ValueError("B must be n x nrhs")
+        Bc = B.to(self.A.dtype).t().contiguous().t()         # column-major, ldb = n
+        ldb = max(self.n, 1)
+        nrhs = Bc.shape[1]
+        X = torch.empty((nrhs, self.n), dtype=self.A.dtype, device=Bc.device).t()
+        reps = (_Report * max(nrhs, 1))()
+        t = term if term is not None else default_term()
+        _check(lib().ir_solve_many(self._h, nrhs, ctypes.c_void_p(Bc.data_ptr()), ldb, ctypes.c_void_p(X.data_ptr()),
+                                   max(self.n, 1), ctypes.byref(t), _stream_ptr(stream), reps))
+        return X, [_report(reps[j]) for j in range(nrhs)]
 
     def gmres_reserve(self, basissize: int = 10):
         """Reserve the Krylov basis (mpglu's allocation, Sec. 4.4)."""

@@ -227,3 +227,22 @@ def test_term_mode_validation(ctx):
     As = [dev_colmajor(A)]
     with pytest.raises(ir.IRError, match="IR_EUNSUPPORTED"):
         ctx.solve_batched(As, [dev_vec(b)], tf="f32", term=ir.default_term(mode=1))
+
+
+def test_solve_many_columns_equal_single_solves(ctx):
+    """ir_solve_many: one factorization, nrhs independent IR loops; each column is
+    bitwise the single-right-hand-side solve, with its own termination."""
+    A, _ = irgen.case_green(777, 800.0)
+    g = np.random.Generator(np.random.PCG64(4242))
+    B = g.standard_normal((777, 5))
+    B[:, 3] = 0.0                                      # a zero column converges at once
+    f = ctx.factor(dev_colmajor(A), tf="f32")
+    X, reps = f.solve_many(torch.from_numpy(B).cuda())
+    X = X.cpu().numpy()
+    for j in range(5):
+        x, rep = f.solve(dev_vec(np.ascontiguousarray(B[:, j])))
+        np.testing.assert_array_equal(X[:, j], x.cpu().numpy())
+        assert reps[j].status == rep.status and reps[j].rhist == rep.rhist
+    assert reps[3].status == "converged" and reps[3].iters == 0
+    xr = O.reference_solution(A, B[:, 0])
+    assert O.rel_err_inf(X[:, 0], xr) <= O.parity_tol(O.cond_inf(A), O.F64)
