@@ -42,15 +42,19 @@ struct PanelSmem {
     alignas(16) float recv[2][kPanelMaxCluster][kRec];
     alignas(8) unsigned long long recv_bar[2];
     int piv_log[NB];             // p_k of every step (the panel's interchanges)
+    int posv[RPC];               // epilogue: each row slot's final position (-1: none)
+    int kpv[RPC];                // and the step at which it became the pivot row
     int zero_piv;                // first zero pivot of this panel (1-based), or 0
     int abort_flag;
 };
 static_assert(offsetof(PanelSmem, stage) % 16 == 0 && offsetof(PanelSmem, recv) % 16 == 0 &&
                   (kRec * 4) % 16 == 0,
               "float4 records of the panel's shared memory must be 16-byte aligned");
-// Dynamic shared memory after PanelSmem: Ls[NB][RPC] multipliers by step and
-// row slot, Us[NB][NB] pivot rows.
-constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)NB * RPC + sizeof(float) * NB * NB + 16;
+// Dynamic shared memory after PanelSmem: Ls[RPC][LS] multipliers by row slot and
+// step (odd stride: the per-step column stores and the epilogue's row reads
+// spread over the banks), Us[NB][NB] pivot rows.
+constexpr int LS = NB + 1;
+constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)RPC * LS + sizeof(float) * NB * NB + 16;
 
 __device__ __forceinline__ unsigned cluster_rank() {
     unsigned r;
@@ -113,32 +117,17 @@ __device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
     }
 }
 
-// Store one operand row (NB values, rounded to TF) into Aop/Bop.
-__device__ __forceinline__ void store_op_row(void *op, int64_t row, const float *v, ir_dtype tf) {
+// Store values 4q .. 4q + 3 of one operand row (rounded to TF) into Aop/Bop.
+__device__ __forceinline__ void store_op_chunk(void *op, int64_t row, int q, float4 v, ir_dtype tf) {
     if (tf == IR_TF32) {
-        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(op) + row * NB);
-#pragma unroll
-        for (int c = 0; c < NB; c += 4)
-            dst[c / 4] = make_float4(round_tf(v[c], tf), round_tf(v[c + 1], tf), round_tf(v[c + 2], tf),
-                                     round_tf(v[c + 3], tf));
+        reinterpret_cast<float4 *>(static_cast<float *>(op) + row * NB)[q] =
+            make_float4(round_tf(v.x, tf), round_tf(v.y, tf), round_tf(v.z, tf), round_tf(v.w, tf));
     } else if (tf == IR_BF16) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(op) + row * NB);
-#pragma unroll
-        for (int c = 0; c < NB; c += 8) {
-            __nv_bfloat162 p[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) p[q] = __floats2bfloat162_rn(v[c + 2 * q], v[c + 2 * q + 1]);
-            dst[c / 8] = *reinterpret_cast<uint4 *>(p);
-        }
+        __nv_bfloat162 p[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
+        reinterpret_cast<uint2 *>(static_cast<__nv_bfloat16 *>(op) + row * NB)[q] = *reinterpret_cast<uint2 *>(p);
     } else if (tf == IR_F16) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__half *>(op) + row * NB);
-#pragma unroll
-        for (int c = 0; c < NB; c += 8) {
-            __half2 p[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) p[q] = __floats2half2_rn(v[c + 2 * q], v[c + 2 * q + 1]);
-            dst[c / 8] = *reinterpret_cast<uint4 *>(p);
-        }
+        __half2 p[2] = {__floats2half2_rn(v.x, v.y), __floats2half2_rn(v.z, v.w)};
+        reinterpret_cast<uint2 *>(static_cast<__half *>(op) + row * NB)[q] = *reinterpret_cast<uint2 *>(p);
     }
 }
 
@@ -150,14 +139,6 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 #pragma unroll
     for (int q = 0; q < 15; ++q) s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
     s4[16] = make_float4(a[61], a[62], a[63], 0.f);
-}
-
-// The row's values at its final position: multipliers of the steps before it
-// became the pivot row (kp; nbp if never), then the U part staged at step kp.
-__device__ __forceinline__ void final_row(float (&a)[NB], const float *Ls, int slot, const float *Us, int kp,
-                                          int nbp) {
-#pragma unroll
-    for (int c = 0; c < NB; ++c) a[c] = (c < kp) ? Ls[c * RPC + slot] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
 }
 
 // One cluster factors the panel AF[j:n, j:j+nbp].  Thread t of CTA c keeps
@@ -182,8 +163,8 @@ __global__ void __launch_bounds__(T, 1)
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
     extern __shared__ __align__(16) unsigned char panel_smem[];
     PanelSmem &sm = *reinterpret_cast<PanelSmem *>(panel_smem);
-    float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [NB][RPC]
-    float *Us = Ls + (size_t)NB * RPC;                                        // [NB][NB]
+    float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [RPC][LS]
+    float *Us = Ls + (size_t)RPC * LS;                                        // [NB][NB]
     const unsigned crank = cluster_rank();
     const unsigned csize = cluster_size();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -324,12 +305,12 @@ __global__ void __launch_bounds__(T, 1)
         if (u0) {
             l0 = a0[0];
             if (piv != 0.f) l0 = (fabsf(piv) >= FLT_MIN) ? l0 * r : l0 / piv;
-            Ls[k * RPC + t] = l0;
+            Ls[t * LS + k] = l0;
         }
         if (u1) {
             l1 = a1[0];
             if (piv != 0.f) l1 = (fabsf(piv) >= FLT_MIN) ? l1 * r : l1 / piv;
-            Ls[k * RPC + T + t] = l1;
+            Ls[(T + t) * LS + k] = l1;
         }
         // No branches on the live width: past it, the windows and the staged
         // record hold zeros (a value shifts left only from inside the live
@@ -371,17 +352,34 @@ __global__ void __launch_bounds__(T, 1)
     cluster_sync_all();   // every perm read of the cluster is done
     if (moved0) perm[j + pos0] = porg0;
     if (moved1) perm[j + pos1] = porg1;
+    // Final rows, written a row (256 contiguous bytes) per half warp: the
+    // multipliers of the steps before a row became the pivot row come from its
+    // slot of Ls, the rest (its U part) from Us; each slot's destination and
+    // pivot step go through shared memory.
+    sm.posv[t] = valid0 ? pos0 : -1;
+    sm.posv[t + T] = valid1 ? pos1 : -1;
+    sm.kpv[t] = kp0;
+    sm.kpv[t + T] = kp1;
+    __syncthreads();
+    {
+        const int q = lane & 15;
+        const bool ops = has_trailing && Aop != nullptr;
+#pragma unroll 4
+        for (int it = 0; it < RPC / (2 * NW); ++it) {
+            const int sl = 2 * NW * it + 2 * warp + (lane >> 4);
+            const int pos = sm.posv[sl];
+            if (pos < 0) continue;
+            const int kp = sm.kpv[sl];
+            float v[4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const bool valid = h ? valid1 : valid0;
-        if (!valid) continue;
-        const int pos = h ? pos1 : pos0, kp = h ? kp1 : kp0;
-        final_row(a0, Ls, t + h * T, Us, kp, nbp);
-        float4 *dst = reinterpret_cast<float4 *>(AF + (int64_t)(j + pos) * ldf + j);
-#pragma unroll
-        for (int c = 0; c < NB; c += 4)
-            if (c < nbp) dst[c / 4] = make_float4(a0[c], a0[c + 1], a0[c + 2], a0[c + 3]);
-        if (has_trailing && Aop != nullptr && pos >= NB) store_op_row(Aop, pos - NB, a0, tf);
+            for (int i = 0; i < 4; ++i) {
+                const int c = 4 * q + i;
+                v[i] = (c < kp) ? Ls[sl * LS + c] : (c < nbp ? Us[kp * NB + (c - kp)] : 0.f);
+            }
+            const float4 w = make_float4(v[0], v[1], v[2], v[3]);
+            if (4 * q < nbp) reinterpret_cast<float4 *>(AF + (int64_t)(j + pos) * ldf + j)[q] = w;
+            if (ops && pos >= NB) store_op_chunk(Aop, pos - NB, q, w, tf);
+        }
     }
     cluster_sync_all();   // no CTA leaves while its shared memory may be written
 }
