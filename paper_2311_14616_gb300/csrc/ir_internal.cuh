@@ -12,6 +12,7 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdlib.h>
 
 #include "../../include/ir.h"
 
@@ -218,6 +219,30 @@ __device__ __forceinline__ unsigned long long globaltimer() {
     unsigned long long t;
     asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
     return t;
+}
+
+// Programmatic dependent launch: a kernel launched with set_pdl() may be
+// scheduled while its predecessor on the stream is still running; it lets its
+// own successor launch at once (pdl_trigger) and waits for the predecessor's
+// completion and memory (pdl_wait) before it reads anything.  Both are no-ops
+// for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+inline bool pdl_enabled() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("IR_NO_PDL");
+        v = !(e && e[0] && e[0] != '0');
+    }
+    return v != 0;
+}
+// Fill a launch attribute for programmatic dependent launch; returns the number
+// of attributes written (0 when disabled).
+inline unsigned set_pdl(cudaLaunchAttribute *a) {
+    if (!pdl_enabled()) return 0;
+    a->id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    a->val.programmaticStreamSerializationAllowed = 1;
+    return 1;
 }
 
 // Bounded wait limit for inter-CTA flags (nanoseconds).

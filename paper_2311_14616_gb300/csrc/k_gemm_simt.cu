@@ -3,6 +3,7 @@
 // from the stored value -- the same operations as the unblocked right-looking
 // algorithm, so the binary32 factors are bitwise those of the plain LU.
 #include "ir_internal.cuh"
+#include "lu_tiles.cuh"
 
 namespace ir {
 namespace {
@@ -13,6 +14,8 @@ constexpr int kShareCluster = 8;
 // Columns [cb, ce) of the trailing matrix (cb, ce multiples of 64, or ce = n);
 // tiles are taken in a grid-stride loop so the grid can leave SMs free.
 __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n, int j, int cb, int ce) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ __align__(16) float As[BK][BM + 4];   // As[k][i] = L21[i][k]
     __shared__ __align__(16) float Bs[BK][BN + 4];   // Bs[k][c] = U12[k][c]
     const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
@@ -89,62 +92,15 @@ __global__ void __launch_bounds__(256) k_gemm_simt(float *AF, int64_t ldf, int n
 }
 
 // The same update for a narrow column range (<= 64 columns: the next block
-// column of the lookahead, on the critical path): 64 x 64 tiles, so twice the
-// CTAs of the wide kernel for the same rows; thread (ty, tx) owns rows
-// 4 ty .. 4 ty + 3 and columns 4 tx .. 4 tx + 3, fmaf chains from C in
-// ascending k.
+// column of the lookahead, on the critical path): 64 x 64 tiles
+// (lu::gemm_tile64), so twice the CTAs of the wide kernel for the same rows.
 constexpr int NT = 64;
 __global__ void __launch_bounds__(256) k_gemm_simt_narrow(float *AF, int64_t ldf, int n, int j, int cb, int ce) {
-    __shared__ __align__(16) float As[NB][NT + 4];   // As[k][i] = L21[i][k]
-    __shared__ __align__(16) float Bs[NB][NT + 4];   // Bs[k][c] = U12[k][c]
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    const int i0 = j + NB + blockIdx.x * NT;
-    {
-        // all eight 16-byte loads of a thread in flight before the stores; for L21 the
-        // row runs fastest over the lanes so that the transposed stores hit 32 banks
-        constexpr int R = NT * NB / 4 / 256;
-        float4 va[R], vb[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int e = t + q * 256, ra = e % NT, ka = (e / NT) * 4, i = i0 + ra;
-            const int rb = e >> 4, cq = (e & 15) * 4, c = cb + cq;
-            va[q] = (i < n) ? *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + ka)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-            vb[q] = (c < ce) ? *reinterpret_cast<const float4 *>(AF + (int64_t)(j + rb) * ldf + c)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int e = t + q * 256, ra = e % NT, ka = (e / NT) * 4, rb = e >> 4, cq = (e & 15) * 4;
-            As[ka + 0][ra] = va[q].x; As[ka + 1][ra] = va[q].y; As[ka + 2][ra] = va[q].z; As[ka + 3][ra] = va[q].w;
-            *reinterpret_cast<float4 *>(&Bs[rb][cq]) = vb[q];
-        }
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty * 4 + r, c = cb + tx * 4;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (i < n && c < ce) v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c);
-        acc[r][0] = v.x; acc[r][1] = v.y; acc[r][2] = v.z; acc[r][3] = v.w;
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < NB; ++k) {
-        const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
-        const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
-        const float ar[4] = {a.x, a.y, a.z, a.w}, br[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(-ar[r], br[q], acc[r][q]);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty * 4 + r, c = cb + tx * 4;
-        if (i < n && c < ce)
-            *reinterpret_cast<float4 *>(AF + (int64_t)i * ldf + c) = make_float4(acc[r][0], acc[r][1], acc[r][2], acc[r][3]);
-    }
+    pdl_trigger();
+    pdl_wait();
+    __shared__ __align__(16) float As[NB][lu::kLd];
+    __shared__ __align__(16) float Bs[NB][lu::kLd];
+    lu::gemm_tile64(AF, ldf, n, j, cb, ce, j + NB + blockIdx.x * NT, As, Bs);
 }
 
 }  // namespace
@@ -158,23 +114,25 @@ cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int c
     if (m <= 0 || ce <= cb) return cudaSuccess;
     const int tiles = ((m + BM - 1) / BM) * ((ce - cb + BN - 1) / BN);
     count_launch();
-    if (max_ctas <= 0 && ce - cb <= NT) {
-        k_gemm_simt_narrow<<<(m + NT - 1) / NT, 256, 0, s>>>(AF, ldf, n, j, cb, ce);
-        return cudaGetLastError();
-    }
-    if (max_ctas <= 0) {
-        k_gemm_simt<<<tiles, 256, 0, s>>>(AF, ldf, n, j, cb, ce);
-        return cudaGetLastError();
-    }
     cudaLaunchConfig_t cfg = {};
     cfg.blockDim = dim3(256, 1, 1);
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
+    cfg.attrs = attr;
+    if (max_ctas <= 0 && ce - cb <= NT) {
+        cfg.gridDim = dim3((m + NT - 1) / NT, 1, 1);
+        cfg.numAttrs = set_pdl(&attr[0]);
+        return cudaLaunchKernelEx(&cfg, k_gemm_simt_narrow, AF, ldf, n, j, cb, ce);
+    }
+    if (max_ctas <= 0) {
+        cfg.gridDim = dim3(tiles, 1, 1);
+        cfg.numAttrs = set_pdl(&attr[0]);
+        return cudaLaunchKernelEx(&cfg, k_gemm_simt, AF, ldf, n, j, cb, ce);
+    }
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = kShareCluster;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
     cfg.numAttrs = 1;
     static int max_clusters = -1;
     if (max_clusters < 0) {
@@ -182,6 +140,7 @@ cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int c
         if (cudaOccupancyMaxActiveClusters(&max_clusters, k_gemm_simt, &cfg) != cudaSuccess) max_clusters = 0;
         (void)cudaGetLastError();
     }
+    cfg.numAttrs = 1 + set_pdl(&attr[1]);
     int clusters = max_clusters - 2;
     if (clusters < 1) clusters = 1;
     const int need = (tiles + kShareCluster - 1) / kShareCluster;

@@ -15,6 +15,7 @@
 #include <cuda_fp16.h>
 
 #include "ir_internal.cuh"
+#include "lu_tiles.cuh"
 
 namespace ir {
 namespace {
@@ -104,18 +105,7 @@ __device__ __forceinline__ bool mbar_try_wait_cluster(unsigned addr, unsigned pa
     return ok != 0;
 }
 
-__device__ __forceinline__ float round_tf(float v, ir_dtype tf) {
-    switch (tf) {
-    case IR_TF32: {
-        uint32_t u;
-        asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u) : "f"(v));
-        return __uint_as_float(u);
-    }
-    case IR_BF16: return __bfloat162float(__float2bfloat16_rn(v));
-    case IR_F16: return __half2float(__float2half_rn(v));
-    default: return v;
-    }
-}
+using lu::round_tf;
 
 // Store values 4q .. 4q + 3 of one operand row (rounded to TF) into Aop/Bop.
 __device__ __forceinline__ void store_op_chunk(void *op, int64_t row, int q, float4 v, ir_dtype tf) {
@@ -161,6 +151,8 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char panel_smem[];
     PanelSmem &sm = *reinterpret_cast<PanelSmem *>(panel_smem);
     float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [RPC][LS]
@@ -390,6 +382,8 @@ __global__ void __launch_bounds__(T, 1)
 constexpr int kLaswpT = 64;   // 2*NB*kLaswpT floats of staging stay under 48 KB
 __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b,
                                                   const int32_t *swap_list) {
+    pdl_trigger();
+    pdl_wait();
     __shared__ int sd[2 * NB], ss[2 * NB];
     __shared__ float vals[2 * NB][kLaswpT];
     const int cnt = swap_list[0];
@@ -406,87 +400,15 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int c
     for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
 }
 
-// U12 = L11^{-1} A12 for the block row j..j+NB and the columns [cb, ce).  The
-// solve is a 63-step dependency chain per column, so it is spread thin for
-// latency: four threads per column, each holding 16 rows; column-oriented:
-// for m ascending the owner of row m broadcasts the final u_m (shuffle) and
-// the rows below take fmaf(-l_km, u_m, u_k), so every entry is the fmaf chain
-// over m < k in ascending order, as in the unblocked LU.  For tensor-core
-// updates the rounded values rTF(u_mc) are also written to Bop (row c).
-constexpr int kNarrowCols = 64;   // columns per CTA (4 threads each)
+// U12 = L11^{-1} A12 for the block row j..j+NB and the columns [cb, ce): one
+// CTA of 256 threads per 64 columns (lu::trsm64).
+constexpr int kNarrowCols = 64;
 __global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
                                                      void *Bop) {
-    __shared__ __align__(16) float Lt[NB][NB + 4];    // Lt[m][k] = L11[k][m]
-    {
-        // all loads in flight before the (transposing) stores: row k, columns 4 m4 .. 4 m4 + 3;
-        // k runs fastest over the lanes so that the transposed stores hit 32 banks
-        float4 v[NB * NB / 4 / (4 * kNarrowCols)];
-#pragma unroll
-        for (int i = 0; i < NB * NB / 4 / (4 * kNarrowCols); ++i) {
-            const int e = threadIdx.x + i * 4 * kNarrowCols, k = e % NB, m4 = e / NB;
-            v[i] = *reinterpret_cast<const float4 *>(AF + (int64_t)(j + k) * ldf + j + 4 * m4);
-        }
-#pragma unroll
-        for (int i = 0; i < NB * NB / 4 / (4 * kNarrowCols); ++i) {
-            const int e = threadIdx.x + i * 4 * kNarrowCols, k = e % NB, m4 = e / NB;
-            Lt[4 * m4 + 0][k] = v[i].x;
-            Lt[4 * m4 + 1][k] = v[i].y;
-            Lt[4 * m4 + 2][k] = v[i].z;
-            Lt[4 * m4 + 3][k] = v[i].w;
-        }
-    }
-    __syncthreads();
-    const int t = threadIdx.x, lane = t & 31, q = t & 3;
-    const int c = cb + blockIdx.x * kNarrowCols + (t >> 2);
-    const bool on = c < ce;
-    float u[16];
-#pragma unroll
-    for (int r = 0; r < 16; ++r) u[r] = on ? AF[(int64_t)(j + q * 16 + r) * ldf + c] : 0.f;
-#pragma unroll
-    for (int m = 0; m < NB - 1; ++m) {
-        const float um = __shfl_sync(0xffffffffu, u[m % 16], (lane & ~3) | (m / 16));
-        const float4 *l4 = reinterpret_cast<const float4 *>(&Lt[m][q * 16]);
-#pragma unroll
-        for (int r4 = 0; r4 < 4; ++r4) {
-            const float4 l = l4[r4];
-            const int k = q * 16 + 4 * r4;
-            if (k + 0 > m) u[4 * r4 + 0] = fmaf(-l.x, um, u[4 * r4 + 0]);
-            if (k + 1 > m) u[4 * r4 + 1] = fmaf(-l.y, um, u[4 * r4 + 1]);
-            if (k + 2 > m) u[4 * r4 + 2] = fmaf(-l.z, um, u[4 * r4 + 2]);
-            if (k + 3 > m) u[4 * r4 + 3] = fmaf(-l.w, um, u[4 * r4 + 3]);
-        }
-    }
-    if (!on) return;
-#pragma unroll
-    for (int r = 0; r < 16; ++r)
-        if (q * 16 + r > 0) AF[(int64_t)(j + q * 16 + r) * ldf + c] = u[r];
-    if (Bop == nullptr) return;
-    const int64_t row = c - (j + NB);
-    if (tf == IR_TF32) {
-        float4 *dst = reinterpret_cast<float4 *>(static_cast<float *>(Bop) + row * NB + q * 16);
-#pragma unroll
-        for (int r = 0; r < 16; r += 4)
-            dst[r / 4] = make_float4(round_tf(u[r], tf), round_tf(u[r + 1], tf), round_tf(u[r + 2], tf),
-                                     round_tf(u[r + 3], tf));
-    } else if (tf == IR_BF16) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__nv_bfloat16 *>(Bop) + row * NB + q * 16);
-#pragma unroll
-        for (int r = 0; r < 16; r += 8) {
-            __nv_bfloat162 p2[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) p2[h] = __floats2bfloat162_rn(u[r + 2 * h], u[r + 2 * h + 1]);
-            dst[r / 8] = *reinterpret_cast<uint4 *>(p2);
-        }
-    } else if (tf == IR_F16) {
-        uint4 *dst = reinterpret_cast<uint4 *>(static_cast<__half *>(Bop) + row * NB + q * 16);
-#pragma unroll
-        for (int r = 0; r < 16; r += 8) {
-            __half2 p2[4];
-#pragma unroll
-            for (int h = 0; h < 4; ++h) p2[h] = __floats2half2_rn(u[r + 2 * h], u[r + 2 * h + 1]);
-            dst[r / 8] = *reinterpret_cast<uint4 *>(p2);
-        }
-    }
+    pdl_trigger();
+    pdl_wait();
+    __shared__ __align__(16) float Lt[NB][lu::kLd];
+    lu::trsm64(AF, ldf, cb + blockIdx.x * kNarrowCols, ce, j, tf, Bop, Lt);
 }
 
 __global__ void k_iota(int n, int32_t *perm) {
@@ -514,13 +436,13 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
     cfg.blockDim = dim3(T, 1, 1);
     cfg.dynamicSmemBytes = kPanelDynSmem;
     cfg.stream = s;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 1 + set_pdl(&attr[1]);
     int has_trailing = (j + NB < n) ? 1 : 0;
     count_launch();
     return cudaLaunchKernelEx(&cfg, k_panel, AF, ldf, n, j, nbp, ipiv, perm, swap_list, dev, tf, Aop,
@@ -532,8 +454,14 @@ cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int 
     const int ncols = (c1a - c0a) + (c1b - c0b);
     if (ncols <= 0) return cudaSuccess;
     count_launch();
-    k_laswp<<<(ncols + kLaswpT - 1) / kLaswpT, kLaswpT, 0, s>>>(AF, ldf, c0a, c1a, c0b, c1b, swap_list);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ncols + kLaswpT - 1) / kLaswpT, 1, 1);
+    cfg.blockDim = dim3(kLaswpT, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = set_pdl(&attr[0]);
+    return cudaLaunchKernelEx(&cfg, k_laswp, AF, ldf, c0a, c1a, c0b, c1b, swap_list);
 }
 
 // U12 for the columns [cb, ce) of the block row j..j+NB.
@@ -541,9 +469,14 @@ cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype 
     const int ncols = ce - cb;
     if (ncols <= 0) return cudaSuccess;
     count_launch();
-    k_trsm_narrow<<<(ncols + kNarrowCols - 1) / kNarrowCols, 4 * kNarrowCols, 0, s>>>(
-        AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ncols + kNarrowCols - 1) / kNarrowCols, 1, 1);
+    cfg.blockDim = dim3(4 * kNarrowCols, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = set_pdl(&attr[0]);
+    return cudaLaunchKernelEx(&cfg, k_trsm_narrow, AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
 }
 
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s) {
