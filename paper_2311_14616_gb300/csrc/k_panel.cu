@@ -57,54 +57,6 @@ static_assert(offsetof(PanelSmem, stage) % 16 == 0 && offsetof(PanelSmem, recv) 
 constexpr int LS = NB + 1;
 constexpr size_t kPanelDynSmem = sizeof(PanelSmem) + sizeof(float) * (size_t)RPC * LS + sizeof(float) * NB * NB + 16;
 
-__device__ __forceinline__ unsigned cluster_rank() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ unsigned cluster_size() {
-    unsigned r;
-    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ void cluster_sync_all() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
-                     : "memory");
-}
-__device__ __forceinline__ unsigned map_cta(unsigned local_addr, unsigned rank) {
-    unsigned r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(local_addr), "r"(rank));
-    return r;
-}
-
-// 16-byte store into another CTA's shared memory, counted (complete_tx) on that
-// CTA's mbarrier; the receiver's acquire of the mbarrier phase makes it visible.
-__device__ __forceinline__ void st_async_v4(unsigned rdst, float4 v, unsigned rbar) {
-    asm volatile("st.async.shared::cluster.mbarrier::complete_tx::bytes.v4.b32 [%0], {%1, %2, %3, %4}, [%5];" ::"r"(rdst),
-                 "r"(__float_as_uint(v.x)), "r"(__float_as_uint(v.y)), "r"(__float_as_uint(v.z)),
-                 "r"(__float_as_uint(v.w)), "r"(rbar)
-                 : "memory");
-}
-__device__ __forceinline__ void mbar_init_p(unsigned addr, unsigned count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(addr), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_arrive(unsigned addr, unsigned bytes) {
-    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(addr),
-                 "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait_cluster(unsigned addr, unsigned parity) {
-    unsigned ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(addr), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
 using lu::round_tf;
 
 // Store values 4q .. 4q + 3 of one operand row (rounded to TF) into Aop/Bop.

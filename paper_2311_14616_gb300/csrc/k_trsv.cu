@@ -519,6 +519,430 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
 
 constexpr size_t kSolveSmem = sizeof(float) * (B * (B + 1) + 2 * B);
 
+// ---- the solve pair in one thread-block cluster ------------------------------
+// For N <= 16 * 2 * B: CTA c of a cluster of C = min(16, nblk) CTAs owns the
+// blocks c and c + C.  A finished block of y (lower solve) or z (upper solve)
+// is pushed to every CTA of the cluster with st.async (32 chunks of 16 bytes
+// per destination, one thread each), counted on that block's mbarrier in the
+// receiving CTA, so a block step costs one on-chip transfer instead of a round
+// trip through global memory, and y never leaves the cluster.  The 128 x 128
+// factor tiles a CTA applies are streamed by TMA (one cp.async.bulk.tensor per
+// tile) through a two-deep ring in shared memory, in the order the CTA
+// applies them (lower: block step ascending, own blocks ascending; upper:
+// descending), so two tiles are always in flight while the CTA waits.  For
+// each of its blocks a CTA applies the tiles in the same order, with the same
+// per-lane products, compensated sums and diagonal solves as k_trsv_lower /
+// k_trsv_upper, so the results are the same bits.
+constexpr int kClCtas = 16;
+constexpr int kClOwn = 2;
+constexpr int kClMaxBlk = kClCtas * kClOwn;
+constexpr unsigned kTileBytes = B * B * 4;
+struct ClSmem {
+    alignas(16) float ybuf[kClMaxBlk][B];          // every block of y, as pushed
+    alignas(16) float zbuf[kClMaxBlk][B];          // every block of z
+    alignas(16) float rhs[kClOwn][B];              // this CTA's right-hand sides (lower)
+    alignas(16) float sv[B];                       // the block being finished
+    alignas(8) unsigned long long bar[2][kClMaxBlk];
+    alignas(8) unsigned long long full[2];         // the tile ring: copy landed
+    alignas(8) unsigned long long dsbar;           // the diagonal inverse copy landed
+    int abort;
+};
+// ring (2 tiles, 128-byte aligned) | ClSmem | Ds
+constexpr size_t kClSmem = 128 + 2 * (size_t)kTileBytes + sizeof(ClSmem) + sizeof(float) * B * (B + 1);
+
+__device__ __forceinline__ void cl_tma_tile(unsigned dst, const CUtensorMap *map, int bj, int bi, unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(bj * B), "r"(bi * B), "r"(mbar)
+        : "memory");
+}
+
+// Wait for the phase `parity` of barrier `bar`: one thread spins, bounded by
+// the launch's deadline, then the CTA meets at a barrier.  A wait that gives up
+// flags the solve as abandoned and returns anyway, so every warp keeps the same
+// control flow (after the deadline every wait returns at once; the results are
+// then garbage and the timeout is reported).
+__device__ __forceinline__ void cta_wait(ClSmem &sm, unsigned bar, unsigned parity, unsigned long long deadline,
+                                         int *timeout) {
+    if (threadIdx.x == 0) {
+        while (!mbar_try_wait_cluster(bar, parity)) {
+            if (globaltimer() > deadline) {
+                if (!sm.abort) {
+                    sm.abort = 1;
+                    atomicExch(timeout, 1);
+                }
+                break;
+            }
+        }
+    }
+    __syncthreads();
+}
+
+// Copy a block's diagonal inverse (B x B binary32, contiguous) into Ds with one
+// bulk asynchronous copy counted on sm.dsbar (issued by thread 0).
+__device__ __forceinline__ void ds_copy(ClSmem &sm, float *Ds, const float *src) {
+    if (threadIdx.x == 0) {
+        const unsigned bar = smem_u32(&sm.dsbar);
+        mbar_expect_arrive(bar, B * B * 4);
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                         smem_u32(Ds)),
+                     "l"(src), "r"(B * B * 4), "r"(bar)
+                     : "memory");
+    }
+}
+
+// Push sv (B values) into buf[bj] of every CTA of the cluster.
+__device__ __forceinline__ void cl_push(ClSmem &sm, float (*buf)[B], int ph, int bj, unsigned C) {
+    const int t = threadIdx.x;
+    if (t < 32 * (int)C) {
+        const int dst = t >> 5, ch = t & 31;
+        const float4 v = reinterpret_cast<const float4 *>(sm.sv)[ch];
+        st_async_v4(map_cta(smem_u32(&buf[bj][4 * ch]), (unsigned)dst), v,
+                    map_cta(smem_u32(&sm.bar[ph][bj]), (unsigned)dst));
+    }
+}
+
+// (p, pl) += tile . y, the tile in shared memory (row-major B x B): the
+// per-lane products of offdiag, compensated.
+__device__ __forceinline__ void cl_apply(const float *tile, const float *yb, int lane, int warp, float (&p)[8],
+                                         float (&pl)[8]) {
+    float y[CPL];
+#pragma unroll
+    for (int c = 0; c < CPL; ++c) y[c] = yb[lane + 32 * c];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const float *row = tile + (warp * 8 + q) * B + lane;
+        float tp = __fmul_rn(row[0], y[0]);
+#pragma unroll
+        for (int c = 1; c < CPL; ++c) tp = fmaf(row[32 * c], y[c], tp);
+        acc_pair(p[q], pl[q], tp, 0.f);
+    }
+}
+
+// sv <- rhs - sum (compensated), then the diagonal block (inverse or substitution).
+template <bool LOWER>
+__device__ __forceinline__ void cl_finish(ClSmem &sm, const float *Ds, bool subst, const float (&p)[8],
+                                          const float (&pl)[8]) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    float pp[8], ppl[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        pp[q] = p[q];
+        ppl[q] = pl[q];
+    }
+    __syncthreads();                     // sv holds the right-hand side
+    {
+        float sh, sl;
+        reduce8_pair(pp, ppl, lane, sh, sl);
+        if ((lane & 3) == 0) {
+            const int il = warp * 8 + reduce8_row(lane);
+            sm.sv[il] = sub_pair(sm.sv[il], sh, sl);
+        }
+    }
+    __syncthreads();
+    if (subst) {
+        if (warp == 0) diag_subst<LOWER>(Ds, sm.sv, lane);
+    } else {
+        const float y = diag_apply(Ds, sm.sv, warp, lane);
+        __syncthreads();
+        if ((lane & 3) == 0) sm.sv[warp * 8 + reduce8_row(lane)] = y;
+    }
+    __syncthreads();
+}
+
+// Outputs of a finished z block (sv): mode 0 x += (rho s) z with the maxima of
+// |d| and |x|; mode 1 dout = z; mode 2 x = (rho s) z.
+__device__ __forceinline__ void cl_out(const float *sv, int r0, int n, int mode, double scale, double *x,
+                                       float *dout, double &dmax, double &xmax) {
+    const int t = threadIdx.x;
+    const int i = r0 + t;
+    if (t >= B || i >= n) return;
+    const float zv = sv[t];
+    if (mode == 1) {
+        dout[i] = zv;
+        return;
+    }
+    const double d = scale * (double)zv;
+    if (mode == 0) {
+        const double xn = x[i] + d;
+        x[i] = xn;
+        dmax = fmax(dmax, fabs(d));
+        xmax = fmax(xmax, fabs(xn));
+    } else {
+        x[i] = d;
+    }
+}
+
+#define OWN(o) ((int)c + (o) * (int)C)
+// The tile sequence of a CTA: phase 0 (lower) tiles (OWN(o), bj) for bj
+// ascending and o ascending with OWN(o) > bj; phase 1 (upper) tiles for bj
+// descending and o descending with OWN(o) < bj; phase 2: none left.
+struct TileSeq {
+    int ph, o, bj;
+};
+__device__ __forceinline__ void seq_first_upper(TileSeq &q, int c, int C, int nown, int nblk) {
+    q.ph = 1;
+    q.bj = nblk - 1;
+    q.o = (nown > 1 && OWN(1) < q.bj) ? 1 : ((OWN(0) < q.bj) ? 0 : -1);
+    if (q.o < 0) q.ph = 2;
+}
+__device__ __forceinline__ void seq_first(TileSeq &q, int c, int C, int nown, int nblk) {
+    q.ph = 0;
+    q.bj = 0;
+    q.o = (OWN(0) > 0) ? 0 : ((nown > 1 && OWN(1) > 0) ? 1 : -1);
+    if (q.o < 0) seq_first_upper(q, c, C, nown, nblk);
+}
+__device__ __forceinline__ void seq_next(TileSeq &q, int c, int C, int nown, int nblk) {
+    if (q.ph == 0) {
+        if (q.o == 0 && nown > 1 && OWN(1) > q.bj) {
+            q.o = 1;
+            return;
+        }
+        q.bj += 1;
+        q.o = (OWN(0) > q.bj) ? 0 : ((nown > 1 && OWN(1) > q.bj) ? 1 : -1);
+        if (q.o < 0) seq_first_upper(q, c, C, nown, nblk);
+    } else if (q.ph == 1) {
+        if (q.o == 1 && OWN(0) < q.bj) {
+            q.o = 0;
+            return;
+        }
+        q.bj -= 1;
+        q.o = (nown > 1 && OWN(1) < q.bj) ? 1 : ((OWN(0) < q.bj) ? 0 : -1);
+        if (q.o < 0) q.ph = 2;
+    }
+}
+
+__global__ void __launch_bounds__(TT, 1) k_trsv_cluster(const __grid_constant__ CUtensorMap tmAF, int64_t ldf, int n,
+                                                        int nblk, const float *AF, const float *Linv,
+                                                        const float *Uinv, const int32_t *blk_subst,
+                                                        const int32_t *perm, const double *r, const float *vin,
+                                                        int mode, const unsigned long long *rho_bits,
+                                                        const int *skip, double *x, float *dout, DevScalars *dev) {
+    if (skip && *skip) return;
+    extern __shared__ __align__(16) unsigned char cl_smem[];
+    const unsigned s0 = smem_u32(cl_smem);
+    unsigned char *base = cl_smem + (((s0 + 127u) & ~127u) - s0);
+    float *ring = reinterpret_cast<float *>(base);                                  // [2][B * B]
+    ClSmem &sm = *reinterpret_cast<ClSmem *>(base + 2 * (size_t)kTileBytes);
+    float *Ds = reinterpret_cast<float *>(base + 2 * (size_t)kTileBytes + sizeof(ClSmem));
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int C = (int)cluster_size(), c = (int)cluster_rank();
+    const int nown = (OWN(1) < nblk) ? 2 : 1;
+    if (t == 0) {
+        sm.abort = 0;
+        for (int b = 0; b < nblk; ++b) {
+            mbar_init_p(smem_u32(&sm.bar[0][b]), 1);
+            mbar_init_p(smem_u32(&sm.bar[1][b]), 1);
+        }
+        mbar_init_p(smem_u32(&sm.full[0]), 1);
+        mbar_init_p(smem_u32(&sm.full[1]), 1);
+        mbar_init_p(smem_u32(&sm.dsbar), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int b = 0; b < nblk; ++b) {
+            mbar_expect_arrive(smem_u32(&sm.bar[0][b]), B * 4);
+            mbar_expect_arrive(smem_u32(&sm.bar[1][b]), B * 4);
+        }
+    }
+    // right-hand sides of this CTA's blocks: fl32(r[perm_i] / ||r||) (mode 0, 2) or vin[perm_i]
+    if (t < B) {
+        const double rn = (mode != 1) ? __longlong_as_double((long long)*rho_bits) : 1.0;
+#pragma unroll
+        for (int o = 0; o < kClOwn; ++o) {
+            float v = 0.f;
+            const int i = OWN(o) * B + t;
+            if (o < nown && i < n) {
+                const int src = perm[i];
+                v = (mode != 1) ? ((rn == 0.0) ? 0.f : __double2float_rn(r[src] / rn)) : vin[src];
+            }
+            sm.rhs[o][t] = v;
+        }
+    }
+    cluster_sync_all();     // every barrier of the cluster is armed before anything is pushed
+    const unsigned long long deadline = globaltimer() + kWaitLimitNs;
+    // the producer (thread 0) keeps two tiles of the sequence in flight
+    TileSeq pq;
+    int issued = 0, used = 0;
+    seq_first(pq, c, C, nown, nblk);
+    if (t == 0) {
+        for (int k = 0; k < 2 && pq.ph < 2; ++k) {
+            const unsigned fb = smem_u32(&sm.full[k]);
+            mbar_expect_arrive(fb, kTileBytes);
+            cl_tma_tile(smem_u32(ring + (size_t)k * B * B), &tmAF, pq.bj, OWN(pq.o), fb);
+            seq_next(pq, c, C, nown, nblk);
+            ++issued;
+        }
+    }
+    // the next tile of the sequence, in shared memory
+    auto tile_ready = [&]() -> const float * {
+        const int k = used;
+        cta_wait(sm, smem_u32(&sm.full[k & 1]), (unsigned)((k >> 1) & 1), deadline, &dev->timeout);
+        return ring + (size_t)(k & 1) * B * B;
+    };
+    // the tile is consumed: its buffer takes the tile two ahead
+    auto tile_done = [&]() {
+        __syncthreads();
+        const int k = used;
+        if (t == 0 && pq.ph < 2) {
+            const unsigned fb = smem_u32(&sm.full[k & 1]);
+            mbar_expect_arrive(fb, kTileBytes);
+            cl_tma_tile(smem_u32(ring + (size_t)(k & 1) * B * B), &tmAF, pq.bj, OWN(pq.o), fb);
+            seq_next(pq, c, C, nown, nblk);
+            ++issued;
+        }
+        ++used;
+    };
+    // the diagonal block of block bi in Ds: its inverse by a bulk copy (waited for
+    // in ds_ready), or its transposed triangle for a block solved by substitution
+    int ds_async = 0, ds_k = 0;
+    auto ds_stage = [&](bool lower, int bi) {
+        const bool subst = blk_subst[(lower ? 0 : nblk) + bi] != 0;
+        if (subst) {
+            if (lower)
+                stage_diag<true>(AF, ldf, n, bi * B, nullptr, true, Ds);
+            else
+                stage_diag<false>(AF, ldf, n, bi * B, nullptr, true, Ds);
+            ds_async = 0;
+        } else {
+            ds_copy(sm, Ds, (lower ? Linv : Uinv) + (int64_t)bi * B * B);
+            ds_async = 1;
+        }
+    };
+    auto ds_ready = [&]() {
+        if (ds_async) {
+            cta_wait(sm, smem_u32(&sm.dsbar), (unsigned)(ds_k & 1), deadline, &dev->timeout);
+            ++ds_k;
+            ds_async = 0;
+        }
+    };
+    float p[kClOwn][8], pl[kClOwn][8];
+
+    // ---------------- lower: y = L^{-1} v, blocks ascending ----------------
+#pragma unroll
+    for (int o = 0; o < kClOwn; ++o)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[o][q] = pl[o][q] = 0.f;
+    ds_stage(true, OWN(0));
+    if (OWN(0) == 0) {                      // block 0 has no predecessors
+        if (t < B) sm.sv[t] = sm.rhs[0][t];
+        ds_ready();
+        cl_finish<true>(sm, Ds, blk_subst[0] != 0, p[0], pl[0]);
+        cl_push(sm, sm.ybuf, 0, 0, C);
+        if (nown > 1) {
+            __syncthreads();
+            ds_stage(true, OWN(1));
+        }
+    }
+    for (int bj = 0; bj + 1 < nblk; ++bj) {
+        if (OWN(nown - 1) <= bj) break;               // nothing of this CTA below bj
+        cta_wait(sm, smem_u32(&sm.bar[0][bj]), 0u, deadline, &dev->timeout);
+        const float *yb = sm.ybuf[bj];
+#pragma unroll
+        for (int o = 0; o < kClOwn; ++o) {
+            if (o >= nown || OWN(o) <= bj) continue;
+            const float *tile = tile_ready();
+            cl_apply(tile, yb, lane, warp, p[o], pl[o]);
+            tile_done();
+            if (OWN(o) == bj + 1) {                   // the chain: finish and push
+                if (t < B) sm.sv[t] = sm.rhs[o][t];
+                ds_ready();
+                cl_finish<true>(sm, Ds, blk_subst[OWN(o)] != 0, p[o], pl[o]);
+                cl_push(sm, sm.ybuf, 0, OWN(o), C);
+                if (o + 1 < nown) {
+                    __syncthreads();
+                    ds_stage(true, OWN(o + 1));
+                }
+            }
+        }
+    }
+
+    // ---------------- upper: z = U^{-1} y, blocks descending ----------------
+    const double scale = (mode != 1) ? __longlong_as_double((long long)*rho_bits) * dev->scale : 1.0;
+    double dmax = 0.0, xmax = 0.0;
+    {
+        const int hi = nown - 1;
+#pragma unroll
+        for (int o = 0; o < kClOwn; ++o)
+#pragma unroll
+            for (int q = 0; q < 8; ++q) p[o][q] = pl[o][q] = 0.f;
+        __syncthreads();
+        ds_stage(false, OWN(hi));
+        // the y blocks of this CTA: the lower solve pushed them here too
+        cta_wait(sm, smem_u32(&sm.bar[0][OWN(hi)]), 0u, deadline, &dev->timeout);
+        if (OWN(hi) == nblk - 1) {
+            if (t < B) sm.sv[t] = sm.ybuf[OWN(hi)][t];       // the last block has no successors
+            ds_ready();
+            if (hi == 1)      // (static indices keep the partial sums in registers)
+                cl_finish<false>(sm, Ds, blk_subst[nblk + OWN(1)] != 0, p[1], pl[1]);
+            else
+                cl_finish<false>(sm, Ds, blk_subst[nblk + OWN(0)] != 0, p[0], pl[0]);
+            cl_push(sm, sm.zbuf, 1, OWN(hi), C);
+            cl_out(sm.sv, OWN(hi) * B, n, mode, scale, x, dout, dmax, xmax);
+            if (hi > 0) {
+                __syncthreads();
+                ds_stage(false, OWN(0));
+            }
+        }
+        for (int bj = nblk - 1; bj > 0; --bj) {
+            if (OWN(0) >= bj) break;                 // nothing of this CTA above bj
+            cta_wait(sm, smem_u32(&sm.bar[1][bj]), 0u, deadline, &dev->timeout);
+            const float *zb = sm.zbuf[bj];
+#pragma unroll
+            for (int oo = 0; oo < kClOwn; ++oo) {
+                const int o = kClOwn - 1 - oo;      // the higher block first
+                if (o >= nown || OWN(o) >= bj) continue;
+                const float *tile = tile_ready();
+                cl_apply(tile, zb, lane, warp, p[o], pl[o]);
+                tile_done();
+                if (OWN(o) == bj - 1) {
+                    cta_wait(sm, smem_u32(&sm.bar[0][OWN(o)]), 0u, deadline, &dev->timeout);
+                    if (t < B) sm.sv[t] = sm.ybuf[OWN(o)][t];
+                    ds_ready();
+                    cl_finish<false>(sm, Ds, blk_subst[nblk + OWN(o)] != 0, p[o], pl[o]);
+                    cl_push(sm, sm.zbuf, 1, OWN(o), C);
+                    cl_out(sm.sv, OWN(o) * B, n, mode, scale, x, dout, dmax, xmax);
+                    if (o > 0) {
+                        __syncthreads();
+                        ds_stage(false, OWN(o - 1));
+                    }
+                }
+            }
+        }
+    }
+    if (mode == 0 && t < B) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+            xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+        }
+        if (lane == 0) {
+            atomic_max_nonneg(&dev->dnorm_bits, dmax);
+            atomic_max_nonneg(&dev->xnorm_bits, xmax);
+        }
+    }
+    // Every push into this CTA and every tile copy it issued has landed
+    // (bounded), then nobody leaves before the others.
+    if (t == 0) {
+        if (ds_async)                            // (only after an abandoned solve)
+            while (!mbar_try_wait_cluster(smem_u32(&sm.dsbar), (unsigned)(ds_k & 1)))
+                if (globaltimer() > deadline + kWaitLimitNs) break;
+        for (int k = used; k < issued; ++k)      // (only after an abandoned solve)
+            while (!mbar_try_wait_cluster(smem_u32(&sm.full[k & 1]), (unsigned)((k >> 1) & 1)))
+                if (globaltimer() > deadline + kWaitLimitNs) break;
+        if (!sm.abort) {
+            for (int b = 0; b < nblk; ++b)
+                for (int ph = 0; ph < 2; ++ph)
+                    while (!mbar_try_wait_cluster(smem_u32(&sm.bar[ph][b]), 0u))
+                        if (globaltimer() > deadline) {
+                            atomicExch(&dev->timeout, 1);
+                            break;
+                        }
+        }
+    }
+    __syncthreads();
+    cluster_sync_all();
+}
+#undef OWN
+
 }  // namespace
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
@@ -534,6 +958,11 @@ cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, fl
     count_launch();
     k_diag_inv<<<dim3(nblk, 2), B, kDiagSmem, s>>>(AF, ldf, n, Linv, Uinv, blk_subst);
     return cudaGetLastError();
+}
+
+static bool cluster_solve_enabled() {
+    const char *e = getenv("IR_NO_CLUSTER_SOLVE");
+    return !(e && e[0] && e[0] != '0');
 }
 
 // ytag/ztag: 2 arrays of nblk*B tagged words (flags buffer).  Tickets are reset here.
@@ -553,11 +982,50 @@ cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *L
         attr = true;
     }
     const int nblk = (n + B - 1) / B;
-    cudaError_t e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
-    if (e != cudaSuccess) return e;
+    cudaError_t e = cudaSuccess;
     const int mode = vin ? 1 : (pw ? 2 : 0);
     if (mode != 2) rho_bits = &dev->rnorm_bits;
     double *xo = (mode == 2) ? pw : x;
+    if (nblk <= kClMaxBlk && cluster_solve_enabled()) {
+        static bool cattr = false;
+        if (!cattr) {
+            e = cudaFuncSetAttribute(k_trsv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute(k_trsv_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            cattr = true;
+        }
+        // the factors as a 2-D tensor (n x n, row stride ldf), 128 x 128 boxes, zero fill past n
+        CUtensorMap tm;
+        TensorMapEncodeFn enc = tensor_map_encoder();
+        if (!enc) return cudaErrorNotSupported;
+        const cuuint64_t dims[2] = {(cuuint64_t)n, (cuuint64_t)n};
+        const cuuint64_t strides[1] = {(cuuint64_t)ldf * 4};
+        const cuuint32_t box[2] = {(cuuint32_t)B, (cuuint32_t)B};
+        const cuuint32_t estr[2] = {1, 1};
+        if (enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float *>(AF), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaErrorInvalidValue;
+        const int C = nblk < kClCtas ? nblk : kClCtas;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C, 1, 1);
+        cfg.blockDim = dim3(TT, 1, 1);
+        cfg.dynamicSmemBytes = kClSmem;
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        count_launch();
+        return cudaLaunchKernelEx(&cfg, k_trsv_cluster, tm, ldf, n, nblk, AF, Linv, Uinv, blk_subst, perm, r, vin,
+                                  mode, rho_bits, skip, xo, dout, dev);
+    }
+    e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
     unsigned long long *ytag = tags, *ztag = tags + (int64_t)nblk * B;
     count_launch();
     k_trsv_lower<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode, rho_bits, skip,

@@ -246,3 +246,43 @@ def test_solve_many_columns_equal_single_solves(ctx):
     assert reps[3].status == "converged" and reps[3].iters == 0
     xr = O.reference_solution(A, B[:, 0])
     assert O.rel_err_inf(X[:, 0], xr) <= O.parity_tol(O.cond_inf(A), O.F64)
+
+
+def test_cluster_solve_pair_is_bitwise_the_two_kernel_pair():
+    """For N <= 4096 the correction solve runs as one thread-block cluster (y and z
+    pushed between CTAs through distributed shared memory, tiles streamed by TMA);
+    it applies the same tiles in the same order with the same arithmetic as the
+    two-kernel pair (selected with IR_NO_CLUSTER_SOLVE=1), so every result is the
+    same bits: raw solves, refinement histories and GMRES-IR corrections."""
+    import os
+    import subprocess
+    import sys
+    code = r'''
+import json, sys, numpy as np
+sys.path.insert(0, ".")
+import irgen
+from paper_2311_14616_gb300 import ir
+from tests.gpu_util import dev_colmajor, dev_vec
+ctx = ir.Context(0)
+out = []
+for n, tf, mk in [(4096, "f32", lambda: irgen.case_green_sine(4096)[:2]), (1, "f32", lambda: irgen.case_gaussian(1, 1)),
+                  (130, "bf16", lambda: irgen.case_green(130, 800.0)), (2049, "f16", lambda: irgen.case_green(2049, 799.0)),
+                  (3000, "tf32", lambda: irgen.case_random(3000, 5))]:
+    A, b = mk()
+    f = ctx.factor(dev_colmajor(A), tf=tf)
+    v = np.random.Generator(np.random.PCG64(n)).standard_normal(n).astype(np.float32)
+    d = f.lu_solve(dev_vec(v)).cpu().numpy()
+    x, rep = f.solve(dev_vec(b))
+    xg, repg = f.solve_gmres(dev_vec(b))
+    out.append([d.tobytes().hex(), x.cpu().numpy().tobytes().hex(), xg.cpu().numpy().tobytes().hex(),
+                rep.rhist, repg.khist])
+print(json.dumps(out))
+'''
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for flag in ("0", "1"):
+        r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600,
+                           env=dict(os.environ, IR_NO_CLUSTER_SOLVE=flag))
+        assert r.returncode == 0, r.stderr[-2000:]
+        res.append(r.stdout.strip().splitlines()[-1])
+    assert res[0] == res[1]
