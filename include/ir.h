@@ -147,9 +147,13 @@ ir_status ir_solve_many(ir_fact *fact, int64_t nrhs, const void *B, int64_t ldb,
                         const ir_term *term, void *stream, ir_report *reps);
 
 /* End-to-end solve from HOST memory: copies A and b to the device, factors,
- * refines, copies x back and releases the device buffers.  A_host: n x n
- * column-major in TW (lda); b_host, x_host: n values in TW.  Synchronous.
- * Host buffers may be pageable; pinned buffers copy faster. */
+ * refines and copies x back.  A_host: n x n column-major in TW (lda); b_host,
+ * x_host: n values in TW.  Synchronous.  Host buffers may be pageable; pinned
+ * buffers copy faster.  The device buffers and the factorization (with its
+ * captured launch graph) are kept by the context for the next call of the
+ * same shape and options, so repeated solves pay only the copies, the
+ * factorization and the refinement; ir_finalize (or a call of another shape)
+ * releases them.  Not for concurrent use of one context from several threads. */
 ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda,
                         const void *b_host, void *x_host, const ir_opts *opts,
                         const ir_term *term, void *stream, ir_report *rep);

@@ -119,6 +119,19 @@ ir_status ensure_partials(ir_ctx *ctx, int64_t n) {
     return IR_OK;
 }
 
+void free_fact(ir_fact *f);
+
+// ir_solve_host's cached buffers and factorization.
+void release_host_cache(ir_ctx *ctx) {
+    if (ctx->host_f) free_fact(ctx->host_f);
+    ctx->host_f = nullptr;
+    cudaFree(ctx->host_dA);
+    cudaFree(ctx->host_db);
+    cudaFree(ctx->host_dx);
+    ctx->host_dA = ctx->host_db = ctx->host_dx = nullptr;
+    ctx->host_n = -1;
+}
+
 void free_fact(ir_fact *f) {
     if (!f) return;
     cudaFree(f->AF);
@@ -624,6 +637,7 @@ ir_status ir_init(int device, ir_ctx **out) {
 
 void ir_finalize(ir_ctx *c) {
     if (!c) return;
+    release_host_cache(c);
     cudaFree(c->partials);
     cudaFree(c->rnorm_tmp);
     delete c;
@@ -1209,33 +1223,49 @@ ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda,
     const size_t es = o.TW == IR_F64 ? 8 : 4;
     cudaStream_t s = (cudaStream_t)stream;
     CK(cudaSetDevice(ctx->device));
-    void *dA = nullptr, *db = nullptr, *dx = nullptr;
-    ir_fact *f = nullptr;
+    const bool same = ctx->host_f && ctx->host_n == n && ctx->host_lda == lda && ctx->host_tw == (int)o.TW &&
+                      ctx->host_tf == (int)o.TF && ctx->host_scale == o.fp16_scale &&
+                      ctx->host_autotune == o.autotune;
+    if (!same) release_host_cache(ctx);
     ir_status st = IR_OK;
+    cudaError_t e = cudaSuccess;
     const int64_t nn = n > 0 ? n : 1;
-    cudaError_t e = cudaMalloc(&dA, (size_t)lda * nn * es);
-    if (e == cudaSuccess) e = cudaMalloc(&db, nn * es);
-    if (e == cudaSuccess) e = cudaMalloc(&dx, nn * es);
-    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(dA, A_host, (size_t)lda * n * es, cudaMemcpyHostToDevice, s);
-    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(db, b_host, n * es, cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) {
-        st = cuda_fail(e, "ir_solve_host upload");
-        goto done;
+    if (!same) {
+        e = cudaMalloc(&ctx->host_dA, (size_t)lda * nn * es);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_db, nn * es);
+        if (e == cudaSuccess) e = cudaMalloc(&ctx->host_dx, nn * es);
+        if (e != cudaSuccess) {
+            release_host_cache(ctx);
+            return cuda_fail(e, "ir_solve_host allocation");
+        }
     }
-    st = ir_factor(ctx, n, dA, lda, &o, stream, &f);
-    if (st != IR_OK) goto done;
-    st = ir_solve(f, db, dx, term, stream, rep);
-    if (st != IR_OK) goto done;
+    if (n > 0) e = cudaMemcpyAsync(ctx->host_dA, A_host, (size_t)lda * n * es, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess && n > 0) e = cudaMemcpyAsync(ctx->host_db, b_host, n * es, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ir_solve_host upload");
+    if (same) {
+        st = ir_refactor(ctx->host_f, ctx->host_dA, lda, stream);
+    } else {
+        st = ir_factor(ctx, n, ctx->host_dA, lda, &o, stream, &ctx->host_f);
+        if (st == IR_OK) {
+            ctx->host_n = n;
+            ctx->host_lda = lda;
+            ctx->host_tw = (int)o.TW;
+            ctx->host_tf = (int)o.TF;
+            ctx->host_scale = o.fp16_scale;
+            ctx->host_autotune = o.autotune;
+        }
+    }
+    if (st != IR_OK) {
+        release_host_cache(ctx);
+        return st;
+    }
+    st = ir_solve(ctx->host_f, ctx->host_db, ctx->host_dx, term, stream, rep);
+    if (st != IR_OK) return st;
     if (n > 0) {
-        e = cudaMemcpyAsync(x_host, dx, n * es, cudaMemcpyDeviceToHost, s);
+        e = cudaMemcpyAsync(x_host, ctx->host_dx, n * es, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) st = cuda_fail(e, "ir_solve_host download");
     }
-done:
-    if (f) ir_fact_destroy(f);
-    cudaFree(dA);
-    cudaFree(db);
-    cudaFree(dx);
     return st;
 }
 

@@ -82,6 +82,12 @@ struct ir_ctx {
     int sms;
     ir_tuned tuned[16];      // ring of tuned schedules
     int ntuned;
+    // ir_solve_host's device buffers and factorization, kept for the next
+    // call of the same shape (released by ir_finalize or a different shape)
+    struct ir_fact *host_f;
+    void *host_dA, *host_db, *host_dx;
+    int64_t host_n, host_lda;
+    int host_tw, host_tf, host_scale, host_autotune;
     double *partials;        // residual split-K partial sums
     int64_t partials_cap;    // capacity in doubles
     double *rnorm_tmp;       // scratch scalar for ir_residual

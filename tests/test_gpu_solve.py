@@ -155,6 +155,17 @@ def test_solve_host_end_to_end(ctx):
     xr = O.reference_solution(A, b)
     assert not xh.is_cuda
     assert O.rel_err_inf(xh.numpy(), xr) <= O.parity_tol(O.cond_inf(A), O.F64)
+    # the context keeps the buffers and the factorization for the same shape: a
+    # second call with another matrix of that shape refactors into them, and a
+    # call of another shape replaces them -- each result is its own system's
+    A2, b2 = irgen.case_gaussian(300, 8)
+    xh2, _ = ctx.solve_host(torch.from_numpy(A2), torch.from_numpy(b2), tf="f32")
+    assert O.rel_err_inf(xh2.numpy(), O.reference_solution(A2, b2)) <= 1e-12
+    xh1, _ = ctx.solve_host(torch.from_numpy(A), torch.from_numpy(b), tf="f32")
+    np.testing.assert_array_equal(xh1.numpy(), xh.numpy())
+    A3, b3 = irgen.case_gaussian(77, 9)
+    xh3, _ = ctx.solve_host(torch.from_numpy(A3), torch.from_numpy(b3), tf="f16")
+    assert O.rel_err_inf(xh3.numpy(), O.reference_solution(A3, b3)) <= 1e-12
 
 
 def test_lu_solve_backward_stable_with_ill_conditioned_diagonal_blocks(ctx):
