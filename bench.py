@@ -583,7 +583,8 @@ def main():
             t_e.append((time.perf_counter() - t0) * 1e3)
         e2e = {"value": max_over_ranks(statistics.mean(t_e), ws) / ws, "unit": "ms",
                "h2d_bytes_per_step": int(n * n * 8 + n * 8), "d2h_bytes_per_step": int(n * 8),
-               "api": "ir_solve_host (pinned host A, b; allocation, copies, factor, refine, copy back)"}
+               "api": "ir_solve_host (pinned host A, b: copies in, factor, refine, copy back; the context keeps "
+                      "its device buffers and factorization across calls of the same shape)"}
 
     # --- CPU oracle on the host cores (rank 0, one GPU only)
     cpu = None
