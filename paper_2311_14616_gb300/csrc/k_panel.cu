@@ -289,11 +289,11 @@ __global__ void __launch_bounds__(T, 1)
         swap_list[2 + 2 * e] = j + home1;
         porg1 = perm[j + home1];
     }
+    cluster_sync_all();   // every perm read of the cluster is done; piv_log is complete
     if (crank == 0) {
         for (int k = t; k < nbp; k += T) ipiv[j + k] = sm.piv_log[k];
         if (t == 0 && sm.zero_piv) atomicMin(&dev->info, sm.zero_piv);
     }
-    cluster_sync_all();   // every perm read of the cluster is done
     if (moved0) perm[j + pos0] = porg0;
     if (moved1) perm[j + pos1] = porg1;
     // Final rows, written a row (256 contiguous bytes) per half warp: the
