@@ -85,7 +85,7 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 
 // One cluster factors the panel AF[j:n, j:j+nbp].  Thread t of CTA c keeps
 // rows j + c*RPC + t and j + c*RPC + T + t for the whole panel in rotating
-// register windows: at step k, a[i] holds column j+k+i (zero past the panel),
+// register windows: at step k, a[i] holds column j+k+i for i < nbp - k (live),
 // so the current column is always a[0] and the update a[i] <- fmaf(-l,
 // u[i+1], a[i+1]) also shifts the window.  Per column k: thread, then warp
 // candidate (largest |a|, ties to the lowest current position: redux.sync)
@@ -256,13 +256,15 @@ __global__ void __launch_bounds__(T, 1)
             if (piv != 0.f) l1 = (fabsf(piv) >= FLT_MIN) ? l1 * r : l1 / piv;
             Ls[(T + t) * LS + k] = l1;
         }
-        // No branches on the live width: past it, the windows and the staged
-        // record hold zeros (a value shifts left only from inside the live
-        // width), so the extra fmas change nothing that is used, and the 16
-        // loads of the pivot row can all be issued ahead of the fmas.
+        // After the update only window entries i < 63 - k are live, so the
+        // update stops at the first 16-column chunk that holds none of them
+        // (one uniform branch per chunk; inside a chunk the 4 loads of the
+        // pivot row are issued ahead of the fmas).  Entries past the live width
+        // are dead: they may hold stale values and are never read.
         const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
+            if (q % 4 == 0 && q > 0 && 4 * q >= NB - 1 - k) break;
             const float4 w = us[q];
             a0[4 * q + 0] = fmaf(-l0, w.x, a0[4 * q + 1]);
             a0[4 * q + 1] = fmaf(-l0, w.y, a0[4 * q + 2]);
