@@ -150,21 +150,31 @@ __global__ void __launch_bounds__(T, 1)
     const unsigned recv_addr = smem_u32(&sm.recv[0][0][0]);
     const unsigned bar_addr = smem_u32(&sm.recv_bar[0]);
 
-#pragma unroll 1
-    for (int k = 0; k < nbp; ++k) {
-        const int buf = k & 1;
-        // 1. candidate of the thread (its two rows), then of the warp: largest
-        //    |a_ik| over rows that are not pivot rows yet, ties to the lowest
-        //    current position; staged as a record
+    // 1. candidate of the thread (its two rows), then of the warp: largest
+    //    |a_ik| over rows that are not pivot rows yet, ties to the lowest
+    //    current position.  For step k + 1 it is formed inside step k's
+    //    update, right after the new column k + 1, so that the reductions
+    //    overlap the rest of the update.
+    bool use1, tc;
+    int tpos, mpos;
+    unsigned kmax;
+    auto candidate = [&]() {
         const bool c0 = valid0 && kp0 == nbp, c1 = valid1 && kp1 == nbp;
         const unsigned k0 = c0 ? __float_as_uint(fabsf(a0[0])) : 0u;
         const unsigned k1 = c1 ? __float_as_uint(fabsf(a1[0])) : 0u;
-        const bool use1 = c1 && (!c0 || k1 > k0 || (k1 == k0 && pos1 < pos0));
-        const bool tc = c0 || c1;
+        use1 = c1 && (!c0 || k1 > k0 || (k1 == k0 && pos1 < pos0));
+        tc = c0 || c1;
         const unsigned key = use1 ? k1 : k0;
-        const int tpos = use1 ? pos1 : pos0;
-        const unsigned kmax = __reduce_max_sync(0xffffffffu, key);
-        const int mpos = __reduce_min_sync(0xffffffffu, (tc && key == kmax) ? tpos : INT_MAX);
+        tpos = use1 ? pos1 : pos0;
+        kmax = __reduce_max_sync(0xffffffffu, key);
+        mpos = __reduce_min_sync(0xffffffffu, (tc && key == kmax) ? tpos : INT_MAX);
+    };
+    candidate();
+#pragma unroll 1
+    for (int k = 0; k < nbp; ++k) {
+        const int buf = k & 1;
+        // the warp's candidate, staged as a record
+        const bool c0 = valid0 && kp0 == nbp, c1 = valid1 && kp1 == nbp;
         float *st = sm.stage[buf][warp];
         if (tc && tpos == mpos) {
             if (use1)
@@ -262,15 +272,21 @@ __global__ void __launch_bounds__(T, 1)
         // pivot row are issued ahead of the fmas).  Entries past the live width
         // are dead: they may hold stale values and are never read.
         const float4 *us = reinterpret_cast<const float4 *>(u + 4);   // u[4 + c] = column k+1+c
+        {
+            const float4 w = us[0];
+            a0[0] = fmaf(-l0, w.x, a0[1]);
+            a1[0] = fmaf(-l1, w.x, a1[1]);
+        }
+        if (k + 1 < nbp) candidate();
 #pragma unroll
         for (int q = 0; q < NB / 4; ++q) {
             if (q % 4 == 0 && q > 0 && 4 * q >= NB - 1 - k) break;
             const float4 w = us[q];
-            a0[4 * q + 0] = fmaf(-l0, w.x, a0[4 * q + 1]);
+            if (q > 0) a0[4 * q + 0] = fmaf(-l0, w.x, a0[4 * q + 1]);
             a0[4 * q + 1] = fmaf(-l0, w.y, a0[4 * q + 2]);
             a0[4 * q + 2] = fmaf(-l0, w.z, a0[4 * q + 3]);
             a0[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l0, w.w, a0[4 * q + 4]) : 0.f;
-            a1[4 * q + 0] = fmaf(-l1, w.x, a1[4 * q + 1]);
+            if (q > 0) a1[4 * q + 0] = fmaf(-l1, w.x, a1[4 * q + 1]);
             a1[4 * q + 1] = fmaf(-l1, w.y, a1[4 * q + 2]);
             a1[4 * q + 2] = fmaf(-l1, w.z, a1[4 * q + 3]);
             a1[4 * q + 3] = (4 * q + 3 < NB - 1) ? fmaf(-l1, w.w, a1[4 * q + 4]) : 0.f;
