@@ -26,78 +26,119 @@ constexpr int CPL = B / 32;      // columns of a tile per lane
 static_assert(B == 128 && TT == 32 * (B / 8), "warp w owns rows 8w..8w+7 of the block");
 
 // Inverse of the diagonal blocks: blockIdx.y = 0 -> L (unit lower), 1 -> U.
-// Thread t computes column t of the inverse by substitution (binary32).
-// Rows/columns beyond n are treated as identity.
-constexpr size_t kDiagSmem = 2 * sizeof(float) * B * (B + 1);
+// The columns of X = T^{-1} are independent, so a cluster of kDiagCG CTAs
+// shares a block, CTA q taking columns 32q .. 32q+31.  Right-looking, one step
+// per row of the block: once row m of X is final, every row below (L) or above
+// (U) takes its term -T[r][m] X[m][t].  Warp w owns the rows r = w mod 16 and
+// lane l column 32q + l; one barrier per step, so the block's dependency chain
+// is 128 short steps instead of one thread's 8k-long fmaf chain.  For L the
+// terms of X[r][t] arrive in the order m = t, ..., r - 1 (the order of forward
+// substitution); for U in the order m = t, ..., r + 1, and X[m][t] is divided
+// by T[m][m] when row m becomes final.  Rows/columns beyond n are treated as
+// identity.  The row sums of |X| for the condition number are summed over the
+// cluster through distributed shared memory.
+constexpr int kDiagCG = 4;                 // CTAs (column groups) per block
+constexpr int kDiagC = B / kDiagCG;        // columns per CTA
+constexpr int kDiagT = 512;
+constexpr int kDiagRG = kDiagT / kDiagC;   // row groups (one per warp)
+static_assert(kDiagC == 32 && kDiagRG == 16, "lane = column, warp = row group");
+struct DiagSmem {
+    float Tb[B][B + 1];
+    float X[B][kDiagC + 1];
+    float xr[B];                 // this CTA's part of the row sums of |X|
+    float red[2][B / 32];
+};
+constexpr size_t kDiagSmem = sizeof(DiagSmem);
 constexpr float kSubstKappa = 1e5f;   // blocks above this condition number are solved by substitution
-__global__ void __launch_bounds__(B) k_diag_inv(const float *AF, int64_t ldf, int n, float *Linv,
-                                                 float *Uinv, int32_t *blk_subst) {
-    extern __shared__ float dsm[];
-    float(*Tb)[B + 1] = reinterpret_cast<float(*)[B + 1]>(dsm);
-    float(*X)[B + 1] = reinterpret_cast<float(*)[B + 1]>(dsm + B * (B + 1));
-    const int b = blockIdx.x, upper = blockIdx.y, t = threadIdx.x;
+__global__ void __launch_bounds__(kDiagT) k_diag_inv(const float *AF, int64_t ldf, int n, float *Linv,
+                                                      float *Uinv, int32_t *blk_subst) {
+    extern __shared__ __align__(16) unsigned char diag_smem[];
+    DiagSmem &sm = *reinterpret_cast<DiagSmem *>(diag_smem);
+    const int b = blockIdx.x, upper = blockIdx.y;
+    const int q = (int)cluster_rank();
+    const int lane = threadIdx.x & 31, g = threadIdx.x >> 5;
+    const int c0 = q * kDiagC, t = c0 + lane;    // this thread's column of the block
     const int r0 = b * B;
-    for (int i = 0; i < B; ++i) {
-        const int gi = r0 + i, gc = r0 + t;
+    for (int i = threadIdx.x >> 7; i < B; i += kDiagT / B) {
+        const int c = threadIdx.x & (B - 1);
+        const int gi = r0 + i, gc = r0 + c;
         float v;
         if (gi < n && gc < n) v = AF[(int64_t)gi * ldf + gc];
-        else v = (i == t) ? 1.f : 0.f;
-        Tb[i][t] = v;
+        else v = (i == c) ? 1.f : 0.f;
+        sm.Tb[i][c] = v;
     }
+    for (int i = g; i < B; i += kDiagRG) sm.X[i][lane] = (i == t) ? 1.f : 0.f;
     __syncthreads();
     if (!upper) {
-        for (int i = 0; i < B; ++i) {
-            float x;
-            if (i < t) x = 0.f;
-            else if (i == t) x = 1.f;
-            else {
-                x = 0.f;
-                for (int m = t; m < i; ++m) x = fmaf(-Tb[i][m], X[m][t], x);
+#pragma unroll 1
+        for (int m = c0; m < B - 1; ++m) {   // X[m][t] = 0 for t > m: steps m < c0 change nothing here
+            if (t <= m) {
+                const float xm = sm.X[m][lane];
+#pragma unroll 2
+                for (int r = m + 1 + ((g - (m + 1)) & (kDiagRG - 1)); r < B; r += kDiagRG)
+                    sm.X[r][lane] = fmaf(-sm.Tb[r][m], xm, sm.X[r][lane]);
             }
-            X[i][t] = x;
+            __syncthreads();
         }
     } else {
-        for (int i = B - 1; i >= 0; --i) {
-            float x;
-            if (i > t) x = 0.f;
-            else {
-                x = (i == t) ? 1.f : 0.f;
-                for (int m = i + 1; m <= t; ++m) x = fmaf(-Tb[i][m], X[m][t], x);
-                x = x / Tb[i][i];
+#pragma unroll 1
+        for (int m = c0 + kDiagC - 1; m >= 0; --m) {   // rows m > c0 + 31 have no term in these columns
+            float xm = 0.f;
+            if (t >= m) xm = sm.X[m][lane] / sm.Tb[m][m];   // row m final (X[m][t] = 0 for t < m)
+            __syncthreads();                                 // every warp has read the row
+            if (t >= m) {
+                if (g == (m & (kDiagRG - 1))) sm.X[m][lane] = xm;
+#pragma unroll 2
+                for (int r = g; r < m; r += kDiagRG) sm.X[r][lane] = fmaf(-sm.Tb[r][m], xm, sm.X[r][lane]);
             }
-            X[i][t] = x;
+            __syncthreads();
         }
     }
-    __syncthreads();
     float *dst = (upper ? Uinv : Linv) + (int64_t)b * B * B;
-    for (int i = 0; i < B; ++i) dst[i * B + t] = X[i][t];
+    for (int i = g; i < B; i += kDiagRG) dst[i * B + t] = sm.X[i][lane];
     // kappa_inf of the triangle: max row sum of |T| times max row sum of |T^{-1}|
-    float tr = 0.f, xr = 0.f;
-    for (int m = 0; m < B; ++m) {
-        const float tv = upper ? (m >= t ? Tb[t][m] : 0.f) : (m < t ? Tb[t][m] : (m == t ? 1.f : 0.f));
-        tr += fabsf(tv);
-        xr += fabsf(X[t][m]);
+    if (threadIdx.x < B) {
+        const int i = threadIdx.x;
+        float xr = 0.f;
+        for (int c = 0; c < kDiagC; ++c) xr += fabsf(sm.X[i][c]);
+        sm.xr[i] = xr;
     }
-    __shared__ float red[2][B / 32];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        tr = fmaxf(tr, __shfl_xor_sync(0xffffffffu, tr, o));
-        xr = fmaxf(xr, __shfl_xor_sync(0xffffffffu, xr, o));
-    }
-    if ((t & 31) == 0) {
-        red[0][t >> 5] = tr;
-        red[1][t >> 5] = xr;
-    }
-    __syncthreads();
-    if (t == 0) {
-        float tm = 0.f, xm = 0.f;
-        for (int w = 0; w < B / 32; ++w) {
-            tm = fmaxf(tm, red[0][w]);
-            xm = fmaxf(xm, red[1][w]);
+    cluster_sync_all();   // every part of the row sums is in place
+    if (q == 0 && threadIdx.x < B) {
+        const int i = threadIdx.x;
+        float tr = 0.f;
+        for (int m = 0; m < B; ++m) {
+            const float tv = upper ? (m >= i ? sm.Tb[i][m] : 0.f) : (m < i ? sm.Tb[i][m] : (m == i ? 1.f : 0.f));
+            tr += fabsf(tv);
         }
-        const float kappa = tm * xm;
-        blk_subst[upper * gridDim.x + b] = !(kappa <= kSubstKappa);   // NaN: substitution too
+        float xr = sm.xr[i];
+        const unsigned a = smem_u32(&sm.xr[i]);
+        for (int p = 1; p < kDiagCG; ++p) {
+            float v;
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(map_cta(a, (unsigned)p)) : "memory");
+            xr += v;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            tr = fmaxf(tr, __shfl_xor_sync(0xffffffffu, tr, o));
+            xr = fmaxf(xr, __shfl_xor_sync(0xffffffffu, xr, o));
+        }
+        if ((i & 31) == 0) {
+            sm.red[0][i >> 5] = tr;
+            sm.red[1][i >> 5] = xr;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(B) : "memory");   // the 4 warps that hold the rows
+        if (i == 0) {
+            float tm = 0.f, xm = 0.f;
+            for (int w = 0; w < B / 32; ++w) {
+                tm = fmaxf(tm, sm.red[0][w]);
+                xm = fmaxf(xm, sm.red[1][w]);
+            }
+            const float kappa = tm * xm;
+            blk_subst[upper * gridDim.x + b] = !(kappa <= kSubstKappa);   // NaN: substitution too
+        }
     }
+    cluster_sync_all();   // no CTA leaves while its row sums may still be read
 }
 
 __device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
@@ -956,8 +997,19 @@ cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, fl
     }
     const int nblk = (n + B - 1) / B;
     count_launch();
-    k_diag_inv<<<dim3(nblk, 2), B, kDiagSmem, s>>>(AF, ldf, n, Linv, Uinv, blk_subst);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nblk, 2, kDiagCG);
+    cfg.blockDim = dim3(kDiagT, 1, 1);
+    cfg.dynamicSmemBytes = kDiagSmem;
+    cfg.stream = s;
+    cudaLaunchAttribute cl[1];
+    cl[0].id = cudaLaunchAttributeClusterDimension;
+    cl[0].val.clusterDim.x = 1;
+    cl[0].val.clusterDim.y = 1;
+    cl[0].val.clusterDim.z = kDiagCG;
+    cfg.attrs = cl;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_diag_inv, AF, ldf, n, Linv, Uinv, blk_subst);
 }
 
 static bool cluster_solve_enabled() {
