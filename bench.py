@@ -69,6 +69,28 @@ def parse():
     return ap.parse_args()
 
 
+# DRAM bytes (read + written) of one k_panel launch from the ncu capture summarised
+# in profiles/k_panel_green_N4096.md (the 21st panel of N = 4096: 2816 rows), and
+# the SHA-256 of the kernel source it was taken on; the traffic is reported only
+# while the source is unchanged, scaled to the average launch by its rows (the
+# panel reads each of its rows once).
+PANEL_TRAFFIC = {"sha256": "a99d0a37d965bbb824be2b60acf53b80c644ea8400fed5db6cf1279e84823ee6",
+                 "bytes": 755968.0, "rows": 2816}
+
+
+def panel_traffic_per_launch(n, nb=64):
+    import hashlib
+    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2311_14616_gb300", "csrc", "k_panel.cu")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    if digest != PANEL_TRAFFIC["sha256"]:
+        return None
+    rows = [n - j for j in range(0, n, nb)]
+    return PANEL_TRAFFIC["bytes"] * (sum(rows) / len(rows)) / PANEL_TRAFFIC["rows"]
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -511,7 +533,7 @@ def main():
         roof = {"bound": "hbm", "achieved": n * n * 4 / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
                 "unit": "GB/s", "kernel": "k_" + dom}
     roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = None
+    roof["traffic"] = panel_traffic_per_launch(n) if dom == "panel" else None   # bytes per launch
     roof["peak_source"] = peaks["source"] if roof["bound"] != "alu" else "unit counts x 2070 MHz"
     roof["share_of_step"] = dom_ms / total_prof
     roof["avg_launch_ms"] = avg_ms
