@@ -295,7 +295,8 @@ def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: 
 
 
 def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
-             nb: int = 0, fp16_scaling: bool = True, tr_wider: Optional[bool] = None) -> IRResult:
+             nb: int = 0, fp16_scaling: bool = True, tr_wider: Optional[bool] = None,
+             solve: str = "lps") -> IRResult:
     """Algorithm IR (Sec. 1) with TR = binary64 and solves in binary32.
 
     1. A_F = round_TF(s A) (s = 2^10/max|a| for TF = binary16, else 1);
@@ -305,7 +306,14 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
        (eq. vdlow); d = (rho s) fl64(v) (eq. promotevd); x += d;
        r = b - A x in binary64; test termination.
     The solution is returned both as the binary64 accumulator and rounded to TW.
+
+    solve = "mps": the mixed precision solves of Sec. 5.3 (interprecision
+    transfers on the fly): r is rounded to TW, not below it, and the triangular
+    solves run in TW on the factors promoted to TW (exactly), so there is no
+    scaling by ||r||: d = s fl64(U^{-1} L^{-1} P fl_W(r)) evaluated in TW.
     """
+    if solve not in ("lps", "mps"):
+        raise ValueError(solve)
     term = term or Term()
     A = np.asfortranarray(A)
     tw = _tw_of(A)
@@ -329,10 +337,17 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
         return res
     anorm = norm1(A) if term.mode == 1 else 0.0
     r = b64.copy()
+    LU64 = LU.astype(np.float64) if (solve == "mps" and tw == F64) else None
     while True:
-        rho = float(np.max(np.abs(r)))
-        v = getrs_f32(LU, ipiv, (r / rho).astype(np.float32))
-        d = (rho * s) * v.astype(np.float64)
+        if solve == "mps":
+            if tw == F64:
+                d = s * getrs_f64(LU64, ipiv, r)
+            else:
+                d = s * getrs_f32(LU, ipiv, r.astype(np.float32)).astype(np.float64)
+        else:
+            rho = float(np.max(np.abs(r)))
+            v = getrs_f32(LU, ipiv, (r / rho).astype(np.float32))
+            d = (rho * s) * v.astype(np.float64)
         x += d
         res.dhist.append(float(np.max(np.abs(d))))
         r = residual(A, b64, x)

@@ -348,6 +348,56 @@ def test_ir_reproduces_paper_double_single_history(golden):
     assert O.rel_err_inf(res.x, np.ones(n)) < 10 * 8.88178e-16
 
 
+def test_ir_mps_reproduces_paper_onthefly_history(golden):
+    """Mixed precision solves (Sec. 5.3, onthefly = true): the residual history
+    printed in Sec. 2.2.1 for A = I - Gmat(4096), b = A 1, digit for digit."""
+    g = golden("paper_values.json")["ir_double_single_onthefly_alpha1_N4096"]
+    A, _ = irgen.case_green(4096, 1.0, rule="trapezoid")
+    n = A.shape[0]
+    b = -O.residual(A, np.zeros(n), np.ones(n))
+    res = O.ir_solve(A, b, O.F32, solve="mps")
+    assert res.status == O.CONVERGED
+    assert [float("%.5e" % v) for v in res.rhist] == g["rhist"]
+    # the same factors with binary32 solves (eq. vdlow) take another path
+    lps = O.ir_solve(A, b, O.F32)
+    assert [float("%.5e" % v) for v in lps.rhist] != g["rhist"]
+
+
+def test_ir_mps_half_precision_factors(golden):
+    """TF = binary16 with mixed precision solves (the paper's default for half,
+    Sec. 2.2.1): converges, within the printed iteration count."""
+    g = golden("paper_values.json")["ir_double_half_alpha1_N4096"]
+    A, _ = irgen.case_green(4096, 1.0, rule="trapezoid")
+    n = A.shape[0]
+    b = -O.residual(A, np.zeros(n), np.ones(n))
+    res = O.ir_solve(A, b, O.F16, solve="mps")
+    assert res.status == O.CONVERGED
+    assert len(res.rhist) <= len(g["rhist"])
+    assert res.rhist[1] <= 10 * g["rhist"][1]
+    assert O.rel_err_inf(res.x, np.ones(n)) < 10 * 8.88178e-16
+
+
+def test_ir_mps_solves_in_working_precision():
+    """With factors that are exact (a diagonal of powers of two) a solve in TW =
+    binary64 gives A^{-1} b exactly, so MPS stops after one step with r = 0;
+    the binary32 solve of eq. (vdlow) rounds P r / ||r|| to binary32 first and
+    needs further steps.  TW = binary32: the solve is binary32 on fl32(r)."""
+    diag = np.array([2.0, -0.5, 4.0, 1.0, 0.25, 8.0, 16.0, -2.0] * 4)
+    A = np.asfortranarray(np.diag(diag))
+    b = np.random.default_rng(3).standard_normal(32)
+    res = O.ir_solve(A, b, O.F32, solve="mps")
+    assert res.status == O.CONVERGED and res.rhist[-1] == 0.0 and res.iters == 1
+    np.testing.assert_array_equal(res.x, b / diag)
+    lps = O.ir_solve(A, b, O.F32)
+    assert lps.iters >= 2
+    A32 = np.asfortranarray(A.astype(np.float32))
+    b32 = b.astype(np.float32)
+    r32 = O.ir_solve(A32, b32, O.F32, solve="mps")
+    np.testing.assert_array_equal(r32.sol, b32 / diag.astype(np.float32))
+    with pytest.raises(ValueError):
+        O.ir_solve(A, b, O.F32, solve="hps")
+
+
 def test_ir_accuracy_alpha800_matches_table(golden):
     """alpha = 800, x = 1: converged error near Table ip3's ELP (soft)."""
     g = golden("paper_values.json")["accuracy_alpha800"]
