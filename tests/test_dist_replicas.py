@@ -1,0 +1,83 @@
+"""Host-side logic of the multi-GPU bench path (replicas only: one dense
+system per GPU, nothing exchanged but a barrier and the max of the step
+times), run as world_size-2 gloo ranks on the CPU."""
+import json
+import os
+import socket
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank_main(rank, ws, port, q):
+    os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port), "WORLD_SIZE": str(ws),
+                       "RANK": str(rank), "LOCAL_RANK": str(rank)})
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    got_ws, got_rank, local = bench.dist_setup(None)
+    try:
+        assert (got_ws, got_rank, local) == (ws, rank, rank)
+        assert dist.get_backend() == "gloo"
+        bench.barrier(ws)
+        # every rank learns the slowest rank's step time
+        m = bench.max_over_ranks(10.0 + 3.5 * rank, ws)
+        bench.barrier(ws)
+        q.put((rank, m))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_replica_barrier_and_max_over_ranks():
+    import torch.multiprocessing as mp
+    ws, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_rank_main, args=(r, ws, port, q)) for r in range(ws)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(timeout=120)
+    assert all(p.exitcode == 0 for p in procs), [p.exitcode for p in procs]
+    got = sorted(q.get(timeout=10) for _ in range(ws))
+    assert got == [(0, 13.5), (1, 13.5)]
+
+
+def test_single_rank_needs_no_process_group():
+    sys.path.insert(0, ROOT)
+    import bench
+    env = {k: os.environ.pop(k) for k in ("WORLD_SIZE", "RANK", "LOCAL_RANK") if k in os.environ}
+    try:
+        assert bench.dist_setup(None) == (1, 0, 0)
+        bench.barrier(1)
+        assert bench.max_over_ranks(7.25, 1) == 7.25
+    finally:
+        os.environ.update(env)
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    """bench.py --impl reference launched like the driver launches N > 1: rank 0
+    times the oracle and prints the one JSON line, the other rank exits 0."""
+    port = _free_port()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+           "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "0"]
+    env = dict(os.environ, OMP_NUM_THREADS="2")
+    out = subprocess.run(cmd, cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["higher_is_better"] is False
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["value"] > 0
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
