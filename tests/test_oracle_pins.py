@@ -6,6 +6,8 @@ rounding-error bound, or numbers printed in the paper.
 """
 from fractions import Fraction
 
+import itertools
+
 import numpy as np
 import pytest
 
@@ -147,6 +149,51 @@ def test_lu_f32_pivots_and_factors_exact_on_small(n):
     for i in range(n):
         for j in range(n):
             assert abs(LU[i, j] - float(M[i][j])) <= 64 * 2 ** -23 * max(1.0, abs(float(M[i][j])))
+
+
+def _rows_with_small_multipliers(A):
+    """Brute force over every row order of a tiny matrix: the orders whose LU
+    without interchanges, in exact arithmetic, has all |l_ik| <= 1."""
+    n = A.shape[0]
+    keep = []
+    for order in itertools.permutations(range(n)):
+        M = [[Fraction(float(A[r][j])) for j in range(n)] for r in order]
+        ok = True
+        for k in range(n):
+            if M[k][k] == 0:
+                ok = all(M[i][k] == 0 for i in range(k + 1, n))
+                if not ok:
+                    break
+                continue
+            for i in range(k + 1, n):
+                l = M[i][k] / M[k][k]
+                if abs(l) > 1:
+                    ok = False
+                    break
+                for j in range(k + 1, n):
+                    M[i][j] -= l * M[k][j]
+            if not ok:
+                break
+        if ok:
+            keep.append(list(order))
+    return keep
+
+
+@pytest.mark.parametrize("n", [2, 3, 4, 5])
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_lu_pivots_are_the_one_row_order_with_small_multipliers(n, seed):
+    """Partial pivoting (first row of maximal |a_ik| at every step) is the unique
+    row order whose unpivoted LU has every multiplier of magnitude <= 1 when no
+    two candidates tie; the oracle's interchanges must produce exactly it."""
+    A, _ = irgen.case_random(n, 500 + 10 * n + seed)
+    orders = _rows_with_small_multipliers(A)
+    assert len(orders) == 1
+    _, ipiv, info = O.getrf_f64(A)
+    assert info == 0
+    assert list(O.perm_from_ipiv(ipiv)) == orders[0]
+    AF = O.cast(A, O.F32)
+    _, ipiv32, _ = O.getrf_tf(AF, O.F32)
+    assert list(O.perm_from_ipiv(ipiv32)) == _rows_with_small_multipliers(AF)[0]
 
 
 def test_lu_tie_breaks_to_first_row_and_zero_pivot():
