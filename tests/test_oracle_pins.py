@@ -445,6 +445,28 @@ def test_ir_mps_solves_in_working_precision():
         O.ir_solve(A, b, O.F32, solve="hps")
 
 
+@pytest.mark.parametrize("case,tf", [("I-G", O.F32), ("I-G", O.TF32), ("I-G", O.F16), ("gauss", O.F32)])
+def test_ir_mps_contraction_within_rate_bound(case, tf):
+    """Eq. (rate2) (Sec. 5.4.2): with mixed precision solves the residual
+    contracts per step by at most alpha = u_F (||A|| + 13 sqrt(N) kappa(L)
+    kappa(U)), infinity norms, while it is far above its rounding floor.  The
+    bound is checked on cases where it is informative (alpha < 1), on the
+    first two steps."""
+    n = 128
+    A, b = (irgen.case_green(n, 1.0, rule="trapezoid") if case == "I-G" else irgen.case_gaussian(n, 7))
+    s = O.fp16_scale(A) if tf == O.F16 else 1.0
+    LU, _, _ = O.getrf_tf(O.cast(A, tf, s), tf, 64)
+    L = np.tril(LU.astype(np.float64), -1) + np.eye(n)
+    U = np.triu(LU.astype(np.float64))
+    kappa = lambda M: np.linalg.norm(M, np.inf) * np.linalg.norm(np.linalg.inv(M), np.inf)
+    u_f = {O.F32: 2.0 ** -23, O.TF32: 2.0 ** -10, O.BF16: 2.0 ** -7, O.F16: 2.0 ** -10}[tf]
+    alpha = u_f * (np.linalg.norm(A, np.inf) + 13 * np.sqrt(n) * kappa(L) * kappa(U))
+    res = O.ir_solve(A, b, tf, solve="mps", nb=64)
+    assert alpha < 1
+    for k in range(2):
+        assert res.rhist[k + 1] <= alpha * res.rhist[k], (k, res.rhist, alpha)
+
+
 def test_ir_accuracy_alpha800_matches_table(golden):
     """alpha = 800, x = 1: converged error near Table ip3's ELP (soft)."""
     g = golden("paper_values.json")["accuracy_alpha800"]
