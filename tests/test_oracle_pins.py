@@ -7,6 +7,7 @@ rounding-error bound, or numbers printed in the paper.
 from fractions import Fraction
 
 import itertools
+import os
 
 import numpy as np
 import pytest
@@ -618,3 +619,27 @@ def test_ir_backward_error_termination_on_ill_conditioned_system():
     assert r1.iters == r0.iters - 1
     assert r1.rhist == r0.rhist[:-1]
     assert r1.rhist[-1] <= 2.0 ** -52 * (1.0 + O.norm1(A) * np.max(np.abs(r1.x)))
+
+
+def test_oracle_is_bitwise_independent_of_the_thread_count():
+    """The oracle's parallel loops split only independent work (rows of a
+    rank-1 update, rows of a residual), so its results do not depend on the
+    number of OpenMP threads: one thread reproduces them bit for bit."""
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    code = (
+        "import sys; sys.path.insert(0, %r); import numpy as np, irgen, oracle as O\n"
+        "A, b = irgen.case_random(300, 77)\n"
+        "LU, ipiv, _ = O.getrf_tf(O.cast(A, O.TF32), O.TF32, 64)\n"
+        "LU64, ipiv64, _ = O.getrf_f64(A)\n"
+        "r = O.residual(A, b, np.linspace(-1, 1, 300))\n"
+        "sys.stdout.buffer.write(LU.tobytes() + ipiv.tobytes() + LU64.tobytes() + ipiv64.tobytes() + r.tobytes())\n"
+    ) % root
+    outs = []
+    for threads in ("1", "4"):
+        env = dict(os.environ, OMP_NUM_THREADS=threads)
+        p = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, timeout=300)
+        assert p.returncode == 0, p.stderr.decode()[-2000:]
+        outs.append(p.stdout)
+    assert len(outs[0]) > 0 and outs[0] == outs[1]
