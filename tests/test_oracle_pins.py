@@ -452,7 +452,9 @@ def test_ir_mps_contraction_within_rate_bound(case, tf):
     contracts per step by at most alpha = u_F (||A|| + 13 sqrt(N) kappa(L)
     kappa(U)), infinity norms, while it is far above its rounding floor.  The
     bound is checked on cases where it is informative (alpha < 1), on the
-    first two steps."""
+    first two steps; then every step against the bound that adds the
+    residual's rounding, and the final residual against the stagnation level
+    of eq. (stagterm)."""
     n = 128
     A, b = (irgen.case_green(n, 1.0, rule="trapezoid") if case == "I-G" else irgen.case_gaussian(n, 7))
     s = O.fp16_scale(A) if tf == O.F16 else 1.0
@@ -466,6 +468,17 @@ def test_ir_mps_contraction_within_rate_bound(case, tf):
     assert alpha < 1
     for k in range(2):
         assert res.rhist[k + 1] <= alpha * res.rhist[k], (k, res.rhist, alpha)
+    # Sec. 5.4.2 with the residual's own rounding (eqs. residerr, stagterm):
+    # ||r_{k+1}|| <= alpha ||r_k|| + (1 + alpha)/(1 - alpha) xi at every step,
+    # xi = gamma_N(u_W) (C ||A|| ||x*|| + ||b||), C the iterates' bound
+    xs = O.reference_solution(A, b)
+    gam = n * 2.0 ** -53 / (1 - n * 2.0 ** -53)
+    c_bound = max(1.0, np.max(np.abs(res.x)) / np.max(np.abs(xs)))
+    xi = gam * (c_bound * np.linalg.norm(A, np.inf) * np.max(np.abs(xs)) + np.max(np.abs(b)))
+    floor = (1 + alpha) / (1 - alpha) * xi
+    for k in range(len(res.rhist) - 1):
+        assert res.rhist[k + 1] <= alpha * res.rhist[k] + floor, (k, res.rhist, alpha, floor)
+    assert res.rhist[-1] <= floor
 
 
 def test_ir_accuracy_alpha800_matches_table(golden):
