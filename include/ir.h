@@ -180,8 +180,11 @@ ir_status ir_residual(ir_ctx *ctx, int64_t n, ir_dtype TW, const void *A, int64_
  * in the library's device image, held by every GPU that loads the library
  * until exit.  No context is needed; the current device is used.
  *   n <= IR_RESIDUAL_NOALLOC_MAX_N, else IR_EUNSUPPORTED (nothing launched).
- *   The first call on a device looks up the array's address (once per device,
- *   with that device current): make it before any stream capture.
+ *   The first successful call on a device looks up the array's address (once
+ *   per device, with that device current): make it before any stream capture.
+ *   A failed lookup is retried by the next call.  The address is kept until
+ *   exit: resetting the device or its primary context afterwards is not
+ *   supported.
  *   All calls share the array: calls that overlap on the GPU race and give
  *   wrong results; calls ordered on one stream are safe (each call writes
  *   every partial sum it reads and clears rnorm itself). */

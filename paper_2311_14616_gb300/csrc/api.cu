@@ -409,6 +409,8 @@ int term_decide(const double *rh, const double *dh, int k, double bnorm, double 
 
 }  // namespace
 
+ir_status ir::record_cuda_error(cudaError_t e, const char *what) { return cuda_fail(e, what); }
+
 // A planned batch (ir_batch_create): descriptors and the largest-first order on
 // the device, the ticket counter of the persistent launch, the workspace slots.
 struct ir_batch {

@@ -144,6 +144,8 @@ namespace ir {
 void count_launch();                       // one call per kernel launch
 void count_launches(unsigned long long k);  // k kernels launched at once (a graph replay)
 unsigned long long launches();
+// Record a failed CUDA call for ir_last_error() and map it to IR_ENOMEM / IR_ECUDA.
+ir_status record_cuda_error(cudaError_t e, const char *what);
 
 // ---- launchers (each returns the launch error) -----------------------------
 cudaError_t launch_maxabs(int64_t n, ir_dtype tw, const void *A, int64_t lda, DevScalars *dev,

@@ -11,10 +11,13 @@
 // the library holds that array (IR_RESIDUAL_NOALLOC_SCRATCH doubles, 8 MiB)
 // until the process exits.
 //
-// Setup: the first call on a device (with that device current) looks up the
-// array's device address with cudaGetSymbolAddress, once per device; make
-// that first call before any stream capture begins.  The host-side name of
-// the array is only a stand-in and is never handed to a kernel.
+// Setup: the first successful call on a device (with that device current)
+// looks up the array's device address with cudaGetSymbolAddress, once per
+// device; make that first call before any stream capture begins.  A lookup
+// that fails is not remembered: the next call tries again.  The address is
+// kept for the life of the process, so resetting the device or its primary
+// context after the first call is not supported.  The host-side name of the
+// array is only a stand-in and is never handed to a kernel.
 //
 // Sharing: all calls use the same array.  Every partial sum a call reads was
 // written by that call's first kernel, and the norm output is cleared by the
@@ -31,9 +34,22 @@ constexpr int64_t kScratchDoubles = IR_RESIDUAL_NOALLOC_SCRATCH;
 static __device__ __align__(256) double g_resid_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
-double *g_scratch_dev[kMaxDevices];            // device address of the array, per device
-cudaError_t g_setup_status[kMaxDevices];
-std::once_flag g_setup_once[kMaxDevices];
+double *g_scratch_dev[kMaxDevices];            // device address of the array, per device (null: not set up)
+std::mutex g_setup_mutex;
+
+// The array's device address on device `dev` (current), looked up on the first
+// successful call; a failed lookup is retried by the next call.
+cudaError_t scratch_address(int dev, double **out) {
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (!g_scratch_dev[dev]) {
+        double *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress((void **)&p, g_resid_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_dev[dev] = p;
+    }
+    *out = g_scratch_dev[dev];
+    return cudaSuccess;
+}
 
 }  // namespace
 
@@ -44,23 +60,25 @@ extern "C" ir_status ir_residual_noalloc(int64_t n, ir_dtype TW, const void *A, 
     if (n > 0 && (!A || !b || !x || !r || !rnorm)) return IR_EINVAL;
     if (n > IR_RESIDUAL_NOALLOC_MAX_N) return IR_EUNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
     if (n == 0) {
-        if (rnorm && cudaMemsetAsync(rnorm, 0, sizeof(double), s) != cudaSuccess) return IR_ECUDA;
+        if (rnorm && (e = cudaMemsetAsync(rnorm, 0, sizeof(double), s)) != cudaSuccess)
+            return ir::record_cuda_error(e, "cudaMemsetAsync(rnorm)");
         return IR_OK;
     }
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return IR_ECUDA;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return ir::record_cuda_error(e, "cudaGetDevice");
     if (dev < 0 || dev >= kMaxDevices) return IR_EUNSUPPORTED;
-    std::call_once(g_setup_once[dev], [dev] {
-        g_setup_status[dev] = cudaGetSymbolAddress((void **)&g_scratch_dev[dev], g_resid_scratch);
-    });
-    if (g_setup_status[dev] != cudaSuccess) return IR_ECUDA;
+    double *scratch = nullptr;
+    if ((e = scratch_address(dev, &scratch)) != cudaSuccess)
+        return ir::record_cuda_error(e, "cudaGetSymbolAddress(residual scratch)");
     int sms = 1;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return IR_ECUDA;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
+        return ir::record_cuda_error(e, "cudaDeviceGetAttribute");
     // fewer column splits when the partial sums would not fit the array
     while (sms > 1 && ir::residual_partials_needed(n, sms) > kScratchDoubles) sms /= 2;
     if (ir::residual_partials_needed(n, sms) > kScratchDoubles) return IR_EUNSUPPORTED;
-    const cudaError_t e = ir::launch_residual(n, TW, A, lda, b, x, r, g_scratch_dev[dev], kScratchDoubles,
-                                              reinterpret_cast<unsigned long long *>(rnorm), sms, s);
-    return e == cudaSuccess ? IR_OK : IR_ECUDA;
+    e = ir::launch_residual(n, TW, A, lda, b, x, r, scratch, kScratchDoubles,
+                            reinterpret_cast<unsigned long long *>(rnorm), sms, s);
+    return e == cudaSuccess ? IR_OK : ir::record_cuda_error(e, "launch_residual (noalloc)");
 }

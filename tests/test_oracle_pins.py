@@ -249,6 +249,49 @@ def test_lu_backward_error_bounds(n, tf):
             assert np.max(np.abs(E)) > 64 * 2 ** -24 * np.max(np.abs(AF)), name
 
 
+@pytest.mark.parametrize("tf", [O.TF32, O.BF16, O.F16])
+def test_lu_tf_update_rounding_points_hand_worked(tf):
+    """The trailing update of the TF factorization (reading of Sec. 5.4.1 eq.
+    (comperr) with tensor-core operands): A22 <- fl32(A22 - fl32(sum_k
+    rTF(l_ik) rTF(u_kj))), both operands rounded to TF, the exact products
+    summed in binary64 and rounded to binary32 once per block.  Worked by
+    hand on a 4 x 4 matrix with nb = 3 whose leading 3 x 3 block is I, so
+    that L11 = U11 = I, l_3k = a_3k, u_k3 = a_k3 and no row moves:
+
+        l_30 = 1/2,              u_03 = 2              -> product 1
+        l_31 = 3*2^-13 + 2^-24,  u_13 = 2^-12 + 2^-24  -> rTF: 3*2^-13, 2^-12 -> 3*2^-25
+        l_32 = -2^-13,           u_23 = 2^-12          -> -2^-25
+
+    (2^-24 is below half the TF spacing at these values for TF32, bf16 and
+    binary16, so rTF drops it.)  The exact sum is 1 + 2^-24, a binary32 tie
+    that rounds to even: 1; so a_33 = 2 becomes 2 - 1 = 1.  Each plausible
+    slip lands on 1 + 2^-23 instead and gives a_33 = 1 - 2^-23:
+      * only L21 rounded: 3*2^-13 (2^-12 + 2^-24) pushes the sum above the tie;
+      * only U12 rounded: (3*2^-13 + 2^-24) 2^-12 does the same;
+      * no rounding at all: both perturbations, above the tie;
+      * products summed in binary32: fl32(1 + 3*2^-25) = 1 + 2^-23, and
+        subtracting 2^-25 keeps it there;
+    and subtracting each product from a_33 in binary32 in turn ends at
+    1 - 2^-23 too (two ties, both to even)."""
+    A = np.zeros((4, 4))
+    A[:3, :3] = np.eye(3)
+    A[3, 0], A[0, 3] = 0.5, 2.0
+    A[3, 1], A[1, 3] = 3 * 2.0 ** -13 + 2.0 ** -24, 2.0 ** -12 + 2.0 ** -24
+    A[3, 2], A[2, 3] = -(2.0 ** -13), 2.0 ** -12
+    A[3, 3] = 2.0
+    AF = np.asfortranarray(A.astype(np.float32))
+    assert np.array_equal(AF.astype(np.float64), A)       # every entry is binary32
+    LU, ipiv, info = O.getrf_tf(AF, tf, nb=3)
+    assert info == 0 and list(ipiv) == [0, 1, 2, 3]
+    assert LU[3, 3] == np.float32(1.0)
+    # the multipliers and U12 are stored unrounded (binary32 storage, reading 8)
+    assert LU[3, 1] == AF[3, 1] and LU[1, 3] == AF[1, 3]
+    # the same block with binary32 factors (no TF rounding, fmaf chain per entry)
+    # takes another path: 2 - 1 - 3*2^-25 (rounded) + 2^-25
+    LU32, _, _ = O.getrf_tf(AF, O.F32)
+    assert LU32[3, 3] != np.float32(1.0)
+
+
 def test_lu_tf_with_one_block_is_the_binary32_lu():
     # nb >= N: no trailing update happens, every TF path is the binary32 factorization
     A, _ = irgen.case_random(40, 21)

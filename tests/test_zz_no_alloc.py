@@ -13,6 +13,7 @@ import pytest
 import torch
 
 import irgen
+import oracle as O
 from gpu_util import dev_colmajor, dev_vec
 from paper_2311_14616_gb300 import ir
 
@@ -60,6 +61,9 @@ def test_noalloc_residual_matches_allocating_entry_point_twice(ctx, tw):
         torch.cuda.synchronize()
         r, r_ref = r.cpu().numpy(), r_ref.cpu().numpy()
         assert np.all(np.abs(r - r_ref) <= _bound(A, b, x) + 1e-300)
+        # and against the CPU oracle's residual (a sequential binary64 fma chain per row)
+        r_orc = O.residual(A, b, x)
+        assert np.all(np.abs(r - r_orc) <= _bound(A, b, x) + 1e-300)
         assert float(rn.cpu()[0]) == np.max(np.abs(r))
         assert abs(float(rn.cpu()[0]) - float(rn_ref.cpu()[0])) <= np.max(_bound(A, b, x))
 
