@@ -7,9 +7,12 @@
   oracle's ir_solve results, for TW = binary64 and for TW = binary32 (where
   TR is wider and eq. (wilkterm) decides).
 * TF = binary16 / bfloat16 / TF32: the trailing update sums in binary32 where
-  the oracle sums exactly, so the factors differ by rounding; converged
-  solutions must agree with the oracle's within the parity tolerance, and
-  every reported residual norm must equal, bitwise, the oracle's binary64
+  the oracle sums exactly, so the factors differ by rounding.  Each member is
+  placed by the oracle's own run (parity.classify): away from the convergence
+  boundary of its TF the status must be the oracle's, and where the oracle's
+  x meets the parity bar against x_ref the GPU's x must meet it against both
+  x_ref and the oracle's x; the tests assert how many members were compared.
+  Every reported residual norm must equal, bitwise, the oracle's binary64
   residual of the returned iterate.
 * The full-size workload (2000 systems, N uniform in [32, 512]) is checked on
   a sample of systems against the oracle and on all systems by the residual
@@ -21,6 +24,7 @@ import torch
 
 import irgen
 import oracle as O
+import parity as P
 from gpu_util import dev_colmajor, dev_vec
 from paper_2311_14616_gb300 import ir
 
@@ -48,10 +52,28 @@ def _run(ctx, As, bs, tf, dtype=np.float64, term=None):
     return xs, res
 
 
-def _clearly_converged(o):
-    """The oracle converged with every residual ratio well below Rmax."""
-    h = o.rhist
-    return o.status == O.CONVERGED and all(h[k + 1] < 0.25 * h[k] for k in range(len(h) - 2))
+# litmax of the low-precision comparisons: bfloat16 factors reach the rounding floor
+# after 8 - 12 steps, so with the default 10 the stop between eq. (stag) and
+# litmax would be decided by floor noise; 20 leaves every converging run room to
+# end by eq. (stag) (parity.status_must_match)
+LITMAX_LP = 20
+
+
+def _judge(A, b, x, r, tf, litmax=LITMAX_LP):
+    """Compare one batch member with the oracle's IR on the same system; returns
+    the oracle's class and whether x and the status were compared."""
+    o = O.ir_solve(A, b, TF[tf], O.Term(litmax=litmax), nb=64)
+    xr = O.reference_solution(A, b)
+    kappa = O.cond_inf(A)
+    tol = P.bar(kappa)
+    cls = P.classify(o, O.rel_err_inf(o.x, xr) <= tol)
+    st = P.status_must_match(o, cls, litmax)
+    if st:
+        assert r["status"] == STATUS[o.status], (A.shape[0], cls, r, o.rhist)
+    if cls == "conv":
+        assert O.rel_err_inf(x, o.x) <= tol, (A.shape[0], O.rel_err_inf(x, o.x), tol)
+        assert O.rel_err_inf(x, xr) <= tol, (A.shape[0], O.rel_err_inf(x, xr), tol)
+    return cls, st
 
 
 def _rnorm_of(A, b, x):
@@ -88,25 +110,23 @@ def test_batch_f32_bitwise_equals_oracle(ctx, tw):
 def test_batch_low_precision_vs_oracle(ctx, tf):
     ns = [32, 47, 64, 65, 96, 130, 192, 257, 320, 384, 449, 512]
     alphas, As, bs = irgen.case_batch_sizes(ns, 4200 + len(tf))
-    xs, res = _run(ctx, As, bs, tf)
+    xs, res = _run(ctx, As, bs, tf, term=ir.default_term(litmax=LITMAX_LP))
+    compared = status_cmp = 0
     for A, b, x, r, alpha in zip(As, bs, xs, res, alphas):
         n = A.shape[0]
-        o = O.ir_solve(A, b, TF[tf], nb=64)
         if tf == "f16":
             assert r["scale"] == 1024.0 / np.max(np.abs(A))
         assert r["status"] != "failed" and not r["nonfinite"]
         # the reported norm is the binary64 residual of the returned iterate, bit for bit
         assert _same(r["rnorm"], _rnorm_of(A, b, x)), n
-        if _clearly_converged(o):
-            assert r["status"] == "converged", (n, alpha, r, o.rhist)
-            kappa = O.cond_inf(A)
-            tol = O.parity_tol(kappa, O.F64)
-            assert np.max(np.abs(x - o.sol)) <= tol * np.max(np.abs(o.sol)), (n, alpha)
-            xr = O.reference_solution(A, b)
-            assert O.rel_err_inf(x, xr) <= tol, (n, alpha)
-        elif r["status"] == "converged":
-            # converged where the oracle did not: the residual test itself must hold
+        if r["status"] == "converged":
+            # the residual test itself must hold
             assert r["rnorm"] <= 2.0 ** -52 * np.max(np.abs(b))
+        cls, st = _judge(A, b, x, r, tf)
+        compared += cls == "conv"
+        status_cmp += st
+    # most members are away from the boundary of their TF: most compare
+    assert compared >= 0.8 * len(ns) and status_cmp >= 0.8 * len(ns), (compared, status_cmp)
 
 
 def test_batch_edge_sizes_low_precision(ctx):
@@ -127,14 +147,12 @@ def test_batch_failures_are_per_system(ctx):
     As[2][5, 7] = np.nan                                  # non-finite input
     bs[3] = bs[3].copy()
     bs[3][0] = np.inf
-    xs, res = _run(ctx, As, bs, "f16")
+    xs, res = _run(ctx, As, bs, "f16", term=ir.default_term(litmax=LITMAX_LP))
     # the healthy systems are solved as if alone
     for i in (0,):
         assert res[i]["status"] != "failed"
         assert _same(res[i]["rnorm"], _rnorm_of(As[i], bs[i], xs[i]))
-        o = O.ir_solve(As[i], bs[i], O.F16, nb=64)
-        if _clearly_converged(o):
-            assert res[i]["status"] == "converged"
+        assert _judge(As[i], bs[i], xs[i], res[i], "f16") == ("conv", True)
     assert res[1]["status"] == "failed" and res[1]["info"] == 1 and not res[1]["nonfinite"]
     assert res[2]["status"] == "failed" and res[2]["nonfinite"]
     assert res[3]["status"] == "failed" and res[3]["nonfinite"]
@@ -167,7 +185,7 @@ def full_batch():
 def test_full_batch_2000_systems(ctx, full_batch, tf):
     ns, alphas, As, bs = full_batch
     Ad, bd = _upload(As, bs)
-    plan = ctx.batch(Ad, bd, tf=tf)
+    plan = ctx.batch(Ad, bd, tf=tf, term=ir.default_term(litmax=LITMAX_LP))
     plan.run()
     torch.cuda.synchronize()
     res = plan.results()
@@ -187,19 +205,24 @@ def test_full_batch_2000_systems(ctx, full_batch, tf):
                     for A, b, x, r in zip(As, bs, xs, res)])
     for i in np.argsort(err)[-3:]:
         if err[i] > 1e-8:
-            o = O.ir_solve(As[i], bs[i], TF[tf], nb=64)
-            assert not _clearly_converged(o), (i, ns[i], alphas[i], err[i])
+            o = O.ir_solve(As[i], bs[i], TF[tf], O.Term(litmax=LITMAX_LP), nb=64)
             xo = o.sol.astype(np.float64)
             xr = O.reference_solution(As[i], bs[i])
+            assert P.classify(o, O.rel_err_inf(xo, xr) <= P.bar(O.cond_inf(As[i]))) != "conv", (i, err[i])
             assert O.rel_err_inf(xo, xr) > 1e-10, (i, err[i])
-    # a sample against the oracle's own IR
+    # a sample against the oracle's own IR: status wherever the member is away from
+    # the convergence boundary, x wherever the oracle's x meets the bar
     g = np.random.Generator(np.random.PCG64(77))
-    for i in g.choice(len(ns), size=12, replace=False):
-        o = O.ir_solve(As[i], bs[i], TF[tf], nb=64)
-        if _clearly_converged(o):
-            assert res[i]["status"] == "converged", (i, ns[i], alphas[i])
-            tol = O.parity_tol(O.cond_inf(As[i]), O.F64)
-            assert np.max(np.abs(xs[i] - o.sol)) <= tol * np.max(np.abs(o.sol))
+    sample = g.choice(len(ns), size=40, replace=False)
+    compared = status_cmp = 0
+    for i in sample:
+        cls, st = _judge(As[i], bs[i], xs[i], res[i], tf)
+        compared += cls == "conv"
+        status_cmp += st
+    # a quarter of these systems have alpha close to a singular mode (kappa up to
+    # ~1e5); bfloat16's convergence boundary (kappa u_F ~ 1) cuts into them
+    frac = 0.8 if tf == "f16" else 0.7
+    assert compared >= frac * len(sample) and status_cmp >= 0.8 * len(sample), (compared, status_cmp)
     # a replay from a CUDA graph gives the same bits
     first = [x.clone() for x in plan.xs]
     graph = torch.cuda.CUDAGraph()
@@ -233,16 +256,17 @@ def test_batch_autotune_picks_a_candidate_and_keeps_parity(ctx):
     the tuned plan's results still meet the oracle bar (the SIMT and tensor-core
     updates round the same operands to TF)."""
     _, As, bs = irgen.case_batch_sizes([48, 130, 200, 257, 384, 512, 96, 300], seed=31)
-    plan = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16", autotune=True)
+    plan = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16", autotune=True,
+                     term=ir.default_term(litmax=LITMAX_LP))
     grid, tcm = plan.schedule()
     assert grid >= 1 and tcm in (64, 128, 192, 256, 1 << 20)
     plan.run()
     res = plan.results()
+    compared = 0
     for A, b, x, r in zip(As, bs, plan.xs, res):
-        ref = O.ir_solve(A, b, O.F16, nb=64)
-        if ref.status == O.CONVERGED:
-            assert r["status"] in ("converged", "stagnated")
-            assert O.rel_err_inf(x.cpu().numpy(), O.reference_solution(A, b)) <= O.parity_tol(O.cond_inf(A), O.F64)
+        cls, _ = _judge(A, b, x.cpu().numpy(), r, "f16")
+        compared += cls == "conv"
+    assert compared >= 0.8 * len(As), compared
     untuned = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16")
     assert untuned.schedule()[1] == 64
 
@@ -250,14 +274,14 @@ def test_batch_autotune_picks_a_candidate_and_keeps_parity(ctx):
 def test_factor_autotune_schedule(ctx):
     A, b, xt = irgen.case_green_sine(2048)
     f = ctx.factor(dev_colmajor(A), tf="f32", autotune=True)
-    nb, r = f.schedule()
-    assert nb == 64 and r in (8, 12, 16, 24, 32)
+    nb, r, grp = f.schedule()
+    assert nb == 64 and r in (8, 12, 16, 24, 32) and grp == 1
     x, rep = f.solve(dev_vec(b))
     assert rep.status in ("converged", "stagnated")
     assert O.rel_err_inf(x.cpu().numpy(), xt) <= O.parity_tol(1.8e5, O.F64)
     # the binary32 factors do not depend on the schedule (bitwise)
     g = ctx.factor(dev_colmajor(A), tf="f32")
-    assert g.schedule() == (64, 16)
+    assert g.schedule() == (64, 16, 1)
     np.testing.assert_array_equal(f.factors(), g.factors())
     # a second tuned factorization of the same size reuses the context's choice
     h = ctx.factor(dev_colmajor(A), tf="f32", autotune=True)

@@ -75,9 +75,12 @@ def test_ir_matches_oracle(ctx, name, make, tf, term):
     slack = 1 if tf == O.F32 else max(1, ref.iters // 3)
     assert abs(rep.iters - ref.iters) <= slack
     assert rep.rhist[0] == ref.rhist[0]
-    if ref.status == O.CONVERGED or tf == O.F32:
-        assert O.rel_err_inf(x, ref.x) <= tol, (O.rel_err_inf(x, ref.x), tol)
-        assert O.rel_err_inf(x, xr) <= tol, (O.rel_err_inf(x, xr), tol)
+    # every case here is one where the oracle's own IR meets the bar against x_ref
+    # (whatever its stopping rule: these runs end by eq. (stag) at the rounding
+    # floor), so the GPU's x is always compared, with both
+    assert O.rel_err_inf(ref.x, xr) <= tol, (name, O.rel_err_inf(ref.x, xr), tol)
+    assert O.rel_err_inf(x, ref.x) <= tol, (O.rel_err_inf(x, ref.x), tol)
+    assert O.rel_err_inf(x, xr) <= tol, (O.rel_err_inf(x, xr), tol)
 
 
 def test_ir_promoted_single_single_double(ctx):
