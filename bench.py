@@ -1,36 +1,45 @@
 #!/usr/bin/env python3
 """Benchmark: time to solution of mixed-precision iterative refinement on GB300.
 
-Workload (one system per step, inputs resident in HBM): the Green's-function
-system of the paper's Sec. 2 at N = 4096, A = I - 800 G (midpoint rule),
-x_true = sin(pi x), b = A x_true; TW = binary64, TF = binary32 (tensor-core
-TF32 trailing update reported beside it), TR = binary64.  A step is the whole
-hot path: rounded copy of A, blocked LU with partial pivoting, and the
-refinement loop (correction solves, x += d, binary64 residual) until the
-termination rule of Sec. 5.1 holds.
+Headline workload (one system per step, inputs resident in HBM): N = 8192,
+A = N(0,1) entries + 2 sqrt(N) I (seed 1002), b ~ N(0,1); TW = binary64,
+TF = binary16 with A scaled by s = 2^10 / max|a_ij| before the cast (binary32
+accumulation on the tensor cores), TR = binary64.  A step is the whole hot
+path: rounded copy of A, blocked LU with partial pivoting, and the refinement
+loop (correction solves, x += d, binary64 residual) until the termination
+rule of Sec. 5.1 holds.
 
 Metric: milliseconds per solved system (lower is better).  With N GPUs
 (torchrun, one process per GPU) every rank solves its own copy of the system
 ("replicas only": one system does not shard); the value is the slowest
 rank's step time divided by the number of systems solved per step.
 
-Besides the headline it reports: the plain binary64 LU solve (cuSOLVER via
-torch.linalg) on the same system, the LU rate in TFLOP/s, a roofline line for
-the kernel that takes the most time, an end-to-end number through the
-host-buffer entry point, and the CPU oracle timed on the host cores.
-
-The batched workload (2000 systems, N uniform in [32, 512], A = I - alpha G
-+ 1e-3 E with alpha uniform in [1, 800], b = 1; TW = binary64, TF = binary16
-scaled and bfloat16, one persistent launch per batch) is reported in the same
-line under "batched": solves per second, accuracy against binary64 LU
-solutions, and the binary64 LU solve of the same systems (cuSOLVER through
-torch.linalg, systems of equal N stacked) for comparison.
+Beside the headline the line reports: the same system with bfloat16 factors;
+the plain binary64 LU solve (cuSOLVER via torch.linalg) and the binary32
+cuSOLVER LU solve on the same system; the LU rate in TFLOP/s; the roofline of
+the tensor-core trailing update against the dtype's measured tensor peak; the
+panel's share of the factorization; accuracy against the oracle's binary64
+solution x_ref and the oracle's own refinement; an end-to-end number through
+the host-buffer entry point; the CPU oracle timed on the host cores; and
+lines for the other workloads:
+  * N = 256 Green's system I - G (b = 1, ||r|| <= 1e-13 ||b||), binary32
+    factors, in microseconds (launch and latency bound);
+  * N = 4096 Green's system I - 800 G, x_true = sin(pi x), binary32 factors
+    (SIMT update, bitwise the unblocked LU) and TF32 tensor-core factors;
+  * N = 8192 A = U diag(s) V^T, s geometric from 1 to 1e-6, TW = TF = binary32,
+    TR = binary64 (the promoted problem);
+  * the batch of 2000 systems, N uniform in [32, 512], A = I - alpha G
+    + 1e-3 E (alpha uniform in [1, 800]), b = 1, binary16 (scaled) and
+    bfloat16 factors, one persistent launch per batch;
+  * GMRES-IR and BiCGSTAB-IR with binary16 factors on the N = 4096 Green's
+    system, where plain IR with the same factors does not converge.
 
 `--impl reference` times the CPU oracle instead (the reference arm).
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -41,15 +50,13 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_DEFAULT = 4096
+N_DEFAULT = 8192
+SEED_GAUSS = 1002          # seed of the headline system
+SEED_SVD = 1003
 ALPHA = 800.0
+NB = 64
 L2_FLUSH_BYTES = 512 * 1024 * 1024
-
-# Algorithmic work per launcher call (for the roofline line).
-#   panel:     the N x nb rank-1 updates of a panel, 2 * sum_k (M - k)(nb - k) flops
-#   gemm_*:    2 m^2 nb flops (trailing update of an m x m block, K = nb)
-#   residual:  N^2 * sizeof(TW) bytes of A read once
-#   trsv_pair: N^2 * 4 bytes of factors read once (L and U)
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 
 
 def parse():
@@ -58,37 +65,63 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--n", type=int, default=N_DEFAULT)
+    ap.add_argument("--order", dest="n", type=int, default=N_DEFAULT, help="order N of the headline system")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-fp64", action="store_true",
-                    help="skip the binary64 cuSOLVER comparators (e.g. under a profiler)")
+                    help="skip the cuSOLVER comparators (e.g. under a profiler)")
+    ap.add_argument("--no-oracle", action="store_true",
+                    help="skip the oracle's reference solutions (accuracy fields become null)")
+    ap.add_argument("--no-extra", action="store_true", help="skip the N = 256 / 4096 / kappa = 1e6 lines")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES-IR / BiCGSTAB-IR lines")
     return ap.parse_args()
 
 
-# DRAM bytes (read + written) of one k_panel launch from the ncu capture summarised
-# in profiles/k_panel_green_N4096.md (the 21st panel of N = 4096: 2816 rows), and
-# the SHA-256 of the kernel source it was taken on; the traffic is reported only
-# while the source is unchanged, scaled to the average launch by its rows (the
-# panel reads each of its rows once).
-PANEL_TRAFFIC = {"sha256": "a99d0a37d965bbb824be2b60acf53b80c644ea8400fed5db6cf1279e84823ee6",
-                 "bytes": 755968.0, "rows": 2816}
+# Algorithmic work per unit (the roofline's numerators):
+#   trailing update:  2 m^2 nb flops per block step (m = trailing order, K = nb),
+#                     summed over the factorization: ~2 N^3 / 3
+#   panel:            2 sum_k (M - k)(nb - k) flops per panel (latency bound: reported
+#                     as a share of the factorization, not as a roofline)
+#   residual:         N^2 sizeof(TW) bytes of A (and 2 N^2 binary64 flops)
+#   correction solve: N^2 x 4 bytes of binary32 factors (L and U)
+#   cast:             N^2 (sizeof(TW) + 4) bytes
+
+def trailing_update_flops(n, nb=NB):
+    return float(sum(2.0 * (n - j - nb) ** 2 * nb for j in range(0, n - nb, nb)))
 
 
-def panel_traffic_per_launch(n, nb=64):
-    import hashlib
-    src = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2311_14616_gb300", "csrc", "k_panel.cu")
+def group_update_flops(n, group, nb=NB):
+    """Flops of the tensor-core factorization's group updates (k_gemm_tc with all
+    of a group's slots): for every group of `group` block steps with far columns,
+    the rows below the group times the far columns times K = nb * group."""
+    W, f = nb * group, 0.0
+    for c0 in range(0, n, W):
+        c1 = min(c0 + W, n)
+        near_end = min(c1 + nb, n)
+        if near_end < n:
+            f += 2.0 * (n - c1) * (n - near_end) * (c1 - c0)
+    return f
+
+
+def lu_flops(n):
+    return 2.0 * n ** 3 / 3.0
+
+
+def traffic_per_launch(kernel):
+    """DRAM bytes (read + written) per launch of `kernel` from the committed ncu
+    summary record, while the kernel's source is the one it was captured on."""
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+        with open(TRAFFIC_FILE) as f:
+            rec = json.load(f)[kernel]
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            digest = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, KeyError, ValueError):
         return None
-    if digest != PANEL_TRAFFIC["sha256"]:
+    if digest != rec.get("sha256"):
         return None
-    rows = [n - j for j in range(0, n, nb)]
-    return PANEL_TRAFFIC["bytes"] * (sum(rows) / len(rows)) / PANEL_TRAFFIC["rows"]
+    return float(rec["bytes_per_launch"])
 
 
 def load_peaks():
@@ -186,28 +219,14 @@ def max_over_ranks(v, ws):
     return float(t.item())
 
 
-def make_inputs(n):
+def headline_inputs(n):
     import irgen
-    A, b, xt = irgen.case_green_sine(n, ALPHA)
-    return A, b, xt
+    return irgen.case_gaussian(n, SEED_GAUSS)
 
 
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle
 # ---------------------------------------------------------------------------
-
-def oracle_sample_time(n_full, sample_n):
-    """Oracle IR (binary32 factorization, binary64 residual) on the host cores for
-    the same workload at N = sample_n; time scaled by (n_full / sample_n)^3 (the
-    LU's N^3 term dominates)."""
-    import oracle as O
-    A, b, _ = make_inputs(sample_n)
-    t0 = time.perf_counter()
-    res = O.ir_solve(A, b, O.F32, nb=64)
-    dt = time.perf_counter() - t0
-    scale = (n_full / sample_n) ** 3
-    return dt * scale * 1e3, res, dt
-
 
 def cpu_cores():
     try:
@@ -216,32 +235,52 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def oracle_solve_ms(A, b, tf):
+    """One oracle IR solve (emulated-TF LU, binary32 solves, binary64 residual) on
+    the host cores: (milliseconds, result)."""
+    import oracle as O
+    t0 = time.perf_counter()
+    res = O.ir_solve(A, b, tf, nb=NB)
+    return (time.perf_counter() - t0) * 1e3, res
+
+
 def run_reference(args):
+    """The oracle on the headline workload: every timed step is one complete
+    oracle solve of the N x N system (no sampling, no scaling); the warm-up
+    steps solve an N/8 instance of the same recipe (they only start the
+    OpenMP pool and page the library in)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    import oracle as O
     cores = cpu_cores()
     os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-    sample_n = min(args.n, 2048)
-    times = []
-    for i in range(args.warmup + args.steps):
-        ms, _, _ = oracle_sample_time(args.n, sample_n)
-        if i >= args.warmup:
-            times.append(ms)
+    n = args.n
+    A, b = headline_inputs(n)
+    Aw, bw = headline_inputs(max(1, n // 8))
+    for _ in range(args.warmup):
+        oracle_solve_ms(Aw, bw, O.F16)
+    times = [oracle_solve_ms(A, b, O.F16)[0] for _ in range(args.steps)]
     v = statistics.mean(times)
-    sample = (f"oracle IR (binary32 LU, binary64 residual) at N={sample_n} of the same workload, "
-              f"time x (N/{sample_n})^3")
+    sample = (f"one complete oracle IR solve of the N={n} system per timed step (binary16 factors emulated: "
+              f"binary32 panel and U12, TF-rounded update operands, exact products summed in binary64; "
+              f"binary32 solves; binary64 residual); warm-up steps solve an N={max(1, n // 8)} instance")
     out = {
         "impl": "reference", "metric": "ir_solve_ms", "value": v, "unit": "ms", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": f"green_sine_N{args.n}_alpha800_TWf64_TFf32_TRf64", "n": args.n,
-                   "alpha": ALPHA},
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16/f32/f64", "data": "synthetic",
+        "config": headline_config(n),
         "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(out), flush=True)
+
+
+def headline_config(n):
+    return {"workload": f"gauss_shift_N{n}_seed{SEED_GAUSS}_TWf64_TFf16scaled_TRf64", "n": n,
+            "A": "N(0,1) entries + 2 sqrt(N) I", "b": "N(0,1)", "TW": "f64", "TF": "f16 (s = 2^10/max|a|)",
+            "TR": "f64", "l2": "flushed by a 512 MiB write before every timed step"}
 
 
 # ---------------------------------------------------------------------------
@@ -431,12 +470,13 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = args.n
-    A, b, xt = make_inputs(n)
+    A, b = headline_inputs(n)
     A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()        # column-major
     b_d = torch.from_numpy(b).to(dev)
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
     ctx = ir.Context(local)
     stream = torch.cuda.current_stream(dev)
+    peaks = load_peaks()
 
     def timed_steps(step_fn, steps, warmup, profile=False):
         for _ in range(warmup):
@@ -462,139 +502,126 @@ def main():
         ms = [a.elapsed_time(z) for a, z in ev]
         return ms, out, prof, launches
 
-    # --- headline: TF = binary32 (bit-exact FP32 LU), default termination
-    fact32 = ctx.factor(A_d, tf="f32", autotune=True)     # schedule timed on this A before the run
-    x32 = torch.empty_like(b_d)
+    def rel(x, ref):
+        if ref is None:
+            return None
+        x = x.double().cpu().numpy() if hasattr(x, "cpu") else np.asarray(x, dtype=np.float64)
+        return float(np.max(np.abs(x - ref)) / np.max(np.abs(ref)))
+
+    oracle_ok = rank == 0 and ws == 1 and not args.no_oracle
+    if oracle_ok:
+        import oracle as O
+        os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
+
+    # --- headline: TF = binary16 (scaled), tensor-core trailing update
+    fact = ctx.factor(A_d, tf="f16", autotune=True)      # schedule timed on this A before the run
+    sched16 = fact.schedule()
+    x16 = torch.empty_like(b_d)
     term = ir.default_term()
 
-    def step32():
-        fact32.refactor(A_d)
-        return fact32.solve(b_d, x32, term)[1]
+    def step16():
+        fact.refactor(A_d)
+        return fact.solve(b_d, x16, term)[1]
 
     clocks = ClockSampler(local)
     clocks.start()
-    ms32, rep32, prof32, _ = timed_steps(step32, args.steps, args.warmup, profile=True)
-    # unprofiled repeat: the headline number carries no event overhead (and runs the
-    # lookahead schedule, which per-launcher profiling turns off); its launches are
-    # the ones reported
-    ms32_plain, rep32, _, launches = timed_steps(step32, args.steps, 1)
+    ms16, rep16, _, launches = timed_steps(step16, args.steps, args.warmup)
     clk = clocks.stop()
-    t32 = max_over_ranks(statistics.mean(ms32_plain), ws)
+    t16 = max_over_ranks(statistics.mean(ms16), ws)
+    # the factorization alone (graph replay of the lookahead schedule)
+    ms_fac, _, _, _ = timed_steps(lambda: fact.refactor(A_d), args.steps, 1)
+    t_fac = max_over_ranks(statistics.mean(ms_fac), ws)
+    # per-launcher CUDA events (kernels issued one after another, no lookahead):
+    # the per-kernel breakdown and the roofline's launch times
+    _, _, prof16, _ = timed_steps(step16, args.steps, 1, profile=True)
+    kms = {k: v[0] / args.steps for k, v in sorted(prof16.items())}
+    kcalls = {k: v[1] / args.steps for k, v in sorted(prof16.items())}
+    x16h = x16.double().cpu().numpy()
 
-    # --- tensor-core arm: TF = TF32, litmax raised so IR reaches its limiting accuracy
-    fact_tc = ctx.factor(A_d, tf="tf32", autotune=True)
-    xtc = torch.empty_like(b_d)
-    term_tc = ir.default_term(litmax=30)
+    # --- the same system with bfloat16 factors (unscaled)
+    factb = ctx.factor(A_d, tf="bf16", autotune=True)
+    xb = torch.empty_like(b_d)
 
-    def step_tc():
-        fact_tc.refactor(A_d)
-        return fact_tc.solve(b_d, xtc, term_tc)[1]
+    def stepb():
+        factb.refactor(A_d)
+        return factb.solve(b_d, xb, term)[1]
 
-    ms_tc, rep_tc, prof_tc, _ = timed_steps(step_tc, max(3, args.steps // 2), 1, profile=True)
-    t_tc = max_over_ranks(statistics.mean(ms_tc), ws)
+    msb, repb, _, _ = timed_steps(stepb, max(3, args.steps // 2), 1)
+    tb = max_over_ranks(statistics.mean(msb), ws)
+    factb.destroy()
 
-    # --- binary64 LU solve (cuSOLVER through torch.linalg) on the same system
+    # --- cuSOLVER LU solves of the same system (torch.linalg): binary64, and binary32 as a yardstick
     A_row = torch.from_numpy(np.ascontiguousarray(A)).to(dev)
-
-    def step64():
-        LU, piv = torch.linalg.lu_factor(A_row)
-        return torch.linalg.lu_solve(LU, piv, b_d.unsqueeze(1))
-
-    if args.no_fp64:
-        t64, x64 = None, None
-    else:
-        ms64, x64, _, _ = timed_steps(step64, max(3, args.steps // 2), 1)
+    t64 = t32 = t32f = None
+    x64h = None
+    if not args.no_fp64:
+        def step64():
+            LU, piv = torch.linalg.lu_factor(A_row)
+            return torch.linalg.lu_solve(LU, piv, b_d.unsqueeze(1))
+        ms64, x64, _, _ = timed_steps(step64, max(3, args.steps // 4), 1)
         t64 = max_over_ranks(statistics.mean(ms64), ws)
-
-    # --- accuracy against the closed form and the binary64 LU solution
-    xg = x32.double().cpu().numpy()
-    err_true = float(np.max(np.abs(xg - xt)) / np.max(np.abs(xt)))
-    err_vs_lu64 = None
-    if x64 is not None:
         x64h = x64.squeeze(1).cpu().numpy()
-        err_vs_lu64 = float(np.max(np.abs(xg - x64h)) / np.max(np.abs(x64h)))
-    err_tc_true = float(np.max(np.abs(xtc.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
+        A32 = A_row.float()
+        b32 = b_d.float().unsqueeze(1)
+        ms32, _, _, _ = timed_steps(lambda: torch.linalg.lu_solve(*torch.linalg.lu_factor(A32), b32),
+                                    max(3, args.steps // 2), 1)
+        t32 = max_over_ranks(statistics.mean(ms32), ws)
+        ms32f, _, _, _ = timed_steps(lambda: torch.linalg.lu_factor(A32), max(3, args.steps // 2), 1)
+        t32f = max_over_ranks(statistics.mean(ms32f), ws)
+        del A32, b32
 
-    # --- roofline of the kernel kind with the largest share of the profiled step
-    peaks = load_peaks()
-    total_prof = sum(v[0] for v in prof32.values())
-    dom = max(prof32, key=lambda k: prof32[k][0])
-    nb = 64
-    dom_ms, dom_calls = prof32[dom]
-    avg_ms = dom_ms / dom_calls
-    sm_mhz = clk.get("sm_mhz") or 2070.0
-    fp32_peak_tflops = 152 * 128 * 2 * 2070e6 / 1e12   # SMs x FP32 lanes x FMA x max clock
-    if dom == "panel":
-        flops = sum(2 * sum((n - j - k) * (min(nb, n - j) - k) for k in range(min(nb, n - j)))
-                    for j in range(0, n, nb)) / dom_calls
-        roof = {"bound": "alu", "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "kernel": "k_panel"}
-    elif dom in ("gemm_simt", "gemm_tc"):
-        flops = sum(2 * (n - j - nb) ** 2 * nb for j in range(0, n - nb, nb)) / dom_calls
-        peak = fp32_peak_tflops if dom == "gemm_simt" else peaks["bf16_tflops"] * 1.1 / 2.25
-        roof = {"bound": "alu" if dom == "gemm_simt" else "tensor",
-                "achieved": flops / (avg_ms * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
-                "kernel": "k_" + dom}
-    elif dom == "residual":
-        roof = {"bound": "hbm", "achieved": n * n * 8 / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "kernel": "k_resid_partial+k_resid_final"}
-    else:
-        roof = {"bound": "hbm", "achieved": n * n * 4 / (avg_ms * 1e-3) / 1e9, "peak": peaks["hbm_gbs"],
-                "unit": "GB/s", "kernel": "k_" + dom}
-    roof["frac"] = roof["achieved"] / roof["peak"]
-    roof["traffic"] = panel_traffic_per_launch(n) if dom == "panel" else None   # bytes per launch
-    roof["peak_source"] = peaks["source"] if roof["bound"] != "alu" else "unit counts x 2070 MHz"
-    roof["share_of_step"] = dom_ms / total_prof
-    roof["avg_launch_ms"] = avg_ms
+    # --- the oracle: x_ref (binary64 LU solve refined with extended residuals) and
+    # its own binary16 refinement, timed on the host cores (the CPU baseline)
+    xr = None
+    cpu = None
+    acc = {"rel_err_vs_x_ref": None, "rel_err_vs_oracle_ir": None, "rel_err_vs_fp64_lu": rel(x16h, x64h)}
+    if oracle_ok:
+        xr = O.reference_solution(A, b)
+        kappa = float(np.linalg.cond(A, np.inf))
+        bar = max(1e-12, 10.0 * kappa * 2.0 ** -52)
+        if not args.no_cpu_baseline:
+            ms_cpu, ores = oracle_solve_ms(A, b, O.F16)
+            cpu = {"value": ms_cpu, "unit": "ms", "cores": cpu_cores(), "kind": "oracle",
+                   "sample": f"one complete oracle IR solve of the same N={n} system (binary16 factors emulated; "
+                             f"{ores.iters} iterations, status {O.STATUS_NAMES[ores.status]})"}
+            acc["rel_err_vs_oracle_ir"] = rel(x16h, ores.x)
+            acc["oracle_ir"] = {"iters": ores.iters, "status": O.STATUS_NAMES[ores.status],
+                                "rel_err_vs_x_ref": rel(ores.x, xr)}
+        e = rel(x16h, xr)
+        acc.update({"rel_err_vs_x_ref": e, "kappa_inf": kappa, "parity_bar": bar,
+                    "parity_bar_met": e <= bar, "literal_1e-12_met": e <= 1e-12,
+                    "bf16_rel_err_vs_x_ref": rel(xb, xr)})
 
-    # --- a roofline line for every kernel kind of the step (the dominant one is the latency-bound panel)
-    def dgemm_rate():
-        G = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
-        torch.matmul(G, G)
-        torch.cuda.synchronize()
-        best = None
-        for _ in range(3):
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            torch.matmul(G, G)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            t_ = e0.elapsed_time(e1)
-            best = t_ if best is None else min(best, t_)
-        return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+    # --- roofline: the tensor-core trailing update at the binary16 tensor peak
+    roof = tensor_roofline(prof16, args.steps, n, peaks, sched16[2])
 
-    fp64_tflops = dgemm_rate()
-    tf32_peak = peaks["bf16_tflops"] * 1.1 / 2.25
-    n_iter = rep32.iters
+    # --- a line for every other kernel kind of the step
+    fp64_tflops = dgemm_rate(torch, dev, stream)
+    iters = rep16.iters
     kr = {}
 
-    def line(kind, prof, steps, bound, work, peak, unit, note):
-        if kind not in prof:
+    def line(kind, bound, work, peak, unit, note):
+        if kind not in prof16:
             return
-        ms_, calls = prof[kind]
-        rate = work / (ms_ / steps * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        ms_ = prof16[kind][0] / args.steps
+        rate = work / (ms_ * 1e-3) / (1e12 if unit == "TFLOP/s" else 1e9)
         kr[kind] = {"bound": bound, "achieved": rate, "peak": peak, "unit": unit, "frac": rate / peak,
-                    "ms_per_step": ms_ / steps, "calls_per_step": calls / steps, "work": note}
+                    "ms_per_step": ms_, "calls_per_step": kcalls[kind], "work": note}
 
-    gemm_flops = sum(2 * (n - j - nb) ** 2 * nb for j in range(0, n - nb, nb))
-    line("gemm_simt", prof32, args.steps, "alu", gemm_flops, fp32_peak_tflops, "TFLOP/s",
-         "2 m^2 nb flops per block step, binary32 FMA pipe (unit counts x 2070 MHz)")
-    tc_steps = max(3, args.steps // 2)
-    line("gemm_tc", prof_tc, tc_steps, "tensor", gemm_flops, tf32_peak, "TFLOP/s",
-         "2 m^2 nb flops per block step, TF32 peak = measured bf16 x 1.1/2.25")
-    line("residual", prof32, args.steps, "alu", 2.0 * n * n * n_iter, fp64_tflops, "TFLOP/s",
+    gflops = group_update_flops(n, sched16[2]) if "gemm_tc_group" in prof16 else 0.0
+    line("gemm_tc", "tensor", trailing_update_flops(n) - gflops, peaks["bf16_tflops"], "TFLOP/s",
+         "single block steps (K = 64): the near columns and the group's own rows; 2 m_rows m_cols 64 flops each")
+    line("residual", "alu", 2.0 * n * n * iters, fp64_tflops, "TFLOP/s",
          "2 N^2 flops per residual on the binary64 pipe; peak = measured binary64 GEMM rate")
-    line("trsv_pair", prof32, args.steps, "hbm", 4.0 * n * n * n_iter, peaks["hbm_gbs"], "GB/s",
-         "N^2 x 4 B of factors (L and U) per correction solve")
-    line("cast", prof32, args.steps, "hbm", 12.0 * n * n, peaks["hbm_gbs"], "GB/s",
-         "N^2 x (8 B read + 4 B written)")
-
-    # --- LU rate of the headline path (2 N^3 / 3 flops over factor time = cast + LU kernels)
-    lu_kinds = ("cast", "iota", "panel", "laswp", "trsm", "gemm_simt", "diag_inv")
-    lu_ms = sum(prof32[k][0] for k in lu_kinds if k in prof32) / args.steps
-    lu_tflops = (2.0 * n ** 3 / 3.0) / (lu_ms * 1e-3) / 1e12
-    lu_tc_ms = sum(prof_tc[k][0] for k in ("cast", "iota", "panel", "laswp", "trsm", "gemm_tc", "diag_inv")
-                   if k in prof_tc) / max(3, args.steps // 2)
+    line("trsv_pair", "hbm", 4.0 * n * n * iters, peaks["hbm_gbs"], "GB/s",
+         "N^2 x 4 B of binary32 factors (L and U) per correction solve")
+    line("cast", "hbm", 12.0 * n * n, peaks["hbm_gbs"], "GB/s", "N^2 x (8 B read + 4 B written)")
+    lu_kinds = ("maxabs", "cast", "iota", "panel", "laswp", "trsm", "gemm_tc", "diag_inv")
+    lu_prof_ms = sum(kms.get(k, 0.0) for k in lu_kinds)
+    panel_share = {"panel_ms_per_factorization": kms.get("panel"),
+                   "share_of_factorization_serial": (kms.get("panel", 0.0) / lu_prof_ms) if lu_prof_ms else None,
+                   "note": "latency bound (one cluster-wide pivot search per column); with lookahead the "
+                           "trailing update runs beside it"}
 
     # --- end to end through the host-buffer entry point (copies inside the timed region)
     e2e = None
@@ -602,7 +629,7 @@ def main():
         A_h = torch.from_numpy(np.ascontiguousarray(A.T)).t().pin_memory()
         b_h = torch.from_numpy(b).pin_memory()
         for _ in range(2):
-            ctx.solve_host(A_h, b_h, tf="f32")
+            ctx.solve_host(A_h, b_h, tf="f16")
         torch.cuda.synchronize()
         barrier(ws)
         t_e = []
@@ -610,99 +637,42 @@ def main():
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            ctx.solve_host(A_h, b_h, tf="f32")
+            ctx.solve_host(A_h, b_h, tf="f16")
             t_e.append((time.perf_counter() - t0) * 1e3)
         e2e = {"value": max_over_ranks(statistics.mean(t_e), ws) / ws, "unit": "ms",
                "h2d_bytes_per_step": int(n * n * 8 + n * 8), "d2h_bytes_per_step": int(n * 8),
                "api": "ir_solve_host (pinned host A, b: copies in, factor, refine, copy back; the context keeps "
                       "its device buffers and factorization across calls of the same shape)"}
+        del A_h, b_h
 
-    # --- CPU oracle on the host cores (rank 0, one GPU only)
-    cpu = None
-    acc_oracle = None
-    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cores = cpu_cores()
-        os.environ.setdefault("OMP_NUM_THREADS", str(cores))
-        sample_n = min(n, 2048)
-        ms_cpu, res, dt = oracle_sample_time(n, sample_n)
-        cpu = {"value": ms_cpu, "unit": "ms", "cores": cores, "kind": "oracle",
-               "sample": f"one oracle IR solve of the same workload at N={sample_n} "
-                         f"({dt:.2f} s), scaled by (N/{sample_n})^3"}
-
+    fact.destroy()
+    del A_row
+    extra = None if args.no_extra else run_extra(args, ctx, dev, stream, flush, ws, rank, timed_steps, rel,
+                                                 oracle_ok)
     batched = None if args.no_batch else run_batched(args, ctx, dev, stream, flush, ws, rank)
+    gmres = None if args.no_gmres else run_krylov(args, ctx, dev, ws, timed_steps)
 
-    # --- GMRES-IR (Sec. 4.3) with binary16 factors on the same system, where plain IR
-    # with the same factors does not converge
-    gmres = None
-    if not args.no_gmres:
-        fact16 = ctx.factor(A_d, tf="f16")
-        fact16.gmres_reserve(10)
-        xg16 = torch.empty_like(b_d)
-        x16 = torch.empty_like(b_d)
-        kopts = ir.krylov_opts()
-
-        def step_gm():
-            fact16.refactor(A_d)
-            return fact16.solve_gmres(b_d, xg16, term, kopts)[1]
-
-        gsteps = max(3, args.steps // 2)
-        _, _, prof_gm, l_gm = timed_steps(step_gm, gsteps, 1, profile=True)
-        ms_gm, rep_gm, _, _ = timed_steps(step_gm, gsteps, 1)
-        _, rep_ir16 = fact16.solve(b_d, x16, term)
-        rel = lambda v: float(np.max(np.abs(v.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
-        gm_kinds = {k: v[0] / gsteps for k, v in sorted(prof_gm.items())}
-
-        # BiCGSTAB-IR (Sec. 2.3, 4.2) on the same factors and system
-        fact16.bicgstab_reserve()
-        xb16 = torch.empty_like(b_d)
-
-        def step_bi():
-            fact16.refactor(A_d)
-            return fact16.solve_bicgstab(b_d, xb16, term, kopts)[1]
-
-        _, _, prof_bi, l_bi = timed_steps(step_bi, gsteps, 1, profile=True)
-        ms_bi, rep_bi, _, _ = timed_steps(step_bi, gsteps, 1)
-        bicgstab = {
-            "ms": max_over_ranks(statistics.mean(ms_bi), ws), "unit": "ms (refactor + BiCGSTAB-IR solve)",
-            "iters": rep_bi.iters, "status": rep_bi.status, "khist": rep_bi.khist,
-            "rel_err_vs_closed_form": rel(xb16),
-            "kernel_ms_per_step": {k: v[0] / gsteps for k, v in sorted(prof_bi.items())},
-            "gpu_launches_per_step": l_bi / gsteps,
-        }
-        gmres = {
-            "workload": f"green_sine_N{n}_alpha800_TWf64_TFf16_TRf64_basis10",
-            "ms": max_over_ranks(statistics.mean(ms_gm), ws), "unit": "ms (refactor + GMRES-IR solve)",
-            "iters": rep_gm.iters, "status": rep_gm.status, "khist": rep_gm.khist,
-            "rhist": rep_gm.rhist, "rel_err_vs_closed_form": rel(xg16),
-            "ir_same_factors": {"iters": rep_ir16.iters, "status": rep_ir16.status,
-                                "rel_err_vs_closed_form": rel(x16)},
-            "kernel_ms_per_step": gm_kinds,
-            "gpu_launches_per_step": l_gm / gsteps,
-            "bicgstab_ir": bicgstab,
-        }
-
-    value = t32 / ws if ws > 1 else t32
+    value = t16 / ws if ws > 1 else t16
+    cfg = headline_config(n)
+    cfg.update({"parallelism": "replicas" if ws > 1 else "single",
+                "schedule": {"nb": sched16[0], "panel_reserve_sms": sched16[1], "group": sched16[2],
+                             "autotuned": True}})
     out = {
         "metric": "ir_solve_ms", "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t32, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": f"green_sine_N{n}_alpha800_TWf64_TFf32_TRf64", "n": n, "alpha": ALPHA,
-                   "TW": "f64", "TF": "f32", "TR": "f64", "rhs": "b = A sin(pi x)",
-                   "l2": "flushed by a 512 MiB write before every timed step",
-                   "parallelism": "replicas" if ws > 1 else "single",
-                   "schedule": {"nb": fact32.schedule()[0], "panel_reserve_sms": fact32.schedule()[1],
-                                "autotuned": True}},
-        "iters": rep32.iters, "status": rep32.status,
-        "rel_err_vs_closed_form": err_true, "rel_err_vs_fp64_lu": err_vs_lu64,
-        "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": (t64 / t32) if t64 else None,
-        "lu_ms": lu_ms, "lu_tflops": lu_tflops,
-        "tf32_tensor_core": {"ms": t_tc, "iters": rep_tc.iters, "status": rep_tc.status,
-                             "lu_ms": lu_tc_ms, "rel_err_vs_closed_form": err_tc_true,
-                             "litmax": 30,
-                             "kernel_ms_per_step": {k: v[0] / max(3, args.steps // 2)
-                                                    for k, v in sorted(prof_tc.items())}},
-        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in sorted(prof32.items())},
+        "warmup": args.warmup, "ms_per_step": t16, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f16/f32/f64", "data": "synthetic",
+        "config": cfg,
+        "iters": rep16.iters, "status": rep16.status, "rhist": rep16.rhist,
+        "accuracy": acc,
+        "fp64_lu_solve_ms": t64, "speedup_vs_fp64_lu": (t64 / t16) if t64 else None,
+        "fp32_lu_solve_ms": t32, "fp32_lu_factor_ms": t32f,
+        "lu_ms": t_fac, "lu_tflops": lu_flops(n) / (t_fac * 1e-3) / 1e12,
+        "lu_tflops_note": "2 N^3 / 3 over the factorization (cast + LU + diagonal-block inverses, lookahead "
+                          "schedule replayed from its graph)",
+        "bf16": {"ms": tb, "iters": repb.iters, "status": repb.status},
+        "kernel_ms_per_step": kms,
         "roofline": roof,
+        "panel": panel_share,
         "kernel_rooflines": kr,
         "fp64_gemm_tflops": fp64_tflops,
         "e2e": e2e,
@@ -710,14 +680,172 @@ def main():
         "gpu_launches": launches,
         "gpu_launches_per_step": launches / args.steps,
         "clocks": clk,
+        "workloads": extra,
         "batched": batched,
-        "gmres_ir": gmres,
+        "krylov_ir": gmres,
     }
     if rank == 0:
         print(json.dumps(out), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def tensor_roofline(prof, steps, n, peaks, group):
+    """The contract's roofline object for the tensor-core trailing update's group
+    kernel (k_gemm_tc applying a group of block steps to the far trailing
+    columns, the launches that carry most of the update's flops): their
+    algorithmic flops over their summed launch time in one step (per-launcher
+    CUDA events), against the measured dense bf16 tensor peak (binary16 has the
+    same rate).  The single-step launches (K = 64) get their own line.
+    prof: {kind: (total ms, calls)} over `steps` steps."""
+    kind = "gemm_tc_group" if "gemm_tc_group" in prof else "gemm_tc"
+    if kind not in prof:
+        return None
+    g_ms, g_calls = prof[kind][0] / steps, prof[kind][1] / steps
+    flops = group_update_flops(n, group) if kind == "gemm_tc_group" else trailing_update_flops(n)
+    achieved = flops / (g_ms * 1e-3) / 1e12
+    peak = peaks["bf16_tflops"]
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic_per_launch("k_gemm_tc"),
+            "kernel": f"k_gemm_tc ({kind}: binary16 operands, binary32 accumulators in TMEM)",
+            "peak_source": f"{peaks['source']} bf16 dense burst (binary16 has the same tensor rate); "
+                           "the kernel is timed alone (per-launcher events)",
+            "work": "2 m_rows m_cols K flops per launch (K = 64 x group), summed over the factorization",
+            "flops_per_step": flops, "flops_per_launch": flops / g_calls, "avg_launch_ms": g_ms / g_calls,
+            "launches_per_step": g_calls, "ms_per_step": g_ms, "group": group}
+
+
+def dgemm_rate(torch, dev, stream):
+    """Measured binary64 GEMM rate (torch.matmul 4096^3, best of 3): the binary64 pipe's ceiling."""
+    G = torch.randn(4096, 4096, dtype=torch.float64, device=dev)
+    torch.matmul(G, G)
+    torch.cuda.synchronize()
+    best = None
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        torch.matmul(G, G)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t_ = e0.elapsed_time(e1)
+        best = t_ if best is None else min(best, t_)
+    return 2 * 4096 ** 3 / (best * 1e-3) / 1e12
+
+
+def run_extra(args, ctx, dev, stream, flush, ws, rank, timed_steps, rel, oracle_ok):
+    """The other single-system workloads: N = 256 (microseconds), N = 4096 Green's
+    system (binary32 and TF32 factors), N = 8192 promoted problem (kappa = 1e6)."""
+    import numpy as np
+    import torch
+
+    import irgen
+    from paper_2311_14616_gb300 import ir
+    steps = max(3, args.steps // 2)
+    out = {}
+
+    def one(A, b, tf, term, steps_):
+        Ad = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+        bd = torch.from_numpy(np.ascontiguousarray(b)).to(dev)
+        f = ctx.factor(Ad, tf=tf, autotune=True)
+        x = torch.empty_like(bd)
+
+        def step():
+            f.refactor(Ad)
+            return f.solve(bd, x, term)[1]
+        ms, rep, _, _ = timed_steps(step, steps_, 1)
+        msf, _, _, _ = timed_steps(lambda: f.refactor(Ad), steps_, 1)
+        f.destroy()
+        return max_over_ranks(statistics.mean(ms), ws), max_over_ranks(statistics.mean(msf), ws), rep, x
+
+    # N = 256, I - G, b = 1, ||r|| <= 1e-13 ||b||
+    A1, b1 = irgen.case_green(256, 1.0)
+    t1, tf1, rep1, x1 = one(A1, b1, "f32", ir.default_term(abs_rel_tol=1e-13), args.steps)
+    out["green_N256_alpha1_TFf32"] = {
+        "us": t1 * 1e3, "lu_us": tf1 * 1e3, "iters": rep1.iters, "status": rep1.status,
+        "rel_err_vs_x_ref": rel(x1, O_ref(A1, b1)) if oracle_ok else None,
+        "note": "L2-resident and launch/latency bound: absolute microseconds, no roofline fraction"}
+    # N = 4096, I - 800 G, x_true = sin(pi x)
+    A2, b2, xt2 = irgen.case_green_sine(4096, ALPHA)
+    xr2 = O_ref(A2, b2) if oracle_ok else None
+    for tf, litmax in (("f32", 10), ("tf32", 30)):
+        t2, tf2, rep2, x2 = one(A2, b2, tf, ir.default_term(litmax=litmax), steps)
+        e = rel(x2, xr2)
+        out[f"green_sine_N4096_alpha800_TF{tf}"] = {
+            "ms": t2, "lu_ms": tf2, "lu_tflops": lu_flops(4096) / (tf2 * 1e-3) / 1e12,
+            "iters": rep2.iters, "status": rep2.status, "litmax": litmax,
+            "rel_err_vs_closed_form": rel(x2, xt2), "rel_err_vs_x_ref": e,
+            "literal_1e-12_met": (e <= 1e-12) if e is not None else None}
+    # N = 8192, U diag(s) V^T, kappa = 1e6, TW = TF = binary32, TR = binary64
+    A4, b4 = irgen.case_svd(8192, SEED_SVD)
+    t4, tf4, rep4, x4 = one(A4, b4, "f32", ir.default_term(litmax=30), steps)
+    d = {"ms": t4, "lu_ms": tf4, "iters": rep4.iters, "status": rep4.status, "litmax": 30,
+         "TW": "f32", "TF": "f32", "TR": "f64"}
+    if oracle_ok:
+        xr4 = O_ref(A4, b4)
+        k4 = float(np.linalg.cond(A4.astype(np.float64), np.inf))
+        d.update({"rel_err_vs_promoted_x_ref": rel(x4, xr4), "kappa_inf": k4,
+                  "bound_thm_irterm": 4 * (8192 + 1) * k4 * 2.0 ** -52 + 2.0 ** -23})
+    out["svd_N8192_kappa1e6_TWf32_TFf32_TRf64"] = d
+    return out
+
+
+def O_ref(A, b):
+    import oracle as O
+    return O.reference_solution(A, b)
+
+
+def run_krylov(args, ctx, dev, ws, timed_steps):
+    """GMRES-IR (Sec. 4.3) and BiCGSTAB-IR (Sec. 2.3, 4.2) with binary16 factors on the
+    N = 4096 Green's system, where plain IR with the same factors does not converge."""
+    import numpy as np
+    import torch
+
+    import irgen
+    from paper_2311_14616_gb300 import ir
+    A, b, xt = irgen.case_green_sine(4096, ALPHA)
+    A_d = torch.from_numpy(np.ascontiguousarray(A.T)).to(dev).t()
+    b_d = torch.from_numpy(b).to(dev)
+    term = ir.default_term()
+    fact16 = ctx.factor(A_d, tf="f16")
+    fact16.gmres_reserve(10)
+    xg16 = torch.empty_like(b_d)
+    x16 = torch.empty_like(b_d)
+    kopts = ir.krylov_opts()
+    rel = lambda v: float(np.max(np.abs(v.double().cpu().numpy() - xt)) / np.max(np.abs(xt)))
+
+    def step_gm():
+        fact16.refactor(A_d)
+        return fact16.solve_gmres(b_d, xg16, term, kopts)[1]
+
+    gsteps = max(3, args.steps // 2)
+    _, _, prof_gm, l_gm = timed_steps(step_gm, gsteps, 1, profile=True)
+    ms_gm, rep_gm, _, _ = timed_steps(step_gm, gsteps, 1)
+    _, rep_ir16 = fact16.solve(b_d, x16, term)
+    fact16.bicgstab_reserve()
+    xb16 = torch.empty_like(b_d)
+
+    def step_bi():
+        fact16.refactor(A_d)
+        return fact16.solve_bicgstab(b_d, xb16, term, kopts)[1]
+
+    _, _, prof_bi, l_bi = timed_steps(step_bi, gsteps, 1, profile=True)
+    ms_bi, rep_bi, _, _ = timed_steps(step_bi, gsteps, 1)
+    fact16.destroy()
+    return {
+        "workload": "green_sine_N4096_alpha800_TWf64_TFf16_TRf64_basis10",
+        "gmres_ir": {"ms": max_over_ranks(statistics.mean(ms_gm), ws), "unit": "ms (refactor + GMRES-IR solve)",
+                     "iters": rep_gm.iters, "status": rep_gm.status, "khist": rep_gm.khist,
+                     "rel_err_vs_closed_form": rel(xg16),
+                     "kernel_ms_per_step": {k: v[0] / gsteps for k, v in sorted(prof_gm.items())},
+                     "gpu_launches_per_step": l_gm / gsteps},
+        "bicgstab_ir": {"ms": max_over_ranks(statistics.mean(ms_bi), ws),
+                        "unit": "ms (refactor + BiCGSTAB-IR solve)", "iters": rep_bi.iters,
+                        "status": rep_bi.status, "khist": rep_bi.khist, "rel_err_vs_closed_form": rel(xb16),
+                        "kernel_ms_per_step": {k: v[0] / gsteps for k, v in sorted(prof_bi.items())},
+                        "gpu_launches_per_step": l_bi / gsteps},
+        "ir_same_factors": {"iters": rep_ir16.iters, "status": rep_ir16.status, "rel_err_vs_closed_form": rel(x16)},
+    }
 
 
 if __name__ == "__main__":

@@ -86,6 +86,26 @@ typedef struct {
     int nb;               /* outer block size; 0 = default (64) */
     int autotune;         /* 1: tune the schedule on the caller's own input (see
                              ir_fact_schedule / ir_batch_schedule); default 0 */
+    int group;            /* TF32 / bf16 / binary16: block steps whose update of the
+                             far trailing columns is applied at once (1 .. 16;
+                             0 = default 8, or the tuned value with autotune) */
+    int onthefly;         /* 0 (default): low precision solves (LPS) -- binary32
+                             triangular solves of fl32(P r / ||r||), scaled back
+                             (eqs. vdlow / promotevd, Sec. 5.3); 1: mixed
+                             precision solves (MPS, mplu(A; onthefly = true),
+                             Sec. 5.3) -- r is kept in TW and the triangular
+                             solves run in TW on the factors promoted exactly,
+                             with no scaling by ||r||.  Used by ir_solve and
+                             ir_solve_many (GMRES-IR / BiCGSTAB-IR keep their
+                             preconditioner of Sec. 4.3). */
+    int store_tf;         /* TF = IR_F16 / IR_BF16 only: 1 keeps the factors in TF,
+                             as the paper's factorization copy is (Sec. 1, 2.5):
+                             after the factorization every entry of L and U is
+                             rounded to TF once, and the correction solves read
+                             a 2-byte copy of them (half the bytes of binary32
+                             factors) and promote each entry exactly.  0
+                             (default): binary32 factors.  An entry that
+                             overflows TF makes the factorization non-finite. */
 } ir_opts;
 
 #define IR_MAX_HIST 32
@@ -161,6 +181,16 @@ ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda,
 /* One correction solve d = U^{-1} L^{-1} P v in binary32 (eq. vdlow without
  * the scaling): v, d are n binary32 device vectors (may alias). */
 ir_status ir_lu_solve(ir_fact *fact, const float *v, float *d, void *stream);
+
+/* Check of the bounded device waits (the paper has no counterpart): one
+ * thread runs the wait the correction solves use for their inter-block
+ * values, on a value of the factorization's solve workspace that no solve
+ * ever writes, with the time limit limit_s (0 < limit_s <= 2 s, the limit
+ * every product wait uses), and must give up.  Returns IR_ETIMEOUT when the
+ * wait gave up as it should (the flag is then cleared again, so the
+ * factorization and its context stay usable), IR_OK if it did not, IR_EINVAL
+ * for a bad limit.  Synchronizes `stream`.  For tests and diagnostics. */
+ir_status ir_check_wait_timeout(ir_fact *fact, double limit_s, void *stream);
 
 /* Residual r = b - A x in binary64 (Algorithm IR, eq. xferrule: A and b in
  * TW are promoted exactly) and rnorm[0] = ||r||_inf.  A: n x n column-major
@@ -316,14 +346,18 @@ ir_status ir_solve_bicgstab(ir_fact *fact, const void *b, void *x, const ir_term
 
 /* The autotuned schedule (opts.autotune = 1; not in the paper).
  * Single system (n >= 1024): the SMs the lookahead's trailing update leaves
- * free for the next panel's cluster, picked among 8, 12, 16, 24, 32 by timing
- * two factorizations of the caller's A per candidate; remembered by the
- * context per (n, TF).  nb is 64 (the tensor-core K block and the panel
- * width).  Batch (TF = FP16/BF16): the smallest trailing block whose update
- * goes to the tensor cores (64, 128, 192, 256 or never), picked by timing
- * two runs of the planned batch per candidate inside ir_batch_create (x is
- * overwritten; A, b only read).  grid = persistent CTAs (one per SM). */
-ir_status ir_fact_schedule(const ir_fact *fact, int *nb, int *panel_reserve_sms);
+ * free for the next panel's cluster, picked among 8, 12, 16, 24, 32, and for
+ * TF32 / bf16 / binary16 factors the block steps per group whose update of
+ * the far trailing columns is applied at once (4, 8 or 16: K = 256, 512 or
+ * 1024 on the tensor cores), picked by timing two factorizations of the
+ * caller's A per candidate; remembered by the context per (n, TF).  nb is 64
+ * (the tensor-core K block and the panel width).  group is 1 for binary32
+ * factors (every block step updates the whole trailing matrix).  Batch (TF =
+ * FP16/BF16): the smallest trailing block whose update goes to the tensor
+ * cores (64, 128, 192, 256 or never), picked by timing two runs of the
+ * planned batch per candidate inside ir_batch_create (x is overwritten; A, b
+ * only read).  grid = persistent CTAs (one per SM). */
+ir_status ir_fact_schedule(const ir_fact *fact, int *nb, int *panel_reserve_sms, int *group);
 ir_status ir_batch_schedule(const ir_batch *batch, int *grid, int *tc_min_trail);
 
 /* Pivots of the factorization (0-based, n entries) copied to host memory. */

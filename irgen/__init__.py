@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "green_g", "gmat_midpoint", "gmat_trapezoid", "midpoint_nodes",
     "case_green", "case_green_sine", "case_gaussian", "case_svd", "case_batch",
-    "case_random", "case_batch_sizes", "SEED_BASE",
+    "case_random", "case_batch_sizes", "row_dot", "SEED_BASE",
 ]
 
 SEED_BASE = 1000
@@ -67,6 +67,17 @@ def gmat_trapezoid(n: int) -> np.ndarray:
     return np.asfortranarray(h * green_g(x, x))
 
 
+def row_dot(A: np.ndarray, x: np.ndarray) -> np.ndarray:
+    """A x in binary64 as a sequential sum per row in column order (multiply, then
+    add, each rounded): the same bits on every machine, unlike a BLAS product,
+    whose blocking and fused operations depend on the library."""
+    A = np.asarray(A, dtype=np.float64)
+    out = np.zeros(A.shape[0])
+    for j in range(A.shape[1]):
+        out = out + A[:, j] * x[j]
+    return out
+
+
 def case_green(n: int, alpha: float, rule: str = "midpoint", rhs: str = "ones"):
     """A = I - alpha G (Sec. 2).  rhs = 'ones' gives b = 1; 'A1' gives b = A 1."""
     G = gmat_midpoint(n) if rule == "midpoint" else gmat_trapezoid(n)
@@ -74,7 +85,7 @@ def case_green(n: int, alpha: float, rule: str = "midpoint", rhs: str = "ones"):
     if rhs == "ones":
         b = np.ones(n)
     elif rhs == "A1":
-        b = A @ np.ones(n)
+        b = row_dot(A, np.ones(n))
     else:
         raise ValueError(rhs)
     return A, b
@@ -84,7 +95,7 @@ def case_green_sine(n: int, alpha: float = 800.0):
     """A = I - alpha G_mid, x_true_i = sin(pi x_i), b = A x_true."""
     A, _ = case_green(n, alpha)
     xt = np.sin(np.pi * midpoint_nodes(n))
-    return A, A @ xt, xt
+    return A, row_dot(A, xt), xt
 
 
 def case_gaussian(n: int, seed: int):
@@ -115,7 +126,7 @@ def case_svd(n: int, seed: int, kappa: float = 1e6):
     else:
         s = np.ones(n)
     A64 = (U * s) @ V.T
-    b = (A64 @ np.ones(n)).astype(np.float32)
+    b = row_dot(A64, np.ones(n)).astype(np.float32)
     return np.asfortranarray(A64.astype(np.float32)), b
 
 

@@ -296,7 +296,7 @@ def term_decide(rhist, dhist, bnorm: float, eps_w: float, term: Term, tr_wider: 
 
 def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
              nb: int = 0, fp16_scaling: bool = True, tr_wider: Optional[bool] = None,
-             solve: str = "lps") -> IRResult:
+             solve: str = "lps", store_tf: bool = False) -> IRResult:
     """Algorithm IR (Sec. 1) with TR = binary64 and solves in binary32.
 
     1. A_F = round_TF(s A) (s = 2^10/max|a| for TF = binary16, else 1);
@@ -311,6 +311,11 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
     transfers on the fly): r is rounded to TW, not below it, and the triangular
     solves run in TW on the factors promoted to TW (exactly), so there is no
     scaling by ||r||: d = s fl64(U^{-1} L^{-1} P fl_W(r)) evaluated in TW.
+
+    store_tf = True (TF = binary16 or bfloat16): the factors are kept in TF,
+    as the paper's factorization copy is (Sec. 1, the MPArray of Sec. 2.5):
+    after the factorization every entry of L and U is rounded to TF once, and
+    the solves use those values (promoted exactly, as in Sec. 5.3).
     """
     if solve not in ("lps", "mps"):
         raise ValueError(solve)
@@ -325,6 +330,10 @@ def ir_solve(A: np.ndarray, b: np.ndarray, tf: int, term: Optional[Term] = None,
     s = fp16_scale(A) if (tf == F16 and fp16_scaling) else 1.0
     AF = cast(A, tf, s)
     LU, ipiv, info = getrf_tf(AF, tf, nb)
+    if store_tf:
+        if tf not in (BF16, F16):
+            raise ValueError("2-byte factor storage is for TF = binary16 or bfloat16")
+        LU = np.asfortranarray(round_tf(LU, tf).reshape(LU.shape))
     x = np.zeros(n)
     res = IRResult(x=x, sol=x.astype(A.dtype), ipiv=ipiv, LU=LU, scale=s, info=info)
     bnorm = float(np.max(np.abs(b64))) if n else 0.0

@@ -28,11 +28,13 @@ namespace {
 // call on the launching stream, summed per kind when profiling stops.
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
-    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_BI_STEP, KC_N
+    KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_BI_STEP,
+    KC_GEMM_TC_GROUP, KC_PACK, KC_TRSV64, KC_STORE, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
-                                "batched", "gm_orth", "krylov_update", "norm1", "bi_step"};
+                                "batched", "gm_orth", "krylov_update", "norm1", "bi_step",
+                                "gemm_tc_group", "pack", "trsv_pair_f64", "store_tf"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -96,6 +98,7 @@ ir_status cuda_fail(cudaError_t e, const char *what) {
 constexpr int kInfoNone = 0x7F7F7F7F;   // memset(0x7F) pattern: no zero pivot
 constexpr int kSwapListInts = 1 + 4 * kPanelNB;
 constexpr int kPanelReserveSMs = 16;     // SMs the trailing update leaves to the next panel
+constexpr int kDefaultGroup = 8;         // block steps per group of the tensor-core LU (K = 512 far updates)
 
 bool tw_ok(ir_dtype t) { return t == IR_F64 || t == IR_F32; }
 bool tf_ok(ir_dtype t) { return t == IR_F32 || t == IR_TF32 || t == IR_BF16 || t == IR_F16; }
@@ -140,6 +143,18 @@ void free_fact(ir_fact *f) {
     cudaFree(f->swap_list);
     cudaFree(f->Aop);
     cudaFree(f->Bop);
+    cudaFree(f->Agrp);
+    cudaFree(f->Bgrp);
+    cudaFree(f->y64);
+    cudaFree(f->z64);
+    cudaFree(f->mps_flags);
+    cudaFree(f->AF16);
+    cudaFree(f->xm);
+    cudaFree(f->rm);
+    cudaFree(f->bm);
+    cudaFree(f->mtags);
+    cudaFree(f->mscal);
+    if (f->host_mscal) cudaFreeHost(f->host_mscal);
     cudaFree(f->Linv);
     cudaFree(f->Uinv);
     cudaFree(f->tags);
@@ -173,6 +188,7 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     f->fp16_scale = o->fp16_scale;
     f->nb = kPanelNB;
     f->reserve_sms = kPanelReserveSMs;
+    f->group = kDefaultGroup;
     f->ldf = ((n > 0 ? n : 1) + 31) / 32 * 32;
     const int64_t nn = n > 0 ? n : 1;
     const int64_t nblk = (nn + kTrsvB - 1) / kTrsvB;
@@ -185,15 +201,31 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     AL(f->AF, (size_t)nn * f->ldf * sizeof(float));
     AL(f->ipiv, nn * sizeof(int32_t));
     AL(f->perm, nn * sizeof(int32_t));
-    AL(f->swap_list, 2 * kSwapListInts * sizeof(int32_t));
+    AL(f->swap_list, 2 * kMaxGroup * kSwapListInts * sizeof(int32_t));
     if (o->TF != IR_F32) {
         AL(f->Aop, 2 * (size_t)nn * kPanelNB * op_elem(o->TF));
         AL(f->Bop, 2 * (size_t)nn * kPanelNB * op_elem(o->TF));
+        if (nn > 2 * kPanelNB) {
+            AL(f->Agrp, (size_t)kMaxGroup * nn * kPanelNB * op_elem(o->TF));
+            AL(f->Bgrp, (size_t)kMaxGroup * nn * kPanelNB * op_elem(o->TF));
+        }
     }
     AL(f->Linv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
     AL(f->Uinv, (size_t)nblk * kTrsvB * kTrsvB * sizeof(float));
     AL(f->tags, (size_t)2 * nblk * kTrsvB * sizeof(unsigned long long));
     AL(f->blk_subst, (size_t)2 * nblk * sizeof(int32_t));
+    f->onthefly = o->onthefly;
+    f->store_tf = o->store_tf;
+    if (o->store_tf) AL(f->AF16, (size_t)nn * f->ldf * 2);
+    if (o->onthefly && o->TW == IR_F64) {
+        AL(f->y64, (size_t)nblk * kTrsvB * sizeof(double));
+        AL(f->z64, (size_t)nblk * kTrsvB * sizeof(double));
+        AL(f->mps_flags, (size_t)2 * nblk * sizeof(int));
+        if (cudaMemset(f->mps_flags, 0, (size_t)2 * nblk * sizeof(int)) != cudaSuccess) {
+            st = IR_ECUDA;
+            goto fail;
+        }
+    }
     AL(f->x, nn * sizeof(double));
     AL(f->r, nn * sizeof(double));
     AL(f->dev, sizeof(DevScalars));
@@ -223,7 +255,7 @@ bool lookahead_enabled() {
 }
 
 ir_status ensure_lookahead(ir_fact *f) {
-    const int need = 2 * (int)((f->n + kPanelNB - 1) / kPanelNB) + 2;
+    const int need = 2 * (int)((f->n + kPanelNB - 1) / kPanelNB) + 3;
     if (!f->la_stream) {
         int lo = 0, hi = 0;
         CK(cudaDeviceGetStreamPriorityRange(&lo, &hi));
@@ -254,7 +286,178 @@ ir_status ensure_lookahead(ir_fact *f) {
 // so the next panel overlaps the bulk of the trailing update.  The swap list
 // and the tensor-core operand buffers alternate between two copies by step
 // parity.  Every element still receives its updates in block order.
+// Tensor-core factorization (TF = TF32, bf16, fp16) in groups of G block steps.
+// Within a group the steps run as in enqueue_factor, but each step updates
+// only the near columns: the rest of its group and the first block column of
+// the next group.  At the group's end the far columns (everything right of
+// that) receive the whole group at once:
+//   1. the group's row interchanges, in order;
+//   2. rTF of the group's L columns is packed into G operand slots;
+//   3. U12 of the group's rows: for each of its 64-row blocks t, the binary32
+//      U12 solve (writing rTF(U) into slot t), then the tensor-core update of
+//      the group's rows below block t by slot t (K = 64) -- the block steps of
+//      the right-looking LU, restricted to the group's rows;
+//   4. the rows below the group minus the products of all G slots (K = 64 G):
+//      one read and one write of each binary32 C tile for the whole group.
+// Every element still receives the same TF-rounded operand products, block by
+// block in order; only the binary32 accumulation of a group's products for the
+// far rows is one sum instead of G.
+// With lookahead (second stream s2): step 4 for the next group's near columns
+// runs at the group's end, the rest of step 4 (the far columns beyond the next
+// group) in G column chunks, one after each step of the next group, so the
+// next group's panels overlap it.
+ir_status enqueue_factor_grouped(ir_fact *f, cudaStream_t s) {
+    const int n = (int)f->n;
+    const int64_t ldf = f->ldf;
+    CK(cudaMemsetAsync(f->dev, 0, sizeof(DevScalars), s));
+    CK(cudaMemsetAsync(&f->dev->info, 0x7F, sizeof(int), s));
+    if (n == 0) return IR_OK;
+    const int use_scale = (f->TF == IR_F16 && f->fp16_scale) ? 1 : 0;
+    if (use_scale) RUN(KC_MAXABS, s, launch_maxabs(n, f->TW, f->A, f->lda, f->dev, f->ctx->sms, s));
+    RUN(KC_CAST, s, launch_cast(n, f->TW, f->A, f->lda, f->TF, use_scale, f->AF, ldf, f->dev, s));
+    RUN(KC_IOTA, s, launch_iota(n, f->perm, s));
+    const int NB = kPanelNB;
+    const int G = f->group;
+    const int W = NB * G;
+    const int sms = f->ctx->sms;
+    const size_t esz = op_elem(f->TF);
+    const size_t opsz = (size_t)n * NB * esz;
+    const bool la = !g_prof.on && lookahead_enabled() && n > 2 * NB;
+    const int share = sms - f->reserve_sms;
+    cudaStream_t s2 = s;
+    int ev = 0;
+    if (la) {
+        ir_status st = ensure_lookahead(f);
+        if (st != IR_OK) return st;
+        s2 = f->la_stream;
+        CK(cudaEventRecord(f->la_events[ev], s));       // s2 joins after the cast
+        CK(cudaStreamWaitEvent(s2, f->la_events[ev], 0));
+        ++ev;
+    }
+    // the far update of the previous group still owed to the columns [pend_cb, n)
+    // (lookahead): Gp slots, column chunks of pend_w, pend_k of them enqueued
+    int pend_c0 = 0, pend_G = 0, pend_cb = n, pend_w = 0, pend_near = 0;
+    auto pend_chunk = [&](cudaStream_t st) -> ir_status {
+        if (pend_cb >= n) return IR_OK;
+        const int ce = (pend_cb + pend_w < n) ? pend_cb + pend_w : n;
+        RUN(KC_GEMM_TC_GROUP, st, launch_gemm_tc_group(f->AF, ldf, pend_c0, pend_G, pend_c0 + NB * pend_G, n, pend_cb,
+                                                       ce, 0, pend_G, f->TF, f->Agrp, n - pend_c0, f->Bgrp,
+                                                       n - pend_near, pend_near, sms, la ? share : 0, f->dev, st));
+        pend_cb = ce;
+        return IR_OK;
+    };
+    cudaEvent_t pending_rest = nullptr;                  // R(j-1): s2's work of the previous step
+    for (int c0 = 0, step = 0; c0 < n; c0 += W) {
+        const int c1 = (c0 + W < n) ? c0 + W : n;
+        const int near_end = (c1 + NB < n) ? c1 + NB : n;
+        const int Gg = (c1 - c0 + NB - 1) / NB;
+        for (int j = c0; j < c1; j += NB, ++step) {
+            const int nbp = (n - j < NB) ? n - j : NB;
+            const int par = step & 1;
+            int32_t *sl = f->swap_list + (step % (2 * kMaxGroup)) * kSwapListInts;
+            void *aop = static_cast<char *>(f->Aop) + par * opsz;
+            void *bop = static_cast<char *>(f->Bop) + par * opsz;
+            RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s));
+            const bool trailing = j + nbp < n;
+            const bool group_end = (j + NB >= c1) && near_end < n;   // far columns get the group's update now
+            cudaStream_t sw = s;                                     // stream of this step's rest
+            if (la) {
+                cudaEvent_t evP = f->la_events[ev++];
+                CK(cudaEventRecord(evP, s));
+                if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
+                pending_rest = nullptr;
+                if (!trailing) {
+                    RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, 0, j, 0, 0, sl, s));
+                    break;
+                }
+                const int nx0 = j + NB, nx1 = (j + 2 * NB < n) ? j + 2 * NB : n;
+                // s1: the next block column
+                RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, nx0, nx1, 0, 0, sl, s));
+                RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, s));
+                RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, nx0, nx1, f->TF, aop, bop, sms, 0, f->dev, s));
+                // s2: the rest of the near columns
+                CK(cudaStreamWaitEvent(s2, evP, 0));
+                sw = s2;
+                RUN(KC_LASWP, s2, launch_laswp(f->AF, ldf, 0, j, nx1, near_end, sl, s2));
+                if (nx1 < near_end) {
+                    RUN(KC_TRSM, s2, launch_trsm(f->AF, ldf, nx1, near_end, j, f->TF, bop, s2));
+                    RUN(KC_GEMM_TC, s2, launch_gemm_tc(f->AF, ldf, n, j, NB, nx1, near_end, f->TF, aop, bop, sms,
+                                                       share, f->dev, s2));
+                }
+                // one chunk of the previous group's far update
+                ir_status st = pend_chunk(s2);
+                if (st != IR_OK) return st;
+            } else {
+                RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, 0, j, j + nbp, near_end, sl, s));
+                if (trailing && j + NB < near_end) {
+                    RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, j + NB, near_end, j, f->TF, bop, s));
+                    RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, j + NB, near_end, f->TF, aop, bop, sms, 0,
+                                                      f->dev, s));
+                }
+            }
+            if (group_end) {
+                // the rest of the previous group's far update comes first (same columns)
+                while (pend_cb < n) {
+                    ir_status st = pend_chunk(sw);
+                    if (st != IR_OK) return st;
+                }
+                const int mshare = la ? share : 0;
+                // 1. the group's interchanges on the far columns, in order
+                RUN(KC_LASWP, sw, launch_laswp_lists(f->AF, ldf, near_end, n, f->swap_list, kSwapListInts,
+                                                     2 * kMaxGroup, step - (Gg - 1), Gg, sw));
+                // 2. rTF of the group's L columns (rows below each block's diagonal block)
+                RUN(KC_PACK, sw, launch_pack_slots(f->AF, ldf, c0, Gg, c0 + NB, n, n - c0, f->TF, f->Agrp, sms, sw));
+                // 3. U12 of the group's rows, block by block, with the group's own block steps
+                //    between them (one kernel, one CTA per 64 far columns)
+                const size_t bslot = (size_t)(n - near_end) * NB * esz;
+                RUN(KC_TRSM, sw, launch_trsm_group(f->AF, ldf, c0, Gg, near_end, n, f->TF, f->Bgrp, (int64_t)bslot, sw));
+                // 4. the rows below the group: all G slots at once
+                pend_c0 = c0;
+                pend_G = Gg;
+                pend_near = near_end;
+                pend_cb = near_end;
+                if (la) {
+                    // now the next group's near columns; the rest in chunks during the next group
+                    const int c2 = (c1 + W < n) ? c1 + W : n;
+                    const int nend2 = (c2 + NB < n) ? c2 + NB : n;
+                    pend_w = nend2 - near_end;
+                    ir_status st = pend_chunk(sw);
+                    if (st != IR_OK) return st;
+                    const int steps2 = (c2 - c1 + NB - 1) / NB;
+                    pend_w = ((n - pend_cb) + steps2 - 1) / steps2;
+                    pend_w = (pend_w + NB - 1) / NB * NB;
+                } else {
+                    pend_w = n - near_end;
+                    ir_status st = pend_chunk(sw);
+                    if (st != IR_OK) return st;
+                }
+            }
+            if (la) {
+                pending_rest = f->la_events[ev++];
+                CK(cudaEventRecord(pending_rest, s2));
+            }
+        }
+    }
+    if (pend_cb < n) {
+        // chunks the last group had no steps left for (not expected; kept for safety)
+        cudaStream_t st = la ? s2 : s;
+        while (pend_cb < n) {
+            ir_status e = pend_chunk(st);
+            if (e != IR_OK) return e;
+        }
+        if (la) {
+            pending_rest = f->la_events[ev++];
+            CK(cudaEventRecord(pending_rest, s2));
+        }
+    }
+    if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
+    if (f->store_tf) RUN(KC_STORE, s, launch_store_tf(f->AF, ldf, n, f->TF, f->AF16, f->dev, sms, s));
+    RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, f->blk_subst, s));
+    return IR_OK;
+}
+
 ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
+    if (f->TF != IR_F32 && f->Agrp) return enqueue_factor_grouped(f, s);
     const int n = (int)f->n;
     const int64_t ldf = f->ldf;
     CK(cudaMemsetAsync(f->dev, 0, sizeof(DevScalars), s));
@@ -330,6 +533,7 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
         }
     }
     if (pending_rest) CK(cudaStreamWaitEvent(s, pending_rest, 0));
+    if (f->store_tf) RUN(KC_STORE, s, launch_store_tf(f->AF, ldf, n, f->TF, f->AF16, f->dev, sms, s));
     RUN(KC_DIAGINV, s, launch_diag_inv(f->AF, ldf, n, f->Linv, f->Uinv, f->blk_subst, s));
     return IR_OK;
 }
@@ -505,43 +709,54 @@ ir_status tune_factor(ir_fact *f, cudaStream_t s) {
     for (int i = 0; i < c->ntuned && i < 16; ++i)
         if (c->tuned[i].n == f->n && c->tuned[i].tf == (int)f->TF) {
             f->reserve_sms = c->tuned[i].reserve_sms;
+            f->group = c->tuned[i].group;
             return IR_OK;
         }
     const int cands[] = {8, 12, 16, 24, 32};
+    // block steps per group of the tensor-core factorization (no groups for binary32)
+    const int gcands_tc[] = {4, 8, 16};
+    const int gcands_f32[] = {kDefaultGroup};
+    const bool tc = f->TF != IR_F32 && f->Agrp;
+    const int *gc = tc ? gcands_tc : gcands_f32;
+    const int ng = tc ? 3 : 1;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     float best = 3.4e38f;
-    int best_r = f->reserve_sms;
+    int best_r = f->reserve_sms, best_g = f->group;
     ir_status st = IR_OK;
-    for (int r : cands) {
-        if (r >= c->sms / 2) continue;
-        f->reserve_sms = r;
-        if (f->graph) {
-            cudaGraphExecDestroy(f->graph);
-            f->graph = nullptr;
-        }
-        float ms = 0.f;
-        for (int rep = 0; rep < 2 && st == IR_OK; ++rep) {
-            cudaError_t e = cudaEventRecord(e0, s);
-            if (e == cudaSuccess) {
-                st = run_factor(f, s);
-                if (st == IR_OK) e = cudaEventRecord(e1, s);
+    for (int gi = 0; gi < ng && st == IR_OK; ++gi)
+        for (int r : cands) {
+            if (r >= c->sms / 2) continue;
+            f->reserve_sms = r;
+            f->group = gc[gi];
+            if (f->graph) {
+                cudaGraphExecDestroy(f->graph);
+                f->graph = nullptr;
             }
-            if (st == IR_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
-            if (st == IR_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (st == IR_OK && e != cudaSuccess) st = cuda_fail(e, "tune_factor");
+            float ms = 0.f;
+            for (int rep = 0; rep < 2 && st == IR_OK; ++rep) {
+                cudaError_t e = cudaEventRecord(e0, s);
+                if (e == cudaSuccess) {
+                    st = run_factor(f, s);
+                    if (st == IR_OK) e = cudaEventRecord(e1, s);
+                }
+                if (st == IR_OK && e == cudaSuccess) e = cudaEventSynchronize(e1);
+                if (st == IR_OK && e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (st == IR_OK && e != cudaSuccess) st = cuda_fail(e, "tune_factor");
+            }
+            if (st != IR_OK) break;
+            if (ms < best) {
+                best = ms;
+                best_r = r;
+                best_g = gc[gi];
+            }
         }
-        if (st != IR_OK) break;
-        if (ms < best) {
-            best = ms;
-            best_r = r;
-        }
-    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (st != IR_OK) return st;
     f->reserve_sms = best_r;
+    f->group = best_g;
     if (f->graph) {
         cudaGraphExecDestroy(f->graph);
         f->graph = nullptr;
@@ -550,6 +765,7 @@ ir_status tune_factor(ir_fact *f, cudaStream_t s) {
     slot.n = f->n;
     slot.tf = (int)f->TF;
     slot.reserve_sms = best_r;
+    slot.group = best_g;
     c->ntuned += 1;
     return IR_OK;
 }
@@ -566,6 +782,9 @@ void ir_default_opts(ir_opts *o) {
     o->fp16_scale = 1;
     o->nb = 0;
     o->autotune = 0;
+    o->group = 0;
+    o->onthefly = 0;
+    o->store_tf = 0;
 }
 
 void ir_default_term(ir_term *t) {
@@ -654,6 +873,8 @@ ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda, const ir
     else ir_default_opts(&o);
     if (!tw_ok(o.TW) || !tf_ok(o.TF) || o.TR != IR_F64) return IR_EINVAL;
     if (o.nb != 0 && o.nb != kPanelNB) return IR_EUNSUPPORTED;
+    if (o.group < 0 || o.group > kMaxGroup || (o.onthefly != 0 && o.onthefly != 1)) return IR_EINVAL;
+    if (o.store_tf != 0 && (o.store_tf != 1 || (o.TF != IR_F16 && o.TF != IR_BF16))) return IR_EINVAL;
     if (n > kMaxN) {
         snprintf(g_last_error, sizeof g_last_error, "n = %lld exceeds the supported maximum %d",
                  (long long)n, kMaxN);
@@ -666,6 +887,7 @@ ir_status ir_factor(ir_ctx *ctx, int64_t n, const void *A, int64_t lda, const ir
     f->A = A;
     f->lda = lda;
     f->anorm_valid = 0;
+    if (o.group > 0) f->group = o.group;
     // the schedule autotuner matters once the lookahead overlaps panels with updates
     if (o.autotune && n >= 1024) st = tune_factor(f, (cudaStream_t)stream);
     if (st == IR_OK) st = run_factor(f, (cudaStream_t)stream);
@@ -745,6 +967,8 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     st = read_dev(f, s);
     if (st != IR_OK) return st;
     if (f->host_dev->nonfinite) {
+        // b (or A's norm) is not finite: the flag belongs to this call, not to the factorization
+        CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));
         R.status = IR_FAILED;
         if (rep) *rep = R;
         return IR_ENONFINITE;
@@ -757,11 +981,22 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
     const double eps_w = eps_of(f->TW);
     int k = 0;
     int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
+    const bool mps64 = f->onthefly && f->TW == IR_F64;
+    if (f->onthefly && !mps64) {
+        // TW = binary32: r rounded to binary32, binary32 solves with unit scale
+        static const double one = 1.0;
+        CK(cudaMemcpyAsync(&f->dev->one_bits, &one, sizeof(double), cudaMemcpyHostToDevice, s));
+    }
     while (status < 0) {
         f->epoch += 1;
         CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
-        RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
-                                         nullptr, nullptr, f->x, f->tags, f->epoch, f->dev, s));
+        if (mps64)
+            RUN(KC_TRSV64, s, launch_mps_pair(f->AF, f->ldf, (int)n, f->perm, f->r, f->x, f->y64, f->z64,
+                                              f->mps_flags, f->epoch, f->dev, s));
+        else
+            RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
+                                             nullptr, nullptr, f->x, f->tags, f->epoch, f->dev, s, nullptr,
+                                             nullptr, nullptr, f->onthefly != 0, f->AF16, f->TF));
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
                            f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
         st = read_dev(f, s);
@@ -906,6 +1141,8 @@ ir_status krylov_solve(int method, ir_fact *f, const void *b, void *x, const ir_
     st = read_dev(f, s);
     if (st != IR_OK) return st;
     if (f->host_dev->nonfinite) {
+        // b (or A's norm) is not finite: the flag belongs to this call, not to the factorization
+        CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));
         R.status = IR_FAILED;
         if (rep) *rep = R;
         return IR_ENONFINITE;
@@ -933,7 +1170,7 @@ ir_status krylov_solve(int method, ir_fact *f, const void *b, void *x, const ir_
         f->epoch += 1;
         RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, W,
                                          nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s, wbits, out,
-                                         skip));
+                                         skip, false, f->AF16, f->TF));
         return IR_OK;
     };
     while (status < 0) {
@@ -942,7 +1179,7 @@ ir_status krylov_solve(int method, ir_fact *f, const void *b, void *x, const ir_
         f->epoch += 1;
         RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, nn, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
                                          nullptr, nullptr, nullptr, f->tags, f->epoch, f->dev, s,
-                                         &f->dev->rnorm_bits, z, nullptr));
+                                         &f->dev->rnorm_bits, z, nullptr, false, f->AF16, f->TF));
         CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
         if (method == KRY_GMRES) {
             RUN(KC_GM_ORTH, s, launch_gm_orth(nn, V, ldv, -1, m, ko.eta, gs, s));     // v_0 = z / ||z||_2
@@ -1007,11 +1244,160 @@ ir_status ir_solve_bicgstab(ir_fact *f, const void *b, void *x, const ir_term *t
     return krylov_solve(KRY_BICGSTAB, f, b, x, term, kopts, stream, rep, khist);
 }
 
+namespace {
+
+// The workspace of ir_solve_many's blocked path (allocated on first use).
+ir_status ensure_multi(ir_fact *f) {
+    if (f->xm) return IR_OK;
+    const int64_t n = f->n;
+    const int64_t nblk = (n + kTrsvB - 1) / kTrsvB;
+    const size_t esz = (f->TW == IR_F64) ? 8 : 4;
+    CK(cudaMalloc(&f->xm, (size_t)kMultiRhs * n * sizeof(double)));
+    CK(cudaMalloc(&f->rm, (size_t)kMultiRhs * n * sizeof(double)));
+    CK(cudaMalloc(&f->bm, (size_t)kMultiRhs * n * esz));
+    CK(cudaMalloc(&f->mtags, (size_t)2 * kMultiRhs * nblk * kTrsvB * sizeof(unsigned long long)));
+    CK(cudaMemset(f->mtags, 0, (size_t)2 * kMultiRhs * nblk * kTrsvB * sizeof(unsigned long long)));
+    CK(cudaMalloc(&f->mscal, sizeof(MultiScalars)));
+    CK(cudaMallocHost(&f->host_mscal, sizeof(MultiScalars)));
+    return IR_OK;
+}
+
+// Several right-hand sides of one factorization refined together, up to 4 at a
+// time: every correction solve applies each factor tile to all of the block's
+// columns (launch_trsv_multi) and every residual reads A once for all of them
+// (launch_residual_multi); each column keeps its own scaling (eq. vdlow), its
+// own history and its own termination test (Sec. 5.1), and a column that has
+// stopped takes no further corrections.
+ir_status solve_many_blocked(ir_fact *f, int64_t nrhs, const void *B, int64_t ldb, void *X, int64_t ldx,
+                             const ir_term &t, cudaStream_t s, ir_report *reps) {
+    const int64_t n = f->n;
+    const size_t esz = (f->TW == IR_F64) ? 8 : 4;
+    ir_status st = ensure_multi(f);
+    if (st != IR_OK) return st;
+    // ns * n * 4 partial sums for the residual of 4 columns
+    const int64_t need = residual_partials_needed(n, f->ctx->sms) * kMultiRhs;
+    if (need > f->ctx->partials_cap) {
+        if (f->ctx->partials) cudaFree(f->ctx->partials);
+        f->ctx->partials = nullptr;
+        f->ctx->partials_cap = 0;
+        CK(cudaMalloc(&f->ctx->partials, need * sizeof(double)));
+        f->ctx->partials_cap = need;
+    }
+    const bool tr_wider = (f->TW == IR_F32);
+    const double eps_w = eps_of(f->TW);
+    double anorm = 0.0;
+    if (t.mode == 1) {
+        if (!f->anorm_valid) RUN(KC_NORM1, s, launch_norm1(n, f->TW, f->A, f->lda, &f->dev->anorm_bits, s));
+        st = read_dev(f, s);
+        if (st != IR_OK) return st;
+        f->anorm_valid = 1;
+        anorm = bits_to_double(f->host_dev->anorm_bits);
+    }
+    ir_status first = IR_OK;
+    MultiScalars *hm = f->host_mscal;
+    for (int64_t c0 = 0; c0 < nrhs; c0 += kMultiRhs) {
+        const int k = (int)((nrhs - c0 < kMultiRhs) ? nrhs - c0 : kMultiRhs);
+        ir_report R[kMultiRhs];
+        int status[kMultiRhs], iters[kMultiRhs];
+        std::memset(R, 0, sizeof R);
+        std::memset(hm, 0, sizeof(MultiScalars));
+        // the block's right-hand sides (zero columns past k), x = 0, r = b, ||b||
+        CK(cudaMemsetAsync(f->bm, 0, (size_t)kMultiRhs * n * esz, s));
+        CK(cudaMemcpy2DAsync(f->bm, (size_t)n * esz, static_cast<const char *>(B) + (size_t)c0 * ldb * esz,
+                             (size_t)ldb * esz, (size_t)n * esz, (size_t)k, cudaMemcpyDeviceToDevice, s));
+        for (int j = 0; j < kMultiRhs; ++j) {
+            R[j].scale = f->host_dev->scale;
+            status[j] = IR_CONVERGED;
+            iters[j] = 0;
+            CK(cudaMemsetAsync(&f->dev->bnorm_bits, 0, sizeof(unsigned long long), s));
+            CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));
+            RUN(KC_INIT, s, launch_init_rb(n, f->TW, static_cast<const char *>(f->bm) + (size_t)j * n * esz,
+                                           f->rm + (size_t)j * n, f->xm + (size_t)j * n, f->dev, s));
+            st = read_dev(f, s);
+            if (st != IR_OK) return st;
+            if (j >= k) continue;
+            const double bn = bits_to_double(f->host_dev->bnorm_bits);
+            R[j].rhist[0] = bn;
+            hm->rho[j] = f->host_dev->bnorm_bits;
+            if (f->host_dev->nonfinite) {
+                status[j] = IR_FAILED;
+                if (first == IR_OK) first = IR_ENONFINITE;
+            } else if (bn != 0.0) {
+                hm->active[j] = 1;
+                status[j] = -1;
+            }
+        }
+        CK(cudaMemcpyAsync(&f->mscal->rho, hm->rho, sizeof hm->rho, cudaMemcpyHostToDevice, s));
+        int nactive = 0;
+        for (int j = 0; j < kMultiRhs; ++j) nactive += hm->active[j];
+        while (nactive > 0) {
+            f->epoch += 1;
+            CK(cudaMemcpyAsync(&f->mscal->active, hm->active, sizeof hm->active, cudaMemcpyHostToDevice, s));
+            CK(cudaMemsetAsync(&f->mscal->dnorm, 0, sizeof hm->dnorm + sizeof hm->xnorm, s));
+            RUN(KC_TRSV, s, launch_trsv_multi(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->rm,
+                                              n, f->mscal->rho, f->mscal->active, f->xm, n, f->mscal->dnorm,
+                                              f->mscal->xnorm, f->mtags, f->epoch, f->dev, s, f->AF16, f->TF));
+            RUN(KC_RESID, s, launch_residual_multi(n, f->TW, f->A, f->lda, f->bm, n, f->xm, n, f->rm, n,
+                                                   f->ctx->partials, f->ctx->partials_cap, f->mscal->rho,
+                                                   f->ctx->sms, s));
+            CK(cudaMemcpyAsync(hm, f->mscal, sizeof(MultiScalars), cudaMemcpyDeviceToHost, s));
+            st = read_dev(f, s);     // synchronizes the stream (hm is current after it)
+            if (st != IR_OK) return st;
+            if (f->host_dev->timeout) {
+                snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the triangular solve timed out");
+                return IR_ETIMEOUT;
+            }
+            for (int j = 0; j < k; ++j) {
+                if (status[j] >= 0) continue;
+                const int kk = ++iters[j];
+                R[j].dhist[kk - 1] = bits_to_double(hm->dnorm[j]);
+                R[j].rhist[kk] = bits_to_double(hm->rho[j]);
+                const int d = term_decide(R[j].rhist, R[j].dhist, kk, R[j].rhist[0], eps_w, &t, tr_wider, t.Rmax,
+                                          anorm, bits_to_double(hm->xnorm[j]));
+                if (d >= 0) {
+                    status[j] = d;
+                    hm->active[j] = 0;
+                    --nactive;
+                }
+            }
+        }
+        for (int j = 0; j < k; ++j) {
+            if (status[j] != IR_FAILED)
+                RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->xm + (size_t)j * n,
+                                                 static_cast<char *>(X) + (size_t)(c0 + j) * ldx * esz, s));
+            R[j].iters = iters[j];
+            R[j].status = (ir_solve_status)status[j];
+            if (reps) reps[c0 + j] = R[j];
+        }
+    }
+    CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));   // a non-finite b is this call's, not the factorization's
+    if (reps) CK(cudaStreamSynchronize(s));
+    return first;
+}
+
+}  // namespace
+
 ir_status ir_solve_many(ir_fact *f, int64_t nrhs, const void *B, int64_t ldb, void *X, int64_t ldx,
                         const ir_term *term, void *stream, ir_report *reps) {
     if (!f || nrhs < 0 || ldb < (f->n > 1 ? f->n : 1) || ldx < (f->n > 1 ? f->n : 1)) return IR_EINVAL;
     if (nrhs > 0 && f->n > 0 && (!B || !X)) return IR_EINVAL;
+    ir_term t;
+    if (term) t = *term;
+    else ir_default_term(&t);
+    if (t.litmax < 1 || t.litmax > IR_MAX_HIST - 1 || !(t.Rmax > 0) || (t.mode != 0 && t.mode != 1))
+        return IR_EINVAL;
     const size_t esz = (f->TW == IR_F64) ? 8 : 4;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (nrhs > 1 && f->n > 0 && !f->onthefly) {
+        CK(cudaSetDevice(f->ctx->device));
+        // the factorization's outcome, as ir_solve reports it
+        ir_status st = read_dev(f, s);
+        if (st != IR_OK) return st;
+        const bool bad = f->host_dev->timeout || f->host_dev->nonfinite || f->host_dev->info != kInfoNone;
+        if (!bad) return solve_many_blocked(f, nrhs, B, ldb, X, ldx, t, s, reps);
+    }
+    // one column at a time: a single right-hand side, mixed precision solves, or a
+    // failed factorization (each ir_solve reports it)
     ir_status first = IR_OK;
     for (int64_t j = 0; j < nrhs; ++j) {
         const void *bj = static_cast<const char *>(B) + (size_t)j * ldb * esz;
@@ -1023,13 +1409,34 @@ ir_status ir_solve_many(ir_fact *f, int64_t nrhs, const void *B, int64_t ldb, vo
     return first;
 }
 
+ir_status ir_check_wait_timeout(ir_fact *f, double limit_s, void *stream) {
+    if (!f || !(limit_s > 0.0) || limit_s * 1e9 > (double)kWaitLimitNs) return IR_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    CK(cudaSetDevice(f->ctx->device));
+    CK(cudaMemsetAsync(&f->dev->timeout, 0, sizeof(int), s));
+    // the tags carry solve epochs; epoch + 2^31 is never written by a solve
+    const unsigned tag = f->epoch + 0x80000000u;
+    CK(launch_wait_probe(f->tags, tag, (unsigned long long)(limit_s * 1e9), &f->dev->timeout, s));
+    ir_status st = read_dev(f, s);
+    if (st != IR_OK) return st;
+    const int gave_up = f->host_dev->timeout;
+    CK(cudaMemsetAsync(&f->dev->timeout, 0, sizeof(int), s));   // the factorization stays usable
+    CK(cudaStreamSynchronize(s));
+    if (gave_up) {
+        snprintf(g_last_error, sizeof g_last_error, "the probe's bounded wait gave up after %.3g s", limit_s);
+        return IR_ETIMEOUT;
+    }
+    return IR_OK;
+}
+
 ir_status ir_lu_solve(ir_fact *f, const float *v, float *d, void *stream) {
     if (!f || (f->n > 0 && (!v || !d))) return IR_EINVAL;
     if (f->n == 0) return IR_OK;
     CK(cudaSetDevice(f->ctx->device));
     f->epoch += 1;
     CK(launch_trsv_pair(f->AF, f->ldf, (int)f->n, f->Linv, f->Uinv, f->blk_subst, f->perm, nullptr, v, d, nullptr,
-                        f->tags, f->epoch, f->dev, (cudaStream_t)stream));
+                        f->tags, f->epoch, f->dev, (cudaStream_t)stream, nullptr, nullptr, nullptr, false, f->AF16,
+                        f->TF));
     return IR_OK;
 }
 
@@ -1137,10 +1544,11 @@ ir_status ir_batch_schedule(const ir_batch *b, int *grid, int *tc_min_trail) {
     return IR_OK;
 }
 
-ir_status ir_fact_schedule(const ir_fact *f, int *nb, int *panel_reserve_sms) {
+ir_status ir_fact_schedule(const ir_fact *f, int *nb, int *panel_reserve_sms, int *group) {
     if (!f) return IR_EINVAL;
     if (nb) *nb = f->nb;
     if (panel_reserve_sms) *panel_reserve_sms = f->reserve_sms;
+    if (group) *group = (f->TF != IR_F32 && f->Agrp) ? f->group : 1;
     return IR_OK;
 }
 
@@ -1227,7 +1635,9 @@ ir_status ir_solve_host(ir_ctx *ctx, int64_t n, const void *A_host, int64_t lda,
     CK(cudaSetDevice(ctx->device));
     const bool same = ctx->host_f && ctx->host_n == n && ctx->host_lda == lda && ctx->host_tw == (int)o.TW &&
                       ctx->host_tf == (int)o.TF && ctx->host_scale == o.fp16_scale &&
-                      ctx->host_autotune == o.autotune;
+                      ctx->host_autotune == o.autotune && ctx->host_f->onthefly == o.onthefly &&
+                      ctx->host_f->store_tf == o.store_tf &&
+                      (o.group == 0 || ctx->host_f->group == o.group);
     if (!same) release_host_cache(ctx);
     ir_status st = IR_OK;
     cudaError_t e = cudaSuccess;

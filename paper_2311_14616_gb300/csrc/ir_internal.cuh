@@ -25,6 +25,7 @@ constexpr int kPanelRows = 512;   // panel rows per CTA (two per thread)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelMaxCluster = 16;
 constexpr int kMaxN = kPanelRows * kPanelMaxCluster;  // 8192 rows per panel cluster
+constexpr int kMaxGroup = 16;     // block steps per group of the tensor-core LU (64 x 16 = 1024 columns)
 
 // Device-side scalars.  Non-negative doubles are ordered like their bit
 // patterns, so maxima are kept with atomicMax on uint64 (deterministic).
@@ -40,7 +41,16 @@ struct DevScalars {
     int nonfinite;                   // 1: NaN/Inf met in A, b or the rounded copy
     int timeout;                     // 1: a bounded wait gave up
     int pad;
+    unsigned long long one_bits;     // 1.0: the unit scale of mixed precision solves with TW = binary32
     unsigned int ticket[2];          // CTA ticket counters of the two solves
+};
+
+// Scalars of a block of up to 4 right-hand sides refined together (ir_solve_many).
+struct MultiScalars {
+    unsigned long long rho[4];     // ||r_j||_inf (the scale of the next solve, then rhist)
+    unsigned long long dnorm[4];   // ||d_j||_inf of the latest correction
+    unsigned long long xnorm[4];   // ||x_j||_inf after it
+    int active[4];                 // 1: column j is still refined
 };
 
 // GMRES state of one correction solve (device memory, written by the
@@ -75,6 +85,7 @@ struct ir_tuned {
     int64_t n;
     int tf;
     int reserve_sms;
+    int group;
 };
 
 struct ir_ctx {
@@ -106,8 +117,21 @@ struct ir_fact {
     float *AF;
     int32_t *ipiv;           // 0-based pivots
     int32_t *perm;           // (P A)[i] = A[perm[i]]
-    int32_t *swap_list;      // 2 x (1 + 2*2*NB) ints: count, then (dst, src) pairs, by step parity
+    int32_t *swap_list;      // 2 kMaxGroup x (1 + 2*2*NB) ints: count, then (dst, src) pairs, by step
     void *Aop, *Bop;         // tensor-core operands, 2 buffers each by step parity (NULL for TF = F32)
+    int group;               // block steps per group of the tensor-core LU (far columns updated once per group)
+    int onthefly;            // 1: mixed precision solves (Sec. 5.3) in ir_solve
+    int store_tf;            // 1: factors kept in TF (2-byte copy AF16 read by the solves)
+    void *AF16;
+    // several right-hand sides refined together (ir_solve_many): 4 columns of x, r
+    // and b (padded), the tagged solve words, the per-column scalars
+    double *xm, *rm;
+    void *bm;
+    unsigned long long *mtags;
+    ir::MultiScalars *mscal, *host_mscal;
+    double *y64, *z64;       // MPS solve vectors (nblk * 128 binary64 each; TW = binary64)
+    int *mps_flags;          // MPS per-block publication flags (2 nblk)
+    void *Agrp, *Bgrp;       // a group's operands: group x n rows x 64 (rTF of its L columns / U rows)
     cudaStream_t la_stream;  // low-priority stream of the lookahead schedule
     cudaEvent_t *la_events;  // fork/join events of the lookahead schedule
     int la_nevents;
@@ -163,6 +187,15 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
                          void *Aop, cudaStream_t s);
 cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b,
                          const int32_t *swap_list, cudaStream_t s);
+// The interchange lists first .. first + count - 1 (of a ring of `ring` lists of
+// list_ints ints) applied in order to the columns [c0, c1).
+cudaError_t launch_laswp_lists(float *AF, int64_t ldf, int c0, int c1, const int32_t *lists, int list_ints, int ring,
+                               int first, int count, cudaStream_t s);
+// U12 of the group of G block rows starting at c0 for the columns [cb, ce), with
+// the group's own block steps between them; rTF(U) of block t into operand slot t
+// of Bgrp (slots of bslot bytes, row c - cb for column c).
+cudaError_t launch_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf, void *Bgrp,
+                              int64_t bslot, cudaStream_t s);
 cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
                         cudaStream_t s);
 cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
@@ -170,6 +203,15 @@ cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int c
 cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
                            ir_dtype tf, const void *Aop, const void *Bop, int sms, int max_ctas,
                            DevScalars *dev, cudaStream_t s);
+// Group update of the tensor-core LU: rows [r0, r1) x columns [cb, ce) of A_F
+// minus the products of slots [s0, s1) of the group operands (k_gemm_tc.cu).
+cudaError_t launch_gemm_tc_group(float *AF, int64_t ldf, int c0, int G, int r0, int r1, int cb, int ce,
+                                 int s0, int s1, ir_dtype tf, const void *Agrp, int64_t a_rows, const void *Bgrp,
+                                 int64_t b_rows, int bbase, int sms, int max_ctas, DevScalars *dev,
+                                 cudaStream_t s);
+// rTF of the factor columns [c0, c0 + 64 G), rows [r0, r1), into G slots of `rows` rows.
+cudaError_t launch_pack_slots(const float *AF, int64_t ldf, int c0, int G, int r0, int r1, int64_t rows, ir_dtype tf,
+                              void *out, int sms, cudaStream_t s);
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s);
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
@@ -184,7 +226,34 @@ cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *L
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
                              cudaStream_t s, const unsigned long long *rho_bits = nullptr,
-                             double *pw = nullptr, const int *skip = nullptr);
+                             double *pw = nullptr, const int *skip = nullptr, bool unit_rho = false,
+                             const void *F16 = nullptr, ir_dtype tf16 = IR_F32);
+// Several right-hand sides (4 columns; k_trsv.cu, k_resid.cu): the correction
+// solve pair applying each factor tile to all columns, and the residual reading
+// A once for all of them.  Column j: R + j ldr, X + j ldx, rho_bits[j], ...;
+// tags: 2 x 4 x nblk*128 words.
+constexpr int kMultiRhs = 4;
+cudaError_t launch_trsv_multi(const float *AF, int64_t ldf, int n, const float *Linv, const float *Uinv,
+                              const int32_t *blk_subst, const int32_t *perm, const double *R, int64_t ldr,
+                              const unsigned long long *rho_bits, const int *active, double *X, int64_t ldx,
+                              unsigned long long *dnorm_bits, unsigned long long *xnorm_bits,
+                              unsigned long long *tags, unsigned epoch, DevScalars *dev, cudaStream_t s,
+                              const void *F16, ir_dtype tf16);
+cudaError_t launch_residual_multi(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *Bm, int64_t ldb,
+                                  const double *X, int64_t ldx, double *R, int64_t ldr, double *partials,
+                                  int64_t partials_cap, unsigned long long *rnorm_bits, int sms, cudaStream_t s);
+// The factors kept in TF (binary16 / bfloat16): A_F rounded in place and copied
+// to the 2-byte array F16 (row stride ldf); overflow raises dev->nonfinite.
+cudaError_t launch_store_tf(float *AF, int64_t ldf, int n, ir_dtype tf, void *F16, DevScalars *dev, int sms,
+                            cudaStream_t s);
+// Mixed precision solve pair (k_trsv64.cu): x += s U^{-1} L^{-1} P r in binary64
+// on the binary32 factors; ||d||, ||x|| into dev.
+cudaError_t launch_mps_pair(const float *AF, int64_t ldf, int n, const int32_t *perm, const double *r, double *x,
+                            double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s);
+// One thread runs the solves' bounded tag wait on tags[0] for a tag that is
+// never written, with the limit limit_ns; it sets *timeout when it gives up.
+cudaError_t launch_wait_probe(const unsigned long long *tags, unsigned tag, unsigned long long limit_ns,
+                              int *timeout, cudaStream_t s);
 // r = b - A x (b == NULL: r = A x) and ||r||_inf into rnorm_bits; skip as above.
 cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *b,
                             const double *x, double *r, double *partials, int64_t partials_cap,

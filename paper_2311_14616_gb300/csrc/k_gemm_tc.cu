@@ -1,24 +1,38 @@
 // Tensor-core trailing update of the mixed-precision blocked LU:
-//     A22 <- A22 - rTF(L21) rTF(U12)
-// with the TF-rounded operands (TF32, bf16 or fp16, written by the panel and
-// U12 kernels) multiplied by tcgen05.mma with binary32 accumulation in tensor
-// memory (TMEM), then subtracted from the binary32 matrix in the epilogue.
+//     C <- C - rTF(L21) rTF(U12)
+// with the TF-rounded operands (TF32, bf16 or fp16) multiplied by
+// tcgen05.mma with binary32 accumulation in tensor memory (TMEM), then
+// subtracted from the binary32 matrix in the epilogue.
+//
+// The operands live in "slot" buffers: slot s holds the 64-column K block of
+// one panel, K-major (rows x 64 values, the row's 64 K values contiguous), and
+// a launch applies the slots [s0, s1) one after another.  One block step of
+// the right-looking LU is one slot; a group of G block steps applied at once
+// to the far trailing columns is G slots, which reads and writes the binary32
+// C tile once for all of them instead of once per block step.  Each slot's 64
+// products are summed in their own TMEM accumulator and subtracted from C in
+// binary32 before the next slot's, so C <- fl32(C - D_s) block by block as in
+// the right-looking algorithm; only the C tile's trips to memory are shared.
 //
 // Persistent, warp-specialised kernel, one CTA per SM:
-//   warp 0      TMA producer: both operand tiles of a 128x128 output tile
-//               (K = 64, 128-byte swizzle) into a shared-memory ring, and the
-//               binary32 C tile itself (four 128x32 boxes) into one of two
-//               C buffers
-//   warp 1      allocates TMEM (2 accumulators x 128 columns) and issues the
-//               MMAs from one thread; tcgen05.commit frees the stage and
-//               signals the accumulator
-//   warps 2-9   epilogue: tcgen05.ld the accumulator, C -= D in shared memory,
-//               one thread stores the tile back with TMA (edges are clipped
+//   warp 0      TMA producer: for every output tile the binary32 C tile (four
+//               128x32 boxes) into one of CBUFS C buffers, then the operand
+//               tiles of each slot, one 128-byte K atom (128 rows, 128-byte
+//               swizzle) of A and of B per stage of a shared-memory ring
+//   warp 1      allocates TMEM (a ring of 4 accumulators x 128 columns) and
+//               issues the MMAs from one thread, one accumulator per slot;
+//               tcgen05.commit frees each stage and signals the accumulator
+//   warps 2-9   epilogue: each thread holds 64 values of its C row in
+//               registers, and for every slot tcgen05.ld's the accumulator,
+//               frees it and subtracts; then the tile goes back to shared
+//               memory and one thread stores it with TMA (edges are clipped
 //               by the tensor map, so ragged tiles need no guards)
 // Every mbarrier wait is bounded (globaltimer); on timeout the CTA records
 // the error, waits (bounded) for its own copies in flight, frees TMEM and
 // returns.
 #include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include "ir_internal.cuh"
 #include "tc_util.cuh"
@@ -30,13 +44,14 @@ constexpr int BM = 128, BN = 128, K = kPanelNB;
 constexpr int kAtomBytes = BM * 128;      // one 128-row x 128-byte swizzle tile = 16 KB
 constexpr int kThreads = 320;             // 10 warps
 constexpr int kEpiThreads = 256;
-constexpr unsigned kTmemCols = 2 * BN;    // double-buffered accumulator
+constexpr int kRing = 4;                  // slot accumulators in TMEM
+constexpr unsigned kTmemCols = kRing * BN;
 
 struct TcParams {
-    float *C;
-    int64_t ldc;
-    int M, N;
+    int M, N;               // rows and columns of C
     int tiles_n, num_tiles;
+    int a_row0, b_row0;     // operand-map row of C's first row (A) / first column (B)
+    int s0, s1;             // slots [s0, s1) of both operand maps
     unsigned idesc;
     int *timeout;
 };
@@ -69,6 +84,13 @@ __device__ __forceinline__ void tma_load_2d(unsigned dst, const CUtensorMap *map
         "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(mbar)
         : "memory");
 }
+__device__ __forceinline__ void tma_load_3d(unsigned dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(mbar)
+        : "memory");
+}
 __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int c0, int c1, unsigned src) {
     asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
                      reinterpret_cast<uint64_t>(map)),
@@ -78,45 +100,48 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int c0, int
 
 constexpr int kCBoxBytes = BM * 32 * 4;       // one 128-row x 32-column binary32 box = 16 KB
 constexpr int kCBufBytes = 4 * kCBoxBytes;    // a 128 x 128 C tile = 64 KB
-constexpr int kCBufs = 2;
 
-template <int KATOMS, int STAGES>   // 128-byte K atoms per operand row: 2 for TF32, 1 for 16-bit
+template <int KATOMS, int STAGES, int CBUFS>   // 128-byte K atoms per slot row: 2 for TF32, 1 for 16-bit
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmC, TcParams p) {
     constexpr bool kTF32 = (KATOMS == 2);
     constexpr int kAtomElems = kTF32 ? 32 : 64;          // elements per 128-byte K atom
     constexpr int kKSteps = 128 / 32;                    // MMAs per atom (32-byte K per MMA)
-    constexpr unsigned kStageBytes = 2u * KATOMS * kAtomBytes;
+    constexpr unsigned kStageBytes = 2u * kAtomBytes;              // one K atom of A and of B
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const unsigned sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
-    const unsigned sA = sbase;                                   // STAGES x KATOMS x 16 KB
-    const unsigned sB = sbase + STAGES * KATOMS * kAtomBytes;
-    const unsigned sC = sbase + 2 * STAGES * KATOMS * kAtomBytes; // kCBufs x 64 KB
-    unsigned char *gC = gbase + 2 * STAGES * KATOMS * kAtomBytes;
-    uint64_t *bars = reinterpret_cast<uint64_t *>(gC + kCBufs * kCBufBytes);
+    const unsigned sA = sbase;                                   // STAGES x 16 KB
+    const unsigned sB = sbase + STAGES * kAtomBytes;
+    const unsigned sC = sbase + 2 * STAGES * kAtomBytes;         // CBUFS x 64 KB
+    unsigned char *gC = gbase + 2 * STAGES * kAtomBytes;
+    uint64_t *bars = reinterpret_cast<uint64_t *>(gC + CBUFS * kCBufBytes);
     const unsigned bar0 = smem_u32(bars);
+    constexpr int kAcc0 = 2 * STAGES, kC0 = kAcc0 + 2 * kRing;
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
-    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
-    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 2 + b); };
-    auto cfull_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 4 + b); };
-    auto cempty_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 6 + b); };
-    auto cdone_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + 8 + b); };   // epilogue wrote C
-    const unsigned drain_bar = bar0 + 8u * (2 * STAGES + 10);
-    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * STAGES + 11);
+    auto accf_bar = [&](int b) { return bar0 + 8u * (kAcc0 + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (kAcc0 + kRing + b); };
+    auto cfull_bar = [&](int b) { return bar0 + 8u * (kC0 + b); };
+    auto cempty_bar = [&](int b) { return bar0 + 8u * (kC0 + CBUFS + b); };
+    auto cdone_bar = [&](int b) { return bar0 + 8u * (kC0 + 2 * CBUFS + b); };   // epilogue wrote C
+    const unsigned drain_bar = bar0 + 8u * (kC0 + 3 * CBUFS);
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + kC0 + 3 * CBUFS + 1);
     volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nslots = p.s1 - p.s0;
     if (threadIdx.x == 0) {
         for (int s = 0; s < STAGES; ++s) {
             mbar_init(full_bar(s), 1);
             mbar_init(empty_bar(s), 1);
         }
-        for (int b = 0; b < 2; ++b) {
+        for (int b = 0; b < kRing; ++b) {
             mbar_init(accf_bar(b), 1);
             mbar_init(acce_bar(b), kEpiThreads);
+        }
+        for (int b = 0; b < CBUFS; ++b) {
             mbar_init(cfull_bar(b), 1);
             mbar_init(cempty_bar(b), 1);
             mbar_init(cdone_bar(b), kEpiThreads);
@@ -140,26 +165,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int s = 0;
             unsigned ph = 0;
-            unsigned last_ph[STAGES], last_cph[kCBufs];  // parity of the latest fill of each buffer
-            bool issued[STAGES], cissued[kCBufs];
+            unsigned last_ph[STAGES], last_cph[CBUFS];  // parity of the latest fill of each buffer
+            bool issued[STAGES], cissued[CBUFS];
             for (int q = 0; q < STAGES; ++q) issued[q] = false;
-            for (int q = 0; q < kCBufs; ++q) cissued[q] = false;
+            for (int q = 0; q < CBUFS; ++q) cissued[q] = false;
             int it = 0;
-            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++it) {
                 const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
-                if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.timeout)) break;
-                mbar_arrive_expect_tx(full_bar(s), kStageBytes);
-#pragma unroll
-                for (int q = 0; q < KATOMS; ++q) {
-                    tma_load_2d(sA + (s * KATOMS + q) * kAtomBytes, &tmA, q * kAtomElems, tm * BM, full_bar(s));
-                    tma_load_2d(sB + (s * KATOMS + q) * kAtomBytes, &tmB, q * kAtomElems, tn * BN, full_bar(s));
-                }
-                last_ph[s] = ph;
-                issued[s] = true;
-                if (++s == STAGES) { s = 0; ph ^= 1u; }
-                // the C tile
-                const int cb = it & 1;
-                const unsigned cph = (unsigned)(it >> 1) & 1u;
+                // the C tile first: the epilogue needs it before the first slot's result
+                const int cb = it % CBUFS;
+                const unsigned cph = (unsigned)(it / CBUFS) & 1u;
                 if (!mbar_wait(cempty_bar(cb), cph ^ 1u, abort_flag, p.timeout)) break;
                 mbar_arrive_expect_tx(cfull_bar(cb), (unsigned)kCBufBytes);
 #pragma unroll
@@ -167,13 +183,23 @@ __global__ void __launch_bounds__(kThreads, 1)
                     tma_load_2d(sC + cb * kCBufBytes + q * kCBoxBytes, &tmC, tn * BN + 32 * q, tm * BM, cfull_bar(cb));
                 last_cph[cb] = cph;
                 cissued[cb] = true;
+                for (int sl = p.s0; ok && sl < p.s1; ++sl)
+                    for (int q = 0; q < KATOMS; ++q) {        // one stage per 128-byte K atom
+                        if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.timeout)) { ok = false; break; }
+                        mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+                        tma_load_3d(sA + s * kAtomBytes, &tmA, q * kAtomElems, p.a_row0 + tm * BM, sl, full_bar(s));
+                        tma_load_3d(sB + s * kAtomBytes, &tmB, q * kAtomElems, p.b_row0 + tn * BN, sl, full_bar(s));
+                        last_ph[s] = ph;
+                        issued[s] = true;
+                        if (++s == STAGES) { s = 0; ph ^= 1u; }
+                    }
             }
             if (*abort_flag) {
                 // drain: wait (bounded) until the copies this thread issued have landed
                 volatile int no_abort = 0;
                 for (int q = 0; q < STAGES; ++q)
                     if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, nullptr);
-                for (int q = 0; q < kCBufs; ++q)
+                for (int q = 0; q < CBUFS; ++q)
                     if (cissued[q]) mbar_wait(cfull_bar(q), last_cph[q], &no_abort, nullptr);
             }
         }
@@ -181,26 +207,30 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (lane == 0) {
             int s = 0;
             unsigned ph = 0;
-            int it = 0;
-            for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
-                const int ab = it & 1;
-                const unsigned aph = (unsigned)(it >> 1) & 1u;
-                if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, p.timeout)) break;
-                tc_fence_after();
-                if (!mbar_wait(full_bar(s), ph, abort_flag, p.timeout)) break;
-                tc_fence_after();
-                const unsigned dt = tmem_base + (unsigned)(ab * BN);
+            unsigned qa = 0;                    // slots issued so far: accumulator qa % kRing
+            bool ok = true;
+            for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x) {
+                for (int sl = 0; sl < nslots; ++sl, ++qa) {
+                    const int ab = (int)(qa % kRing);
+                    const unsigned aph = (qa / kRing) & 1u;
+                    if (!mbar_wait(acce_bar(ab), aph ^ 1u, abort_flag, p.timeout)) { ok = false; break; }
+                    tc_fence_after();
+                    const unsigned dt = tmem_base + (unsigned)(ab * BN);
+                    for (int q = 0; q < KATOMS; ++q) {
+                        if (!mbar_wait(full_bar(s), ph, abort_flag, p.timeout)) { ok = false; break; }
+                        tc_fence_after();
 #pragma unroll
-                for (int q = 0; q < KATOMS; ++q)
-#pragma unroll
-                    for (int kk = 0; kk < kKSteps; ++kk) {
-                        const uint64_t ad = make_desc(sA + (s * KATOMS + q) * kAtomBytes + kk * 32);
-                        const uint64_t bd = make_desc(sB + (s * KATOMS + q) * kAtomBytes + kk * 32);
-                        mma<kTF32>(dt, ad, bd, p.idesc, (q | kk) != 0);
+                        for (int kk = 0; kk < kKSteps; ++kk) {
+                            const uint64_t ad = make_desc(sA + s * kAtomBytes + kk * 32);
+                            const uint64_t bd = make_desc(sB + s * kAtomBytes + kk * 32);
+                            mma<kTF32>(dt, ad, bd, p.idesc, (q | kk) != 0);
+                        }
+                        mma_commit(empty_bar(s));
+                        if (++s == STAGES) { s = 0; ph ^= 1u; }
                     }
-                mma_commit(empty_bar(s));
-                mma_commit(accf_bar(ab));
-                if (++s == STAGES) { s = 0; ph ^= 1u; }
+                    if (!ok) break;
+                    mma_commit(accf_bar(ab));
+                }
             }
             if (*abort_flag) {
                 // wait (bounded) until the tensor core has finished everything issued
@@ -217,40 +247,60 @@ __global__ void __launch_bounds__(kThreads, 1)
         const int r = quarter * 32 + lane;                 // row within the tile
         const bool leader = (warp == 2 && lane == 0);
         int it = 0;
-        for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++it) {
+        unsigned qa = 0;
+        bool ok = true;
+        for (int tile = blockIdx.x; ok && tile < p.num_tiles; tile += gridDim.x, ++it) {
             const int tm = tile / p.tiles_n, tn = tile % p.tiles_n;
-            const int ab = it & 1, cb = it & 1;
-            const unsigned aph = (unsigned)(it >> 1) & 1u;
-            if (!mbar_wait(accf_bar(ab), aph, abort_flag, p.timeout)) break;
-            tc_fence_after();
-            float v0[32], v1[32];
-            const unsigned tl = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * BN + half * 64);
-            tmem_ld32(tl, v0);
-            tmem_ld32(tl + 32, v1);
-            tc_fence_before();
-            mbar_arrive(acce_bar(ab));                     // the accumulator may be reused
-            if (!mbar_wait(cfull_bar(cb), aph, abort_flag, p.timeout)) break;
-            // C -= D in the 128B-swizzled boxes: 16-byte chunk c16 of row r sits at c16 ^ (r & 7)
+            const int cb = it % CBUFS;
+            const unsigned cph = (unsigned)(it / CBUFS) & 1u;
+            if (!mbar_wait(cfull_bar(cb), cph, abort_flag, p.timeout)) break;
+            // this thread's 64 values of row r, from the 128B-swizzled boxes:
+            // 16-byte chunk c16 of row r sits at c16 ^ (r & 7)
+            float c[64];
 #pragma unroll
             for (int h = 0; h < 2; ++h) {
-                const float *v = h ? v1 : v0;
-                unsigned char *box = gC + cb * kCBufBytes + (half * 2 + h) * kCBoxBytes + r * 128;
+                const unsigned char *box = gC + cb * kCBufBytes + (half * 2 + h) * kCBoxBytes + r * 128;
 #pragma unroll
                 for (int c16 = 0; c16 < 8; ++c16) {
-                    float4 *q4 = reinterpret_cast<float4 *>(box + ((c16 ^ (r & 7)) << 4));
-                    float4 c = *q4;
-                    c.x -= v[4 * c16 + 0];
-                    c.y -= v[4 * c16 + 1];
-                    c.z -= v[4 * c16 + 2];
-                    c.w -= v[4 * c16 + 3];
-                    *q4 = c;
+                    const float4 v4 = *reinterpret_cast<const float4 *>(box + ((c16 ^ (r & 7)) << 4));
+                    c[32 * h + 4 * c16 + 0] = v4.x;
+                    c[32 * h + 4 * c16 + 1] = v4.y;
+                    c[32 * h + 4 * c16 + 2] = v4.z;
+                    c[32 * h + 4 * c16 + 3] = v4.w;
                 }
+            }
+            for (int sl = 0; sl < nslots; ++sl, ++qa) {
+                const int ab = (int)(qa % kRing);
+                const unsigned aph = (qa / kRing) & 1u;
+                if (!mbar_wait(accf_bar(ab), aph, abort_flag, p.timeout)) { ok = false; break; }
+                tc_fence_after();
+                float v0[32], v1[32];
+                const unsigned tl = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * BN + half * 64);
+                tmem_ld32(tl, v0);
+                tmem_ld32(tl + 32, v1);
+                tc_fence_before();
+                mbar_arrive(acce_bar(ab));                 // the accumulator may be reused
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    c[q] -= v0[q];
+                    c[32 + q] -= v1[q];
+                }
+            }
+            if (!ok) break;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                unsigned char *box = gC + cb * kCBufBytes + (half * 2 + h) * kCBoxBytes + r * 128;
+#pragma unroll
+                for (int c16 = 0; c16 < 8; ++c16)
+                    *reinterpret_cast<float4 *>(box + ((c16 ^ (r & 7)) << 4)) =
+                        make_float4(c[32 * h + 4 * c16], c[32 * h + 4 * c16 + 1], c[32 * h + 4 * c16 + 2],
+                                    c[32 * h + 4 * c16 + 3]);
             }
             // make the generic-proxy writes visible to the TMA store, then signal
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             mbar_arrive(cdone_bar(cb));
             if (leader) {
-                if (!mbar_wait(cdone_bar(cb), aph, abort_flag, p.timeout)) break;
+                if (!mbar_wait(cdone_bar(cb), cph, abort_flag, p.timeout)) break;
 #pragma unroll
                 for (int q = 0; q < 4; ++q) tma_store_2d(&tmC, tn * BN + 32 * q, tm * BM, sC + cb * kCBufBytes + q * kCBoxBytes);
                 asm volatile("cp.async.bulk.commit_group;" ::: "memory");
@@ -269,22 +319,56 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
 }
 
+// Pack rTF of the binary32 factor columns [c0, c0 + 64 G) for the rows
+// [r0, r1) into G slots of `rows` x 64 values each (slot s = columns
+// c0 + 64 s .. c0 + 64 s + 63; row i of the matrix at slot row i - c0).
+// One thread per 4 consecutive values of one row; A_F is row-major, so a row's
+// 64 G values are contiguous and both the read and the write are coalesced.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack_slots(const float *AF, int64_t ldf, int c0, int G, int r0, int r1,
+                                                    int64_t rows, ir_dtype tf, T *out) {
+    const int q4 = 16 * G;                                  // float4 per row
+    const int64_t total = (int64_t)(r1 - r0) * q4;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int i = r0 + (int)(e / q4), q = (int)(e % q4);
+        const float4 v = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + c0 + 4 * q);
+        const int s = q / 16, k = 4 * (q % 16);
+        T *dst = out + ((int64_t)s * rows + (i - c0)) * K + k;
+        if constexpr (sizeof(T) == 4) {
+            uint32_t u[4];
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u[0]) : "f"(v.x));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u[1]) : "f"(v.y));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u[2]) : "f"(v.z));
+            asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(u[3]) : "f"(v.w));
+            *reinterpret_cast<uint4 *>(dst) = make_uint4(u[0], u[1], u[2], u[3]);
+        } else if (tf == IR_BF16) {
+            __nv_bfloat162 p2[2] = {__floats2bfloat162_rn(v.x, v.y), __floats2bfloat162_rn(v.z, v.w)};
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<uint2 *>(p2);
+        } else {
+            __half2 p2[2] = {__floats2half2_rn(v.x, v.y), __floats2half2_rn(v.z, v.w)};
+            *reinterpret_cast<uint2 *>(dst) = *reinterpret_cast<uint2 *>(p2);
+        }
+    }
+}
+
 using EncodeTiledFn = TensorMapEncodeFn;
 EncodeTiledFn get_encoder() { return tensor_map_encoder(); }
 
-// rows x K operand, row-major, K contiguous; box = one 128-byte K atom x 128 rows.
-bool make_map(CUtensorMap *m, const void *base, int rows, ir_dtype tf) {
+// Operand slots: `slots` x rows x K, K contiguous (K-major); box = one 128-byte
+// K atom x 128 rows x 1 slot.
+bool make_slot_map(CUtensorMap *m, const void *base, int64_t rows, int slots, ir_dtype tf) {
     EncodeTiledFn enc = get_encoder();
     if (!enc) return false;
     const int esz = (tf == IR_TF32) ? 4 : 2;
     const CUtensorMapDataType dt = (tf == IR_TF32) ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                    : (tf == IR_BF16) ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
-    cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)K * esz};
-    cuuint32_t box[2] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM};
-    cuuint32_t estr[2] = {1, 1};
-    return enc(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+    cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slots};
+    cuuint64_t strides[2] = {(cuuint64_t)K * esz, (cuuint64_t)rows * K * esz};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM, 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
@@ -311,38 +395,36 @@ unsigned make_idesc(ir_dtype tf) {
     return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(BM >> 4) << 24);
 }
 
-template <int KATOMS, int STAGES>
-size_t smem_bytes() {
-    return 1024 + 2 * STAGES * KATOMS * kAtomBytes + kCBufs * kCBufBytes + 8 * (2 * STAGES + 11) + 16;
+template <int KATOMS, int STAGES, int CBUFS>
+constexpr size_t smem_bytes() {
+    return 1024 + 2 * STAGES * kAtomBytes + CBUFS * kCBufBytes + 8 * (2 * STAGES + 2 * kRing + 1 + 3 * CBUFS) + 16;
 }
+// 3 stages of one K atom (32 KB for A and B) and 2 C buffers (64 KB each)
+static_assert(smem_bytes<1, 3, 2>() <= 232448, "16-bit configuration exceeds shared memory");
+static_assert(smem_bytes<2, 3, 2>() <= 232448, "TF32 configuration exceeds shared memory");
 
-}  // namespace
-
-// Columns [cb, ce) of the trailing matrix (cb a multiple of 64); at most
-// max_ctas persistent CTAs (0: one per SM).
-cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce, ir_dtype tf,
-                           const void *Aop, const void *Bop, int sms, int max_ctas, DevScalars *dev,
-                           cudaStream_t s) {
-    const int m = n - (j + nb);
-    if (m <= 0 || ce <= cb) return cudaSuccess;
-    if (nb != K) return cudaErrorInvalidValue;
-    const int ncols = ce - cb;
-    const size_t esz = (tf == IR_TF32) ? 4 : 2;
-    const void *Bsub = static_cast<const char *>(Bop) + (size_t)(cb - (j + nb)) * K * esz;
-    CUtensorMap ta, tb;
-    if (!make_map(&ta, Aop, m, tf) || !make_map(&tb, Bsub, ncols, tf)) return cudaErrorInvalidValue;
+// Launch one update of C (rows x cols, binary32, row stride ldf) by the slots
+// [s0, s1) of the operand maps; a_row0 / b_row0: operand rows of C's first
+// row / column.  max_ctas > 0: share the GPU with a concurrent panel (8-CTA
+// clusters, two clusters fewer than fit at once).
+cudaError_t launch_slots(float *C, int64_t ldf, int rows, int cols, const CUtensorMap &ta, const CUtensorMap &tb,
+                         int a_row0, int b_row0, int s0, int s1, ir_dtype tf, int sms, int max_ctas,
+                         DevScalars *dev, cudaStream_t s) {
+    if (rows <= 0 || cols <= 0 || s1 <= s0) return cudaSuccess;
     TcParams p;
-    p.C = AF + (int64_t)(j + nb) * ldf + cb;
-    p.ldc = ldf;
-    p.M = m;
-    p.N = ncols;
-    const int tiles_m = (m + BM - 1) / BM;
-    p.tiles_n = (ncols + BN - 1) / BN;
+    p.M = rows;
+    p.N = cols;
+    const int tiles_m = (rows + BM - 1) / BM;
+    p.tiles_n = (cols + BN - 1) / BN;
     p.num_tiles = tiles_m * p.tiles_n;
+    p.a_row0 = a_row0;
+    p.b_row0 = b_row0;
+    p.s0 = s0;
+    p.s1 = s1;
     p.idesc = make_idesc(tf);
     p.timeout = &dev->timeout;
     CUtensorMap tc;
-    if (!make_c_map(&tc, p.C, m, ncols, ldf)) return cudaErrorInvalidValue;
+    if (!make_c_map(&tc, C, rows, cols, ldf)) return cudaErrorInvalidValue;
     const bool share = max_ctas > 0;
     int grid = p.num_tiles < sms ? p.num_tiles : sms;
     auto launch = [&](auto kern, size_t smem) -> cudaError_t {
@@ -351,8 +433,6 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb,
             kern<<<grid, kThreads, smem, s>>>(ta, tb, tc, p);
             return cudaGetLastError();
         }
-        // share the GPU with a concurrent panel: clusters of 8 CTAs, two
-        // clusters fewer than fit at once, so whole GPC slots stay free
         cudaLaunchConfig_t cfg = {};
         cfg.blockDim = dim3(kThreads, 1, 1);
         cfg.dynamicSmemBytes = smem;
@@ -377,23 +457,73 @@ cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb,
     };
     if (tf == IR_TF32) {
         static bool attr = false;
-        const size_t sm = smem_bytes<2, 1>();
+        constexpr size_t sm = smem_bytes<2, 3, 2>();
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        return launch(k_gemm_tc<2, 1>, sm);
+        return launch(k_gemm_tc<2, 3, 2>, sm);
     } else {
         static bool attr = false;
-        const size_t sm = smem_bytes<1, 2>();
+        constexpr size_t sm = smem_bytes<1, 3, 2>();
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        return launch(k_gemm_tc<1, 2>, sm);
+        return launch(k_gemm_tc<1, 3, 2>, sm);
     }
+}
+
+}  // namespace
+
+// One block step: rows [j + nb, n) x columns [cb, ce) of the trailing matrix
+// (cb a multiple of 64) by the step's operands (Aop: rows j + nb .. n - 1,
+// Bop: columns j + nb .. n - 1, K = 64 each); at most max_ctas persistent
+// CTAs (0: one per SM).
+cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce, ir_dtype tf,
+                           const void *Aop, const void *Bop, int sms, int max_ctas, DevScalars *dev,
+                           cudaStream_t s) {
+    const int m = n - (j + nb);
+    if (m <= 0 || ce <= cb) return cudaSuccess;
+    if (nb != K) return cudaErrorInvalidValue;
+    CUtensorMap ta, tb;
+    if (!make_slot_map(&ta, Aop, m, 1, tf) || !make_slot_map(&tb, Bop, m, 1, tf)) return cudaErrorInvalidValue;
+    return launch_slots(AF + (int64_t)(j + nb) * ldf + cb, ldf, m, ce - cb, ta, tb, 0, cb - (j + nb), 0, 1, tf,
+                        sms, max_ctas, dev, s);
+}
+
+// Group update (see the file comment): C = rows [r0, r1) x columns [cb, ce) of
+// A_F minus the products of the group's slots [s0, s1).  Agrp: G slots of
+// a_rows rows (slot row i - c0 holds rTF of row i of the group's L columns);
+// Bgrp: G slots of b_rows rows (slot row c - bbase holds rTF(U) of column c).
+cudaError_t launch_gemm_tc_group(float *AF, int64_t ldf, int c0, int G, int r0, int r1, int cb, int ce,
+                                 int s0, int s1, ir_dtype tf, const void *Agrp, int64_t a_rows, const void *Bgrp,
+                                 int64_t b_rows, int bbase, int sms, int max_ctas, DevScalars *dev,
+                                 cudaStream_t s) {
+    if (r1 <= r0 || ce <= cb || s1 <= s0) return cudaSuccess;
+    CUtensorMap ta, tb;
+    if (!make_slot_map(&ta, Agrp, a_rows, G, tf) || !make_slot_map(&tb, Bgrp, b_rows, G, tf))
+        return cudaErrorInvalidValue;
+    return launch_slots(AF + (int64_t)r0 * ldf + cb, ldf, r1 - r0, ce - cb, ta, tb, r0 - c0, cb - bbase, s0, s1, tf,
+                        sms, max_ctas, dev, s);
+}
+
+// rTF of the factor columns [c0, c0 + 64 G), rows [r0, r1), into the G slots of
+// `rows` rows each (row i at slot row i - c0).
+cudaError_t launch_pack_slots(const float *AF, int64_t ldf, int c0, int G, int r0, int r1, int64_t rows, ir_dtype tf,
+                              void *out, int sms, cudaStream_t s) {
+    if (r1 <= r0 || G <= 0) return cudaSuccess;
+    count_launch();
+    const int64_t total = (int64_t)(r1 - r0) * 16 * G;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8 * sms) blocks = 8 * sms;
+    if (tf == IR_TF32)
+        k_pack_slots<float><<<(int)blocks, 256, 0, s>>>(AF, ldf, c0, G, r0, r1, rows, tf, static_cast<float *>(out));
+    else
+        k_pack_slots<__half><<<(int)blocks, 256, 0, s>>>(AF, ldf, c0, G, r0, r1, rows, tf, static_cast<__half *>(out));
+    return cudaGetLastError();
 }
 
 }  // namespace ir

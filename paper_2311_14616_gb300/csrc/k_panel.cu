@@ -370,6 +370,34 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp(float *AF, int64_t ldf, int c
     for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
 }
 
+// The interchanges of several consecutive panels, in order, on the columns
+// [c0, c1): lists `first` .. `first + count - 1` of a ring of `ring` swap lists
+// (kListInts ints each).  One thread per column; each list's sources are read
+// before its destinations are written, and list t + 1 sees list t's result.
+__global__ void __launch_bounds__(kLaswpT) k_laswp_lists(float *AF, int64_t ldf, int c0, int c1,
+                                                        const int32_t *lists, int list_ints, int ring, int first,
+                                                        int count) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ int sd[2 * NB], ss[2 * NB];
+    __shared__ float vals[2 * NB][kLaswpT];
+    const int c = c0 + blockIdx.x * blockDim.x + threadIdx.x;
+    for (int t = 0; t < count; ++t) {
+        const int32_t *sl = lists + (int64_t)((first + t) % ring) * list_ints;
+        const int cnt = sl[0];
+        __syncthreads();                         // the previous list's entries are no longer read
+        for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+            sd[e] = sl[1 + 2 * e];
+            ss[e] = sl[2 + 2 * e];
+        }
+        __syncthreads();
+        if (c < c1) {
+            for (int e = 0; e < cnt; ++e) vals[e][threadIdx.x] = AF[(int64_t)ss[e] * ldf + c];
+            for (int e = 0; e < cnt; ++e) AF[(int64_t)sd[e] * ldf + c] = vals[e][threadIdx.x];
+        }
+    }
+}
+
 // U12 = L11^{-1} A12 for the block row j..j+NB and the columns [cb, ce): one
 // CTA of 256 threads per 64 columns (lu::trsm64).
 constexpr int kNarrowCols = 64;
@@ -379,6 +407,33 @@ __global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int
     pdl_wait();
     __shared__ __align__(16) float Lt[NB][lu::kLd];
     lu::trsm64(AF, ldf, cb + blockIdx.x * kNarrowCols, ce, j, tf, Bop, Lt);
+}
+
+// U12 of a group's rows for the far columns [cb, ce) of the tensor-core LU,
+// one CTA per 64 columns, the group's G block rows in order: for block t, the
+// binary32 U12 solve (lu::trsm64, writing rTF(U) into operand slot t), then the
+// group's later block rows take block t's update (binary32 sum of the TF-rounded
+// products, subtracted) -- the right-looking LU's block steps restricted to the
+// group's rows.  bop0: slot 0's base shifted so that trsm64's operand row
+// c - (j + 64) lands at row c - cb; slot t is bslot bytes further.
+__global__ void __launch_bounds__(256) k_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce,
+                                                    ir_dtype tf, char *bop0, int64_t bslot) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ __align__(16) float Lt[NB][lu::kLd];   // trsm64's L11, then the update's L tile
+    __shared__ __align__(16) float Bs[NB][lu::kLd];
+    const int col0 = cb + blockIdx.x * kNarrowCols;
+    const size_t esz = (tf == IR_TF32) ? 4 : 2;
+    for (int t = 0; t < G; ++t) {
+        const int jt = c0 + NB * t;
+        char *bt = bop0 + t * bslot + (int64_t)(NB * t) * NB * (int64_t)esz;
+        lu::trsm64(AF, ldf, col0, ce, jt, tf, bt, Lt);
+        __syncthreads();                                   // this block row's U is in A_F
+        for (int t2 = t + 1; t2 < G; ++t2) {
+            lu::gemm_tile64_tf(AF, ldf, jt, col0, ce, c0 + NB * t2, tf, Lt, Bs);
+            __syncthreads();                               // the tiles are restaged next
+        }
+    }
 }
 
 __global__ void k_iota(int n, int32_t *perm) {
@@ -434,6 +489,20 @@ cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int 
     return cudaLaunchKernelEx(&cfg, k_laswp, AF, ldf, c0a, c1a, c0b, c1b, swap_list);
 }
 
+cudaError_t launch_laswp_lists(float *AF, int64_t ldf, int c0, int c1, const int32_t *lists, int list_ints, int ring,
+                               int first, int count, cudaStream_t s) {
+    if (c1 <= c0 || count <= 0) return cudaSuccess;
+    count_launch();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((c1 - c0 + kLaswpT - 1) / kLaswpT, 1, 1);
+    cfg.blockDim = dim3(kLaswpT, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = set_pdl(&attr[0]);
+    return cudaLaunchKernelEx(&cfg, k_laswp_lists, AF, ldf, c0, c1, lists, list_ints, ring, first, count);
+}
+
 // U12 for the columns [cb, ce) of the block row j..j+NB.
 cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop, cudaStream_t s) {
     const int ncols = ce - cb;
@@ -447,6 +516,24 @@ cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype 
     cfg.attrs = attr;
     cfg.numAttrs = set_pdl(&attr[0]);
     return cudaLaunchKernelEx(&cfg, k_trsm_narrow, AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
+}
+
+cudaError_t launch_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf, void *Bgrp,
+                              int64_t bslot, cudaStream_t s) {
+    const int ncols = ce - cb;
+    if (ncols <= 0 || G <= 0) return cudaSuccess;
+    count_launch();
+    // slot 0's operand row for column c must be c - cb: trsm64 writes row c - (c0 + 64), so shift by cb - c0 - 64
+    const size_t esz = (tf == IR_TF32) ? 4 : 2;
+    char *bop0 = static_cast<char *>(Bgrp) - (int64_t)(cb - (c0 + NB)) * NB * (int64_t)esz;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ncols + kNarrowCols - 1) / kNarrowCols, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = set_pdl(&attr[0]);
+    return cudaLaunchKernelEx(&cfg, k_trsm_group, AF, ldf, c0, G, cb, ce, tf, bop0, bslot);
 }
 
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s) {

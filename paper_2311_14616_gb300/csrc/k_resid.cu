@@ -96,6 +96,85 @@ __global__ void k_resid_final(int64_t n, const TW *b, const double *partials, in
     if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rnorm_bits, m);
 }
 
+// K columns at once: R(:, j) = B(:, j) - A X(:, j); A is read once for all
+// columns, each thread keeping 2 rows x K sums (the same fma chain per column
+// as k_resid_partial); partials[(split * K + j) * n + i].
+template <typename TW, int K>
+__global__ void __launch_bounds__(RT) k_mresid_partial(int64_t n, const TW *A, int64_t lda, const double *X,
+                                                       int64_t ldx, int64_t cols_per_split, double *partials,
+                                                       int vec_ok) {
+    __shared__ double xs[K][XCH / 2];
+    constexpr int XC = XCH / 2;
+    const int64_t i = (int64_t)blockIdx.x * RB + 2 * threadIdx.x;
+    const int64_t c0 = (int64_t)blockIdx.y * cols_per_split;
+    int64_t c1 = c0 + cols_per_split;
+    if (c1 > n) c1 = n;
+    double s0[K], s1[K];
+#pragma unroll
+    for (int j = 0; j < K; ++j) s0[j] = s1[j] = 0.0;
+    const bool both = (i + 1 < n);
+    for (int64_t cb = c0; cb < c1; cb += XC) {
+        const int64_t ce = (cb + XC < c1) ? cb + XC : c1;
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < K * (ce - cb); e += RT) {
+            const int j = (int)(e / (ce - cb));
+            const int64_t c = cb + e % (ce - cb);
+            xs[j][c - cb] = X[j * ldx + c];
+        }
+        __syncthreads();
+        if (i >= n) continue;
+        const TW *col = A + i + cb * lda;
+        const int cnt = (int)(ce - cb);
+        if (vec_ok && both) {
+            using V = typename Vec2<TW>::T;
+            for (int c = 0; c < cnt; ++c) {
+                const V a = __ldg(reinterpret_cast<const V *>(col + (int64_t)c * lda));
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    s0[j] = fma((double)a.x, xs[j][c], s0[j]);
+                    s1[j] = fma((double)a.y, xs[j][c], s1[j]);
+                }
+            }
+        } else {
+            for (int c = 0; c < cnt; ++c) {
+                const double a0 = (double)__ldg(col + (int64_t)c * lda);
+                const double a1 = both ? (double)__ldg(col + (int64_t)c * lda + 1) : 0.0;
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    s0[j] = fma(a0, xs[j][c], s0[j]);
+                    s1[j] = fma(a1, xs[j][c], s1[j]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < K; ++j) {
+        if (i < n) partials[((int64_t)blockIdx.y * K + j) * n + i] = s0[j];
+        if (both) partials[((int64_t)blockIdx.y * K + j) * n + i + 1] = s1[j];
+    }
+}
+
+template <typename TW, int K>
+__global__ void k_mresid_final(int64_t n, const TW *Bm, int64_t ldb, const double *partials, int nsplit, double *R,
+                               int64_t ldr, unsigned long long *rnorm_bits) {
+    const int j = blockIdx.y;
+    double m = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double s = partials[(int64_t)j * n + i];
+        for (int k = 1; k < nsplit; ++k) s += partials[((int64_t)k * K + j) * n + i];
+        const double ri = (double)Bm[j * ldb + i] - s;
+        R[j * ldr + i] = ri;
+        m = fmax(m, fabs(ri));
+        if (ri != ri) m = ri;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        double v = __shfl_xor_sync(0xffffffffu, m, o);
+        m = (v != v || v > m) ? v : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(rnorm_bits + j, m);
+}
+
 int nsplit_for(int64_t n, int sms) {
     const int64_t rowblocks = (n + RB - 1) / RB;
     int64_t ns = (4 * (int64_t)sms + rowblocks - 1) / rowblocks;
@@ -133,6 +212,37 @@ cudaError_t launch_residual(int64_t n, ir_dtype tw, const void *A, int64_t lda, 
         k_resid_partial<float><<<grid, RT, 0, s>>>(n, (const float *)A, lda, x, cps, partials, vec_ok, skip);
         count_launch();
         k_resid_final<float><<<fg, 256, 0, s>>>(n, (const float *)b, partials, ns, r, rnorm_bits, skip);
+    }
+    return cudaGetLastError();
+}
+
+// R(:, j) = B(:, j) - A X(:, j) for j < 4 and ||R(:, j)||_inf into rnorm_bits[j];
+// partials: nsplit * 4 * n doubles (residual_partials_needed(n, sms) * 4).
+cudaError_t launch_residual_multi(int64_t n, ir_dtype tw, const void *A, int64_t lda, const void *Bm, int64_t ldb,
+                                  const double *X, int64_t ldx, double *R, int64_t ldr, double *partials,
+                                  int64_t partials_cap, unsigned long long *rnorm_bits, int sms, cudaStream_t s) {
+    constexpr int K = 4;
+    if (n == 0) return cudaSuccess;
+    const int ns = nsplit_for(n, sms);
+    if ((int64_t)ns * n * K > partials_cap) return cudaErrorInvalidValue;
+    const int64_t cps = (n + ns - 1) / ns;
+    const int64_t rowblocks = (n + RB - 1) / RB;
+    dim3 grid((unsigned)rowblocks, (unsigned)ns);
+    const size_t esz = (tw == IR_F64) ? 8 : 4;
+    const int vec_ok = ((lda % 2) == 0) && (((uintptr_t)A % (2 * esz)) == 0);
+    cudaError_t e = cudaMemsetAsync(rnorm_bits, 0, K * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return e;
+    const int fg = (int)((n + 255) / 256 < 256 ? (n + 255) / 256 : 256);
+    count_launch();
+    count_launch();
+    if (tw == IR_F64) {
+        k_mresid_partial<double, K><<<grid, RT, 0, s>>>(n, (const double *)A, lda, X, ldx, cps, partials, vec_ok);
+        k_mresid_final<double, K><<<dim3(fg, K), 256, 0, s>>>(n, (const double *)Bm, ldb, partials, ns, R, ldr,
+                                                              rnorm_bits);
+    } else {
+        k_mresid_partial<float, K><<<grid, RT, 0, s>>>(n, (const float *)A, lda, X, ldx, cps, partials, vec_ok);
+        k_mresid_final<float, K><<<dim3(fg, K), 256, 0, s>>>(n, (const float *)Bm, ldb, partials, ns, R, ldr,
+                                                             rnorm_bits);
     }
     return cudaGetLastError();
 }

@@ -15,6 +15,11 @@
 // solve is a chain of N / B dependent block steps, so the block is large:
 // 512 threads, warp w owns rows 8w .. 8w+7 of the block and lane l columns
 // l, l+32, l+64, l+96 of every 128-column tile.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <type_traits>
+
 #include "ir_internal.cuh"
 
 namespace ir {
@@ -150,9 +155,10 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Wait (bounded, with a short back-off) until the word carries `tag`; return its value.
+// Wait (bounded by limit_ns, with a short back-off) until the word carries `tag`;
+// return its value.  On timeout: *timeout = 1 and 0 is returned.
 __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsigned tag,
-                                             int *timeout) {
+                                             int *timeout, unsigned long long limit_ns = kWaitLimitNs) {
     unsigned long long v = ld_relaxed_u64(p);
     if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
     const unsigned long long t0 = globaltimer();
@@ -162,7 +168,7 @@ __device__ __forceinline__ float poll_tagged(const unsigned long long *p, unsign
         if (ns < 64) ns <<= 1;
         v = ld_relaxed_u64(p);
         if ((unsigned)(v >> 32) == tag) return __uint_as_float((unsigned)v);
-        if (*reinterpret_cast<volatile int *>(timeout) || globaltimer() - t0 > kWaitLimitNs) {
+        if (*reinterpret_cast<volatile int *>(timeout) || globaltimer() - t0 > limit_ns) {
             atomicExch(timeout, 1);
             return 0.f;
         }
@@ -282,9 +288,18 @@ __device__ __forceinline__ float sub_pair(float v, float hi, float lo) {
     return __fadd_rn(s, __fsub_rn(e, lo));
 }
 
+// Factor entries as binary32: the binary32 factors themselves, or the 2-byte
+// copy kept in TF (binary16 / bfloat16), promoted exactly.
+__device__ __forceinline__ float factor_value(const float *F, int64_t e) { return __ldg(F + e); }
+__device__ __forceinline__ float factor_value(const __half *F, int64_t e) { return __half2float(__ldg(F + e)); }
+__device__ __forceinline__ float factor_value(const __nv_bfloat16 *F, int64_t e) {
+    return __bfloat162float(__ldg(F + e));
+}
+
 // One 128x128 off-diagonal tile slice: warp w rows 8w..8w+7, lane l columns
 // l + 32c (c < 4) of block column bj.
-__device__ __forceinline__ void load_tile(const float *AF, int64_t ldf, int n, int row0, int bj,
+template <typename T>
+__device__ __forceinline__ void load_tile(const T *AF, int64_t ldf, int n, int row0, int bj,
                                           int lane, float (&a)[8][CPL]) {
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
@@ -292,7 +307,7 @@ __device__ __forceinline__ void load_tile(const float *AF, int64_t ldf, int n, i
 #pragma unroll
         for (int c = 0; c < CPL; ++c) {
             const int col = bj * B + lane + 32 * c;
-            a[q][c] = (i < n && col < n) ? __ldg(AF + (int64_t)i * ldf + col) : 0.f;
+            a[q][c] = (i < n && col < n) ? factor_value(AF, (int64_t)i * ldf + col) : 0.f;
         }
     }
 }
@@ -300,8 +315,8 @@ __device__ __forceinline__ void load_tile(const float *AF, int64_t ldf, int n, i
 // Accumulate the off-diagonal products of block bi: (p[q], pl[q]) += sum_j
 // A[row0+q][j] y_j over the predecessor blocks, in order (compensated); the
 // next tile is in flight while the current one waits for its published values.
-template <bool LOWER>
-__device__ __forceinline__ void offdiag(const float *AF, int64_t ldf, int n, int nblk, int bi,
+template <bool LOWER, typename T>
+__device__ __forceinline__ void offdiag(const T *AF, int64_t ldf, int n, int nblk, int bi,
                                         const unsigned long long *tags, unsigned tag, float *ys,
                                         int *timeout, float (&p)[8], float (&pl)[8]) {
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -412,7 +427,8 @@ __device__ __forceinline__ void stage_diag(const float *AF, int64_t ldf, int n, 
 
 // mode 0 / 2: v = fl32(r[perm[i]] / rho), rho = *rho_bits (||r||; v = 0 when
 // rho = 0); mode 1: v = vin[perm[i]].  Publishes tagged y for the upper solve.
-__global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t ldf, int n, int nblk,
+template <typename T>
+__global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, const T *F, int64_t ldf, int n, int nblk,
                                                       const float *Linv, const int32_t *blk_subst,
                                                       const int32_t *perm, const double *r, const float *vin,
                                                       int mode, const unsigned long long *rho_bits,
@@ -448,7 +464,7 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t l
     float p[8], pl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) p[q] = pl[q] = 0.f;
-    offdiag<true>(AF, ldf, n, nblk, bi, ytag, tag, ys, &dev->timeout, p, pl);
+    offdiag<true>(F, ldf, n, nblk, bi, ytag, tag, ys, &dev->timeout, p, pl);
     __syncthreads();
     {
         float sh, sl;
@@ -476,7 +492,8 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_lower(const float *AF, int64_t l
 // Back substitution with U, reading the tagged y of the lower solve.
 // mode 0: d = (rho s) fl64(z); x += d; ||d||, ||x|| into dev; mode 1: dout = z;
 // mode 2: x = (rho s) fl64(z).
-__global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t ldf, int n, int nblk,
+template <typename T>
+__global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, const T *F, int64_t ldf, int n, int nblk,
                                                       const float *Uinv, const int32_t *blk_subst,
                                                       const unsigned long long *ytag,
                                                       unsigned long long *ztag, unsigned tag,
@@ -504,7 +521,7 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
     float p[8], pl[8];
 #pragma unroll
     for (int q = 0; q < 8; ++q) p[q] = pl[q] = 0.f;
-    offdiag<false>(AF, ldf, n, nblk, bi, ztag, tag, ys, &dev->timeout, p, pl);
+    offdiag<false>(F, ldf, n, nblk, bi, ztag, tag, ys, &dev->timeout, p, pl);
     __syncthreads();
     {
         float sh, sl;
@@ -559,6 +576,183 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_upper(const float *AF, int64_t l
 }
 
 constexpr size_t kSolveSmem = sizeof(float) * (B * (B + 1) + 2 * B);
+
+// ---- several right-hand sides at once ------------------------------------------
+// The same blocked, synchronisation-free pair for K columns of right-hand
+// sides: each factor tile is loaded once and applied to all K columns (per
+// column the products, compensated sums, diagonal solves and the order of the
+// blocks are those of k_trsv_lower / k_trsv_upper), so one block step of the
+// chain serves K refinement loops.  Column j of the tagged words lives at
+// tags + j * ntag.  active[j] = 0: column j takes v = 0 (d = 0, x unchanged).
+constexpr int kRhs = 4;
+constexpr size_t kMultiSmem = sizeof(float) * (B * (B + 1) + 2 * kRhs * B);
+
+template <bool LOWER, typename T>
+__device__ __forceinline__ void offdiag_multi(const T *F, int64_t ldf, int n, int nblk, int bi,
+                                              const unsigned long long *tags, int64_t ntag, unsigned tag,
+                                              float (*ys)[B], int *timeout, float (&p)[kRhs][8],
+                                              float (&pl)[kRhs][8]) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int row0 = bi * B + warp * 8;
+    const int npred = LOWER ? bi : (nblk - 1 - bi);
+    float la[8][CPL], na[8][CPL];
+    if (npred > 0) load_tile(F, ldf, n, row0, LOWER ? 0 : nblk - 1, lane, la);
+    for (int it = 0; it < npred; ++it) {
+        const int bj = LOWER ? it : (nblk - 1 - it);
+        if (it + 1 < npred) load_tile(F, ldf, n, row0, LOWER ? bj + 1 : bj - 1, lane, na);
+        if (warp < kRhs) poll_block(tags + warp * ntag + bj * B, tag, ys[warp], lane, timeout);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < kRhs; ++j) {
+            float y[CPL];
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) y[c] = ys[j][lane + 32 * c];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                float tp = __fmul_rn(la[q][0], y[0]);
+#pragma unroll
+                for (int c = 1; c < CPL; ++c) tp = fmaf(la[q][c], y[c], tp);
+                acc_pair(p[j][q], pl[j][q], tp, 0.f);
+            }
+        }
+        __syncthreads();                       // ys consumed before the next fetch
+#pragma unroll
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int c = 0; c < CPL; ++c) la[q][c] = na[q][c];
+    }
+}
+
+// sv[j] <- sv[j] - (off-diagonal sums of column j), then the diagonal block
+// applied to every column (inverse, or substitution by warps 0 .. K-1).
+template <bool LOWER>
+__device__ __forceinline__ void finish_multi(const float *Ds, bool subst, float (*sv)[B], float (&p)[kRhs][8],
+                                             float (&pl)[kRhs][8]) {
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+#pragma unroll
+    for (int j = 0; j < kRhs; ++j) {
+        float sh, sl;
+        reduce8_pair(p[j], pl[j], lane, sh, sl);
+        if ((lane & 3) == 0) {
+            const int il = warp * 8 + reduce8_row(lane);
+            sv[j][il] = sub_pair(sv[j][il], sh, sl);
+        }
+    }
+    __syncthreads();
+    if (subst) {
+        if (warp < kRhs) diag_subst<LOWER>(Ds, sv[warp], lane);
+    } else {
+        float out[kRhs];
+#pragma unroll
+        for (int j = 0; j < kRhs; ++j) out[j] = diag_apply(Ds, sv[j], warp, lane);
+        __syncthreads();
+        if ((lane & 3) == 0)
+#pragma unroll
+            for (int j = 0; j < kRhs; ++j) sv[j][warp * 8 + reduce8_row(lane)] = out[j];
+    }
+    __syncthreads();
+}
+
+// v_ij = fl32(R[j][perm[i]] / rho_j) (0 when rho_j = 0 or column j inactive);
+// publishes tagged y for the upper solve.
+template <typename T>
+__global__ void __launch_bounds__(TT, 1) k_mtrsv_lower(const float *AF, const T *F, int64_t ldf, int n, int nblk,
+                                                       const float *Linv, const int32_t *blk_subst,
+                                                       const int32_t *perm, const double *R, int64_t ldr,
+                                                       const unsigned long long *rho_bits, const int *active,
+                                                       unsigned long long *ytag, int64_t ntag, unsigned tag,
+                                                       DevScalars *dev) {
+    extern __shared__ __align__(16) float tsm[];
+    float *Ds = tsm;
+    float (*sv)[B] = reinterpret_cast<float (*)[B]>(Ds + B * (B + 1));
+    float (*ys)[B] = sv + kRhs;
+    __shared__ int s_bi;
+    const int t = threadIdx.x;
+    if (t == 0) s_bi = (int)atomicAdd(&dev->ticket[0], 1u);
+    __syncthreads();
+    const int bi = s_bi, r0 = bi * B;
+    const bool subst = blk_subst[bi] != 0;
+    stage_diag<true>(AF, ldf, n, r0, Linv + (int64_t)bi * B * B, subst, Ds);
+    for (int e = t; e < kRhs * B; e += TT) {
+        const int j = e / B, i = r0 + e % B;
+        float v = 0.f;
+        if (i < n && active[j]) {
+            const double rn = __longlong_as_double((long long)rho_bits[j]);
+            v = (rn == 0.0) ? 0.f : __double2float_rn(R[j * ldr + perm[i]] / rn);
+        }
+        sv[j][e % B] = v;
+    }
+    float p[kRhs][8], pl[kRhs][8];
+#pragma unroll
+    for (int j = 0; j < kRhs; ++j)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[j][q] = pl[j][q] = 0.f;
+    offdiag_multi<true>(F, ldf, n, nblk, bi, ytag, ntag, tag, ys, &dev->timeout, p, pl);
+    __syncthreads();
+    finish_multi<true>(Ds, subst, sv, p, pl);
+    for (int e = t; e < kRhs * B; e += TT) {
+        const int j = e / B, i = e % B;
+        const float yv = (r0 + i < n) ? sv[j][i] : 0.f;
+        st_relaxed_u64(ytag + j * ntag + r0 + i, ((unsigned long long)tag << 32) | __float_as_uint(yv));
+    }
+}
+
+// z = U^{-1} y per column; d_ij = (rho_j s) fl64(z_ij), X[j][i] += d_ij for
+// active columns; ||d_j||, ||x_j|| into dnorm_bits[j], xnorm_bits[j].
+template <typename T>
+__global__ void __launch_bounds__(TT, 1) k_mtrsv_upper(const float *AF, const T *F, int64_t ldf, int n, int nblk,
+                                                       const float *Uinv, const int32_t *blk_subst,
+                                                       const unsigned long long *ytag, unsigned long long *ztag,
+                                                       int64_t ntag, unsigned tag,
+                                                       const unsigned long long *rho_bits, const int *active,
+                                                       double *X, int64_t ldx, unsigned long long *dnorm_bits,
+                                                       unsigned long long *xnorm_bits, DevScalars *dev) {
+    extern __shared__ __align__(16) float tsm[];
+    float *Ds = tsm;
+    float (*sv)[B] = reinterpret_cast<float (*)[B]>(Ds + B * (B + 1));
+    float (*ys)[B] = sv + kRhs;
+    __shared__ int s_bi;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) s_bi = nblk - 1 - (int)atomicAdd(&dev->ticket[1], 1u);
+    __syncthreads();
+    const int bi = s_bi, r0 = bi * B;
+    const bool subst = blk_subst[nblk + bi] != 0;
+    stage_diag<false>(AF, ldf, n, r0, Uinv + (int64_t)bi * B * B, subst, Ds);
+    for (int e = t; e < kRhs * B; e += TT) {
+        const int j = e / B, i = r0 + e % B;
+        sv[j][e % B] = (i < n) ? __uint_as_float((unsigned)ld_relaxed_u64(ytag + j * ntag + i)) : 0.f;
+    }
+    float p[kRhs][8], pl[kRhs][8];
+#pragma unroll
+    for (int j = 0; j < kRhs; ++j)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p[j][q] = pl[j][q] = 0.f;
+    offdiag_multi<false>(F, ldf, n, nblk, bi, ztag, ntag, tag, ys, &dev->timeout, p, pl);
+    __syncthreads();
+    finish_multi<false>(Ds, subst, sv, p, pl);
+    // column j is handled by warps 4j .. 4j + 3 (128 rows, one per lane)
+    const int j = warp >> 2, i = r0 + (warp & 3) * 32 + lane;
+    const float zv = (i < n) ? sv[j][i - r0] : 0.f;
+    st_relaxed_u64(ztag + j * ntag + i, ((unsigned long long)tag << 32) | __float_as_uint(zv));
+    double dmax = 0.0, xmax = 0.0;
+    if (i < n && active[j]) {
+        const double scale = __longlong_as_double((long long)rho_bits[j]) * dev->scale;
+        const double d = scale * (double)zv;
+        const double xn = X[j * ldx + i] + d;
+        X[j * ldx + i] = xn;
+        dmax = fabs(d);
+        xmax = fabs(xn);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+        xmax = fmax(xmax, __shfl_xor_sync(0xffffffffu, xmax, o));
+    }
+    if (lane == 0 && active[j]) {
+        atomic_max_nonneg(dnorm_bits + j, dmax);
+        atomic_max_nonneg(xnorm_bits + j, xmax);
+    }
+}
 
 // ---- the solve pair in one thread-block cluster ------------------------------
 // For N <= 16 * 2 * B: CTA c of a cluster of C = min(16, nblk) CTAs owns the
@@ -984,6 +1178,13 @@ __global__ void __launch_bounds__(TT, 1) k_trsv_cluster(const __grid_constant__ 
 }
 #undef OWN
 
+// The correction solves' tag wait on a word that never receives `tag` (one
+// thread): it must give up after limit_ns and raise *timeout.
+__global__ void k_wait_probe(const unsigned long long *tags, unsigned tag, unsigned long long limit_ns,
+                             int *timeout) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) (void)poll_tagged(tags, tag, timeout, limit_ns);
+}
+
 }  // namespace
 
 cudaError_t launch_diag_inv(const float *AF, int64_t ldf, int n, float *Linv, float *Uinv,
@@ -1018,27 +1219,37 @@ static bool cluster_solve_enabled() {
 }
 
 // ytag/ztag: 2 arrays of nblk*B tagged words (flags buffer).  Tickets are reset here.
+cudaError_t launch_wait_probe(const unsigned long long *tags, unsigned tag, unsigned long long limit_ns,
+                              int *timeout, cudaStream_t s) {
+    count_launch();
+    k_wait_probe<<<1, 32, 0, s>>>(tags, tag, limit_ns, timeout);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *Linv,
                              const float *Uinv, const int32_t *blk_subst, const int32_t *perm, const double *r,
                              const float *vin, float *dout, double *x,
                              unsigned long long *tags, unsigned epoch, DevScalars *dev,
                              cudaStream_t s, const unsigned long long *rho_bits, double *pw,
-                             const int *skip) {
+                             const int *skip, bool unit_rho, const void *F16, ir_dtype tf16) {
     if (n == 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_trsv_lower, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem);
-        if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_trsv_upper, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem);
+        cudaError_t e = cudaSuccess;
+        const void *kerns[6] = {(const void *)k_trsv_lower<float>, (const void *)k_trsv_upper<float>,
+                                (const void *)k_trsv_lower<__half>, (const void *)k_trsv_upper<__half>,
+                                (const void *)k_trsv_lower<__nv_bfloat16>, (const void *)k_trsv_upper<__nv_bfloat16>};
+        for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+            e = cudaFuncSetAttribute(kerns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSolveSmem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
     const int nblk = (n + B - 1) / B;
     cudaError_t e = cudaSuccess;
     const int mode = vin ? 1 : (pw ? 2 : 0);
-    if (mode != 2) rho_bits = &dev->rnorm_bits;
+    if (mode != 2) rho_bits = unit_rho ? &dev->one_bits : &dev->rnorm_bits;
     double *xo = (mode == 2) ? pw : x;
-    if (nblk <= kClMaxBlk && cluster_solve_enabled()) {
+    if (!F16 && nblk <= kClMaxBlk && cluster_solve_enabled()) {
         static bool cattr = false;
         if (!cattr) {
             e = cudaFuncSetAttribute(k_trsv_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kClSmem);
@@ -1079,14 +1290,100 @@ cudaError_t launch_trsv_pair(const float *AF, int64_t ldf, int n, const float *L
     e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
     unsigned long long *ytag = tags, *ztag = tags + (int64_t)nblk * B;
-    count_launch();
-    k_trsv_lower<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode, rho_bits, skip,
-                                              ytag, epoch, dev);
-    e = cudaGetLastError();
+    auto pair = [&](auto *F) -> cudaError_t {
+        using T = std::remove_const_t<std::remove_pointer_t<decltype(F)>>;
+        count_launch();
+        k_trsv_lower<T><<<nblk, TT, kSolveSmem, s>>>(AF, F, ldf, n, nblk, Linv, blk_subst, perm, r, vin, mode,
+                                                     rho_bits, skip, ytag, epoch, dev);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) return e2;
+        count_launch();
+        k_trsv_upper<T><<<nblk, TT, kSolveSmem, s>>>(AF, F, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, epoch, mode,
+                                                     rho_bits, skip, xo, dout, dev);
+        return cudaGetLastError();
+    };
+    if (!F16) return pair(AF);
+    if (tf16 == IR_BF16) return pair(static_cast<const __nv_bfloat16 *>(F16));
+    return pair(static_cast<const __half *>(F16));
+}
+
+// The solve pair for kRhs right-hand sides (see k_mtrsv_lower / k_mtrsv_upper).
+cudaError_t launch_trsv_multi(const float *AF, int64_t ldf, int n, const float *Linv, const float *Uinv,
+                              const int32_t *blk_subst, const int32_t *perm, const double *R, int64_t ldr,
+                              const unsigned long long *rho_bits, const int *active, double *X, int64_t ldx,
+                              unsigned long long *dnorm_bits, unsigned long long *xnorm_bits,
+                              unsigned long long *tags, unsigned epoch, DevScalars *dev, cudaStream_t s,
+                              const void *F16, ir_dtype tf16) {
+    if (n == 0) return cudaSuccess;
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaSuccess;
+        const void *kerns[6] = {(const void *)k_mtrsv_lower<float>, (const void *)k_mtrsv_upper<float>,
+                                (const void *)k_mtrsv_lower<__half>, (const void *)k_mtrsv_upper<__half>,
+                                (const void *)k_mtrsv_lower<__nv_bfloat16>,
+                                (const void *)k_mtrsv_upper<__nv_bfloat16>};
+        for (int q = 0; q < 6 && e == cudaSuccess; ++q)
+            e = cudaFuncSetAttribute(kerns[q], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMultiSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    const int nblk = (n + B - 1) / B;
+    const int64_t ntag = (int64_t)nblk * B;
+    cudaError_t e = cudaMemsetAsync(&dev->ticket[0], 0, 2 * sizeof(unsigned), s);
     if (e != cudaSuccess) return e;
+    unsigned long long *ytag = tags, *ztag = tags + kRhs * ntag;
+    auto pair = [&](auto *F) -> cudaError_t {
+        using T = std::remove_const_t<std::remove_pointer_t<decltype(F)>>;
+        count_launch();
+        k_mtrsv_lower<T><<<nblk, TT, kMultiSmem, s>>>(AF, F, ldf, n, nblk, Linv, blk_subst, perm, R, ldr, rho_bits,
+                                                      active, ytag, ntag, epoch, dev);
+        cudaError_t e2 = cudaGetLastError();
+        if (e2 != cudaSuccess) return e2;
+        count_launch();
+        k_mtrsv_upper<T><<<nblk, TT, kMultiSmem, s>>>(AF, F, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, ntag, epoch,
+                                                      rho_bits, active, X, ldx, dnorm_bits, xnorm_bits, dev);
+        return cudaGetLastError();
+    };
+    if (!F16) return pair(AF);
+    if (tf16 == IR_BF16) return pair(static_cast<const __nv_bfloat16 *>(F16));
+    return pair(static_cast<const __half *>(F16));
+}
+
+// The factors kept in TF: every entry of A_F (L and U, rows and columns < n)
+// rounded to TF in place (binary32 storage of the TF value) and written to the
+// 2-byte copy F16 (same layout, row stride ldf); an entry that overflows TF
+// raises the non-finite flag.
+template <typename T>
+__global__ void k_store_tf(float *AF, int64_t ldf, int n, T *F16, DevScalars *dev) {
+    const int64_t total = (int64_t)n * n;
+    int bad = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = e / n, j = e % n;
+        const float v = AF[i * ldf + j];
+        T h;
+        if constexpr (sizeof(T) == 2 && std::is_same<T, __half>::value) h = __float2half_rn(v);
+        else h = __float2bfloat16_rn(v);
+        float w;
+        if constexpr (std::is_same<T, __half>::value) w = __half2float(h);
+        else w = __bfloat162float(h);
+        bad |= (isfinite(v) && !isfinite(w));
+        AF[i * ldf + j] = w;
+        F16[i * ldf + j] = h;
+    }
+    if (bad) atomicExch(&dev->nonfinite, 1);
+}
+
+cudaError_t launch_store_tf(float *AF, int64_t ldf, int n, ir_dtype tf, void *F16, DevScalars *dev, int sms,
+                            cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
     count_launch();
-    k_trsv_upper<<<nblk, TT, kSolveSmem, s>>>(AF, ldf, n, nblk, Uinv, blk_subst, ytag, ztag, epoch, mode, rho_bits,
-                                              skip, xo, dout, dev);
+    const int64_t total = (int64_t)n * n;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 16 * sms) blocks = 16 * sms;
+    if (tf == IR_BF16)
+        k_store_tf<__nv_bfloat16><<<(int)blocks, 256, 0, s>>>(AF, ldf, n, static_cast<__nv_bfloat16 *>(F16), dev);
+    else
+        k_store_tf<__half><<<(int)blocks, 256, 0, s>>>(AF, ldf, n, static_cast<__half *>(F16), dev);
     return cudaGetLastError();
 }
 

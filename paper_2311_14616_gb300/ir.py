@@ -37,7 +37,8 @@ class IRError(RuntimeError):
 
 class Opts(ctypes.Structure):
     _fields_ = [("TW", ctypes.c_int), ("TF", ctypes.c_int), ("TR", ctypes.c_int),
-                ("fp16_scale", ctypes.c_int), ("nb", ctypes.c_int), ("autotune", ctypes.c_int)]
+                ("fp16_scale", ctypes.c_int), ("nb", ctypes.c_int), ("autotune", ctypes.c_int),
+                ("group", ctypes.c_int), ("onthefly", ctypes.c_int), ("store_tf", ctypes.c_int)]
 
 
 class Term(ctypes.Structure):
@@ -102,6 +103,7 @@ def lib():
             "ir_solve": (i32, [vp, vp, vp, P(Term), vp, P(_Report)]),
             "ir_solve_host": (i32, [vp, i64, vp, i64, vp, vp, P(Opts), P(Term), vp, P(_Report)]),
             "ir_lu_solve": (i32, [vp, vp, vp, vp]),
+            "ir_check_wait_timeout": (i32, [vp, ctypes.c_double, vp]),
             "ir_solve_many": (i32, [vp, i64, vp, i64, vp, i64, P(Term), vp, vp]),
             "ir_default_krylov_opts": (None, [P(KrylovOpts)]),
             "ir_gmres_reserve": (i32, [vp, i32]),
@@ -115,7 +117,7 @@ def lib():
             "ir_batch_destroy": (None, [vp]),
             "ir_factor_solve_batched": (i32, [vp, i64, vp, vp, vp, vp, vp, P(Opts), P(Term), vp, vp]),
             "ir_fact_pivots": (i32, [vp, vp]),
-            "ir_fact_schedule": (i32, [vp, P(i32), P(i32)]),
+            "ir_fact_schedule": (i32, [vp, P(i32), P(i32), P(i32)]),
             "ir_batch_schedule": (i32, [vp, P(i32), P(i32)]),
             "ir_fact_factors": (i32, [vp, vp, i64]),
             "ir_fact_info": (i32, [vp, P(i64), P(i32)]),
@@ -183,10 +185,14 @@ def krylov_opts(**kw) -> KrylovOpts:
     return k
 
 
-def make_opts(TW: int, TF: int, fp16_scale: bool = True, nb: int = 0, autotune: bool = False) -> Opts:
+def make_opts(TW: int, TF: int, fp16_scale: bool = True, nb: int = 0, autotune: bool = False,
+              group: int = 0, onthefly: bool = False, store_tf: bool = False) -> Opts:
     o = Opts()
     lib().ir_default_opts(ctypes.byref(o))
     o.TW, o.TF, o.TR, o.fp16_scale, o.nb, o.autotune = TW, TF, F64, int(fp16_scale), nb, int(autotune)
+    o.group = int(group)
+    o.onthefly = int(onthefly)
+    o.store_tf = int(store_tf)
     return o
 
 
@@ -216,10 +222,13 @@ class Context:
             pass
 
     def factor(self, A: torch.Tensor, tf="f32", fp16_scale: bool = True, nb: int = 0,
-               stream=None, autotune: bool = False) -> "Factorization":
+               stream=None, autotune: bool = False, group: int = 0, onthefly: bool = False,
+               store_tf: bool = False) -> "Factorization":
+        """mplu (Sec. 2.4): onthefly = True selects the mixed precision solves of Sec. 5.3;
+        store_tf = True keeps binary16 / bfloat16 factors in 2 bytes (Sec. 1, 2.5)."""
         Ac, lda = as_colmajor(A)
         tfc = DTYPES[tf] if isinstance(tf, str) else int(tf)
-        opts = make_opts(_tw_code(Ac), tfc, fp16_scale, nb, autotune)
+        opts = make_opts(_tw_code(Ac), tfc, fp16_scale, nb, autotune, group, onthefly, store_tf)
         h = ctypes.c_void_p()
         _check(lib().ir_factor(self._h, Ac.shape[0], ctypes.c_void_p(Ac.data_ptr()), lda,
                                ctypes.byref(opts), _stream_ptr(stream), ctypes.byref(h)))
@@ -240,7 +249,7 @@ class Context:
         return r, rn
 
     def solve_host(self, A_host: torch.Tensor, b_host: torch.Tensor, tf="f32", term=None,
-                   fp16_scale: bool = True, stream=None):
+                   fp16_scale: bool = True, stream=None, onthefly: bool = False):
         """End-to-end solve from host (CPU) tensors; returns (x_host, Report)."""
         if A_host.is_cuda or b_host.is_cuda:
             raise ValueError("solve_host takes CPU tensors")
@@ -249,7 +258,7 @@ class Context:
         bb = b_host.to(Ac.dtype).contiguous()
         x = torch.empty(n, dtype=Ac.dtype, pin_memory=Ac.is_pinned())
         tfc = DTYPES[tf] if isinstance(tf, str) else int(tf)
-        opts = make_opts(_tw_code(Ac), tfc, fp16_scale)
+        opts = make_opts(_tw_code(Ac), tfc, fp16_scale, onthefly=onthefly)
         t = term if term is not None else default_term()
         rep = _Report()
         _check(lib().ir_solve_host(self._h, n, ctypes.c_void_p(Ac.data_ptr()), lda,
@@ -461,10 +470,10 @@ class Factorization:
         return x, R
 
     def schedule(self):
-        """(nb, panel_reserve_sms) of the factorization (ir_fact_schedule)."""
-        nb, r = ctypes.c_int(), ctypes.c_int()
-        _check(lib().ir_fact_schedule(self._h, ctypes.byref(nb), ctypes.byref(r)))
-        return nb.value, r.value
+        """(nb, panel_reserve_sms, group) of the factorization (ir_fact_schedule)."""
+        nb, r, g = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().ir_fact_schedule(self._h, ctypes.byref(nb), ctypes.byref(r), ctypes.byref(g)))
+        return nb.value, r.value, g.value
 
     def lu_solve(self, v: torch.Tensor, stream=None) -> torch.Tensor:
         """d = U^{-1} L^{-1} P v in binary32."""
@@ -473,6 +482,11 @@ class Factorization:
         _check(lib().ir_lu_solve(self._h, ctypes.c_void_p(vv.data_ptr()), ctypes.c_void_p(d.data_ptr()),
                                  _stream_ptr(stream)))
         return d
+
+    def check_wait_timeout(self, limit_s: float, stream=None) -> int:
+        """ir_check_wait_timeout: the solves' bounded wait on a value nobody writes,
+        limited to limit_s seconds; returns the status code (6 = IR_ETIMEOUT expected)."""
+        return int(lib().ir_check_wait_timeout(self._h, ctypes.c_double(limit_s), _stream_ptr(stream)))
 
     def pivots(self):
         import numpy as np

@@ -19,7 +19,8 @@ def test_header_declares_the_boundary():
     for must in ("ir_init", "ir_factor", "ir_refactor", "ir_solve", "ir_solve_host", "ir_lu_solve",
                  "ir_residual", "ir_fact_pivots", "ir_fact_factors", "ir_fact_destroy", "ir_finalize",
                  "ir_gmres_reserve", "ir_solve_gmres", "ir_default_krylov_opts", "ir_solve_bicgstab",
-                 "ir_bicgstab_reserve", "ir_fact_schedule", "ir_batch_schedule", "ir_solve_many", "ir_batch_run_escalate"):
+                 "ir_bicgstab_reserve", "ir_fact_schedule", "ir_batch_schedule", "ir_solve_many", "ir_batch_run_escalate",
+                 "ir_check_wait_timeout"):
         assert must in names
 
 

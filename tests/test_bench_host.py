@@ -1,6 +1,7 @@
 """Host-side logic of bench.py that needs no GPU: the clock / throttle-reason
-sampler (against a fake nvidia-smi on PATH) and the panel's DRAM-traffic
-figure, which is reported only for the kernel source it was measured on."""
+sampler (against a fake nvidia-smi on PATH), the tensor-core roofline's
+arithmetic on a synthetic per-kernel profile, and the DRAM-traffic figure,
+which is reported only for the kernel source it was measured on."""
 import os
 import stat
 import sys
@@ -53,11 +54,55 @@ def test_clock_sampler_without_nvidia_smi(monkeypatch, tmp_path):
     assert c.stop()["reasons"] == ["unavailable"]
 
 
-def test_panel_traffic_only_for_the_measured_source(monkeypatch):
-    t = bench.panel_traffic_per_launch(4096)
-    # the committed capture matches the committed kernel: 21st panel (2816 rows)
-    # scaled to the average panel of N = 4096 (2080 rows)
-    assert t is not None
-    assert abs(t - bench.PANEL_TRAFFIC["bytes"] * 2080 / 2816) < 1e-6
-    monkeypatch.setitem(bench.PANEL_TRAFFIC, "sha256", "0" * 64)
-    assert bench.panel_traffic_per_launch(4096) is None
+def test_trailing_update_flops_is_two_thirds_n_cubed():
+    # sum over block steps of 2 m^2 nb, m = n - j - nb: ~ 2 n^3 / 3 for n >> nb
+    assert bench.trailing_update_flops(128, 64) == 2.0 * 64 ** 2 * 64
+    f = bench.trailing_update_flops(8192)
+    assert abs(f / (2 * 8192 ** 3 / 3) - 1) < 0.02
+
+
+def test_group_update_flops():
+    # n = 3 groups of 2 block steps (nb = 64): groups 0 and 1 have far columns
+    n = 6 * 64
+    f = bench.group_update_flops(n, 2)
+    want = 2.0 * (n - 128) * (n - 192) * 128 + 2.0 * (n - 256) * (n - 320) * 128
+    assert f == want
+    # the group launches carry most of the update; never more than all of it
+    for g in (1, 4, 8, 16):
+        assert bench.group_update_flops(8192, g) < bench.trailing_update_flops(8192)
+    assert bench.group_update_flops(8192, 8) > 0.8 * bench.trailing_update_flops(8192)
+
+
+def test_tensor_roofline_is_per_step_not_per_run():
+    """The profile sums every launch of every profiled step; the roofline divides
+    one factorization's flops by one step's kernel time, so the result does not
+    depend on how many steps were profiled."""
+    n, peaks = 8192, {"bf16_tflops": 2000.0, "source": "measured"}
+    flops = bench.group_update_flops(n, 4)
+    per_step_ms, per_step_calls = 2.0, 31
+    for steps in (1, 5, 20):
+        prof = {"gemm_tc_group": (per_step_ms * steps, per_step_calls * steps), "panel": (10.0 * steps, 128 * steps)}
+        r = bench.tensor_roofline(prof, steps, n, peaks, 4)
+        assert abs(r["achieved"] - flops / 2e-3 / 1e12) < 1e-9 * r["achieved"]
+        assert abs(r["frac"] - r["achieved"] / 2000.0) < 1e-15
+        assert r["launches_per_step"] == per_step_calls
+        assert abs(r["avg_launch_ms"] - per_step_ms / per_step_calls) < 1e-15
+        # per launch: flops of an average launch over its average duration
+        assert abs(r["flops_per_launch"] / (r["avg_launch_ms"] * 1e-3) / 1e12 - r["achieved"]) < 1e-6
+    assert bench.tensor_roofline({"panel": (1.0, 1)}, 1, n, peaks, 4) is None
+
+
+def test_traffic_only_for_the_measured_source(tmp_path, monkeypatch):
+    import hashlib
+    import json
+    src = tmp_path / "k.cu"
+    src.write_text("kernel source")
+    rec = {"k_gemm_tc": {"source": str(src), "sha256": hashlib.sha256(b"kernel source").hexdigest(),
+                         "bytes_per_launch": 1234.5}}
+    f = tmp_path / "traffic.json"
+    f.write_text(json.dumps(rec))
+    monkeypatch.setattr(bench, "TRAFFIC_FILE", str(f))
+    assert bench.traffic_per_launch("k_gemm_tc") == 1234.5
+    assert bench.traffic_per_launch("k_panel") is None
+    src.write_text("kernel source, changed")
+    assert bench.traffic_per_launch("k_gemm_tc") is None

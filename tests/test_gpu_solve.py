@@ -5,6 +5,7 @@ import torch
 
 import irgen
 import oracle as O
+import parity as P
 from gpu_util import dev_colmajor, dev_vec
 from paper_2311_14616_gb300 import ir
 
@@ -69,11 +70,22 @@ def test_ir_matches_oracle(ctx, name, make, tf, term):
     xr = O.reference_solution(A, b)
     kappa = O.cond_inf(A)
     tol = O.parity_tol(kappa, O.F64)
-    assert rep.status == O.STATUS_NAMES[ref.status]
-    # binary32 factors contract fast (one iteration of slack); TF32/16-bit factors of an
-    # ill-conditioned system contract slowly and the stopping step moves with rounding
-    slack = 1 if tf == O.F32 else max(1, ref.iters // 3)
-    assert abs(rep.iters - ref.iters) <= slack
+    # status away from the convergence boundary of the TF (parity.classify).  Binary32
+    # factors are bitwise the oracle's (one iteration of slack for the solves' order);
+    # with TF32 / 16-bit factors the contraction factor kappa u_F c (Sec. 5.4.2) carries
+    # the factorization's own error, which the tensor core's binary32 accumulation and
+    # the oracle's exact sums make differently -- near the boundary (TF32 on the
+    # kappa ~ 1e5 Green's system: kappa u_TF32 ~ 65) by a factor of two or so -- so the
+    # step count is held to within a factor of two
+    cls = P.classify(ref, O.rel_err_inf(ref.x, xr) <= tol)
+    if P.status_must_match(ref, cls, ir.default_term(**term).litmax):
+        assert rep.status == O.STATUS_NAMES[ref.status]
+    else:
+        assert rep.status in ("converged", "stagnated")
+    if tf == O.F32:
+        assert abs(rep.iters - ref.iters) <= 1
+    else:
+        assert ref.iters // 2 <= rep.iters <= 2 * ref.iters + 1, (rep.iters, ref.iters)
     assert rep.rhist[0] == ref.rhist[0]
     # every case here is one where the oracle's own IR meets the bar against x_ref
     # (whatever its stopping rule: these runs end by eq. (stag) at the rounding
@@ -260,6 +272,40 @@ def test_solve_many_columns_equal_single_solves(ctx):
     assert reps[3].status == "converged" and reps[3].iters == 0
     xr = O.reference_solution(A, B[:, 0])
     assert O.rel_err_inf(X[:, 0], xr) <= O.parity_tol(O.cond_inf(A), O.F64)
+
+
+@pytest.mark.parametrize("n,tf,store", [(700, "f32", False), (5000, "f32", False), (1500, "f16", True),
+                                         (300, "bf16", False)])
+def test_solve_many_blocked_equals_single_solves(ctx, n, tf, store):
+    """ir_solve_many refines up to 4 columns together: each factor tile of the
+    correction solve is applied to all of them and each residual reads A once,
+    with every column's own scaling, history and termination.  Per column the
+    arithmetic is that of the single-column path, in the same order, so x and
+    the histories are bitwise the single solves' -- for blocks of 4, a ragged
+    last block, a zero column, a non-finite column, the sync-free solve pair
+    (n > 4096), 2-byte factors, and the backward-error test."""
+    A, _ = irgen.case_gaussian(n, 5000 + n)
+    g = np.random.Generator(np.random.PCG64(n))
+    B = g.standard_normal((n, 9))
+    B[:, 5] = 0.0
+    B[:, 2] *= 1e-3
+    f = ctx.factor(dev_colmajor(A), tf=tf, store_tf=store)
+    for mode in (0, 1):
+        term = ir.default_term(mode=mode)
+        X, reps = f.solve_many(torch.from_numpy(B).cuda(), term=term)
+        X = X.cpu().numpy()
+        for j in range(9):
+            x, rep = f.solve(dev_vec(np.ascontiguousarray(B[:, j])), term=term)
+            np.testing.assert_array_equal(X[:, j], x.cpu().numpy())
+            assert reps[j].status == rep.status and reps[j].rhist == rep.rhist and reps[j].dhist == rep.dhist
+        assert reps[5].status == "converged" and reps[5].iters == 0
+    # a non-finite column fails alone; the others are solved
+    B[7, 3] = np.inf
+    with pytest.raises(ir.IRError) as e:
+        f.solve_many(torch.from_numpy(B).cuda())
+    assert e.value.code == 5
+    x0, rep0 = f.solve(dev_vec(np.ascontiguousarray(B[:, 0])))
+    assert rep0.status in ("converged", "stagnated")     # the factorization is still usable
 
 
 def test_cluster_solve_pair_is_bitwise_the_two_kernel_pair():

@@ -489,6 +489,53 @@ def test_ir_mps_solves_in_working_precision():
         O.ir_solve(A, b, O.F32, solve="hps")
 
 
+def test_ir_tf_storage_hand_worked():
+    """Factors kept in TF (store_tf).  A = [[3, 0], [1, 1]] (every entry exact in
+    TF): the panel's binary32 scaling gives l21 = 1 * fl32(1/3), which is not a
+    TF number, u11 = 3, u12 = 0, u22 = 1.  Stored in binary16, l21 becomes
+    rTF(fl32(1/3)) = 1365 * 2^-12 = 0.333251953125 (bfloat16: 171 * 2^-9).  For
+    b = (3, 0) the first step (eq. vdlow: rho = 3, v = (1, 0)) solves L y = v,
+    U z = y: z2 = -l21, and d = rho z, so d2 = -3 l21: -0.999755859375 with
+    binary16 storage, -1.001953125 with bfloat16, and -3 fl32(1/3) =
+    -1.0000000298023224 (exact in binary64) when the binary32 multiplier is
+    used."""
+    A = np.asfortranarray(np.array([[3.0, 0.0], [1.0, 1.0]]))
+    b = np.array([3.0, 0.0])
+    third = float(np.float32(1.0) / np.float32(3.0))
+    for tf, l21 in ((O.F16, 1365 * 2.0 ** -12), (O.BF16, 171 * 2.0 ** -9)):
+        res = O.ir_solve(A, b, tf, fp16_scaling=False, store_tf=True, term=O.Term(litmax=1))
+        assert res.LU[1, 0] == np.float32(l21)
+        assert res.x[1] == -3 * l21
+        plain = O.ir_solve(A, b, tf, fp16_scaling=False, term=O.Term(litmax=1))
+        assert plain.LU[1, 0] == np.float32(third) and plain.x[1] == -3 * third == -1.0000000298023224
+    with pytest.raises(ValueError):
+        O.ir_solve(A, b, O.F32, store_tf=True)
+
+
+@pytest.mark.parametrize("tf", [O.F16, O.BF16])
+def test_ir_tf_storage_rounds_every_factor_once(tf):
+    """The stored factors are exactly the TF roundings of the binary32 ones (every
+    entry, diagonal included); exact factors are unchanged (a diagonal of powers
+    of two solves in one step either way); IR with stored factors still converges
+    on a well-conditioned system, with its contraction bounded by the storage
+    error u_TF (|L||U|) of eq. (comperr)."""
+    A, b = irgen.case_gaussian(150, 77)
+    plain = O.ir_solve(A, b, tf, nb=64)
+    st = O.ir_solve(A, b, tf, nb=64, store_tf=True)
+    np.testing.assert_array_equal(st.LU, O.round_tf(plain.LU, tf).reshape(plain.LU.shape))
+    assert np.array_equal(st.ipiv, plain.ipiv)
+    assert st.status in (O.CONVERGED, O.STAGNATED)
+    xr = O.reference_solution(A, b)
+    assert O.rel_err_inf(st.x, xr) <= 1e-12
+    h = st.rhist
+    u = O.UNIT_ROUNDOFF[tf]
+    kappa = O.cond_inf(A)
+    assert h[1] / h[0] <= 4 * 150 * u * kappa      # first step's contraction, storage error included
+    d = np.asfortranarray(np.diag(2.0 ** np.arange(-3, 5, dtype=float)))
+    e = O.ir_solve(d, np.ones(8), tf, fp16_scaling=False, store_tf=True)
+    assert e.iters == 1 and e.rhist[-1] == 0.0
+
+
 @pytest.mark.parametrize("case,tf", [("I-G", O.F32), ("I-G", O.TF32), ("I-G", O.F16), ("gauss", O.F32)])
 def test_ir_mps_contraction_within_rate_bound(case, tf):
     """Eq. (rate2) (Sec. 5.4.2): with mixed precision solves the residual
