@@ -76,6 +76,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the N = 256 / 4096 / kappa = 1e6 lines")
     ap.add_argument("--batch-count", type=int, default=2000)
     ap.add_argument("--no-gmres", action="store_true", help="skip the GMRES-IR / BiCGSTAB-IR lines")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip the headline system's variants (mixed precision solves, 2-byte factors, 4 right-hand sides)")
     return ap.parse_args()
 
 
@@ -645,6 +647,7 @@ def main():
                       "its device buffers and factorization across calls of the same shape)"}
         del A_h, b_h
 
+    variants = None if args.no_variants else run_variants(args, ctx, A_d, b_d, timed_steps, rel, xr, x16h)
     fact.destroy()
     del A_row
     extra = None if args.no_extra else run_extra(args, ctx, dev, stream, flush, ws, rank, timed_steps, rel,
@@ -670,6 +673,7 @@ def main():
         "lu_tflops_note": "2 N^3 / 3 over the factorization (cast + LU + diagonal-block inverses, lookahead "
                           "schedule replayed from its graph)",
         "bf16": {"ms": tb, "iters": repb.iters, "status": repb.status},
+        "variants": variants,
         "kernel_ms_per_step": kms,
         "roofline": roof,
         "panel": panel_share,
@@ -788,6 +792,55 @@ def run_extra(args, ctx, dev, stream, flush, ws, rank, timed_steps, rel, oracle_
                   "bound_thm_irterm": 4 * (8192 + 1) * k4 * 2.0 ** -52 + 2.0 ** -23})
     out["svd_N8192_kappa1e6_TWf32_TFf32_TRf64"] = d
     return out
+
+
+def run_variants(args, ctx, A_d, b_d, timed_steps, rel, xr, x16h):
+    """The headline system with the paper's other solve arrangements: mixed
+    precision solves (binary64 triangular solves on the promoted binary16
+    factors, mplu(A; onthefly = true), Sec. 5.3), the factors kept in 2 bytes
+    (Sec. 1, 2.5), and four right-hand sides refined together on one
+    factorization (per column)."""
+    import numpy as np
+    import torch
+
+    from paper_2311_14616_gb300 import ir
+    out = {}
+    steps = max(3, args.steps // 2)
+    term = ir.default_term()
+    for name, kw in (("mps_binary64_solves", dict(onthefly=True)), ("factors_in_2_bytes", dict(store_tf=True))):
+        f = ctx.factor(A_d, tf="f16", autotune=True, **kw)
+        x = torch.empty_like(b_d)
+
+        def step():
+            f.refactor(A_d)
+            return f.solve(b_d, x, term)[1]
+        ms, rep, prof, _ = timed_steps(step, steps, 1, profile=True)
+        ms2, rep, _, _ = timed_steps(step, steps, 1)
+        solve_kind = "trsv_pair_f64" if kw.get("onthefly") else "trsv_pair"
+        out[name] = {"ms": max_over_ranks(statistics.mean(ms2), ws_of()), "iters": rep.iters, "status": rep.status,
+                     "solve_ms_per_step": prof[solve_kind][0] / steps if solve_kind in prof else None,
+                     "rel_err_vs_x_ref": rel(x, xr)}
+        f.destroy()
+    # four right-hand sides on one factorization: ms per right-hand side of the refinement
+    f = ctx.factor(A_d, tf="f16", autotune=True)
+    g = np.random.Generator(np.random.PCG64(7))
+    B = torch.from_numpy(g.standard_normal((A_d.shape[0], 4))).to(A_d.device)
+    B[:, 0] = b_d
+    _, rep1 = f.solve(b_d, term=term)
+    ms1, _, _, _ = timed_steps(lambda: f.solve(b_d, term=term)[1], steps, 1)
+    ms4, out4, _, _ = timed_steps(lambda: f.solve_many(B, term=term), steps, 1)
+    X, reps = f.solve_many(B, term=term)
+    out["four_rhs"] = {"refine_ms_per_rhs": statistics.mean(ms4) / 4, "refine_ms_single_rhs": statistics.mean(ms1),
+                       "iters": [r.iters for r in reps], "status": [r.status for r in reps],
+                       "column0_bitwise_single": bool(np.array_equal(X[:, 0].cpu().numpy(), x16h)),
+                       "note": "refinement only (the factorization is shared); solves apply each factor tile to "
+                               "all four columns, the residual reads A once for all of them"}
+    f.destroy()
+    return out
+
+
+def ws_of():
+    return int(os.environ.get("WORLD_SIZE", "1"))
 
 
 def O_ref(A, b):

@@ -29,12 +29,12 @@ namespace {
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
     KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_BI_STEP,
-    KC_GEMM_TC_GROUP, KC_PACK, KC_TRSV64, KC_STORE, KC_N
+    KC_GEMM_TC_GROUP, KC_PACK, KC_TRSV64, KC_STORE, KC_U12_GROUP, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
                                 "batched", "gm_orth", "krylov_update", "norm1", "bi_step",
-                                "gemm_tc_group", "pack", "trsv_pair_f64", "store_tf"};
+                                "gemm_tc_group", "pack", "trsv_pair_f64", "store_tf", "u12_group"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -218,10 +218,12 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     f->store_tf = o->store_tf;
     if (o->store_tf) AL(f->AF16, (size_t)nn * f->ldf * 2);
     if (o->onthefly && o->TW == IR_F64) {
-        AL(f->y64, (size_t)nblk * kTrsvB * sizeof(double));
-        AL(f->z64, (size_t)nblk * kTrsvB * sizeof(double));
-        AL(f->mps_flags, (size_t)2 * nblk * sizeof(int));
-        if (cudaMemset(f->mps_flags, 0, (size_t)2 * nblk * sizeof(int)) != cudaSuccess) {
+        // the mixed precision solves run in blocks of kMpsB rows
+        const int64_t mblk = (nn + kMpsB - 1) / kMpsB;
+        AL(f->y64, (size_t)mblk * kMpsB * sizeof(double));
+        AL(f->z64, (size_t)mblk * kMpsB * sizeof(double));
+        AL(f->mps_flags, (size_t)2 * mblk * sizeof(int));
+        if (cudaMemset(f->mps_flags, 0, (size_t)2 * mblk * sizeof(int)) != cudaSuccess) {
             st = IR_ECUDA;
             goto fail;
         }
@@ -409,8 +411,8 @@ ir_status enqueue_factor_grouped(ir_fact *f, cudaStream_t s) {
                 RUN(KC_PACK, sw, launch_pack_slots(f->AF, ldf, c0, Gg, c0 + NB, n, n - c0, f->TF, f->Agrp, sms, sw));
                 // 3. U12 of the group's rows, block by block, with the group's own block steps
                 //    between them (one kernel, one CTA per 64 far columns)
-                const size_t bslot = (size_t)(n - near_end) * NB * esz;
-                RUN(KC_TRSM, sw, launch_trsm_group(f->AF, ldf, c0, Gg, near_end, n, f->TF, f->Bgrp, (int64_t)bslot, sw));
+                RUN(KC_U12_GROUP, sw, launch_u12_group_tc(f->AF, ldf, c0, Gg, near_end, n, f->TF, f->Agrp, n - c0,
+                                                          f->Bgrp, n - near_end, near_end, f->dev, sw));
                 // 4. the rows below the group: all G slots at once
                 pend_c0 = c0;
                 pend_G = Gg;

@@ -25,6 +25,7 @@ constexpr int kPanelRows = 512;   // panel rows per CTA (two per thread)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelMaxCluster = 16;
 constexpr int kMaxN = kPanelRows * kPanelMaxCluster;  // 8192 rows per panel cluster
+constexpr int kMpsB = 64;         // row block of the mixed precision (binary64) solves
 constexpr int kMaxGroup = 16;     // block steps per group of the tensor-core LU (64 x 16 = 1024 columns)
 
 // Device-side scalars.  Non-negative doubles are ordered like their bit
@@ -129,8 +130,8 @@ struct ir_fact {
     void *bm;
     unsigned long long *mtags;
     ir::MultiScalars *mscal, *host_mscal;
-    double *y64, *z64;       // MPS solve vectors (nblk * 128 binary64 each; TW = binary64)
-    int *mps_flags;          // MPS per-block publication flags (2 nblk)
+    double *y64, *z64;       // MPS solve vectors (ceil(n / kMpsB) * kMpsB binary64 each; TW = binary64)
+    int *mps_flags;          // MPS per-block publication flags (2 ceil(n / kMpsB))
     void *Agrp, *Bgrp;       // a group's operands: group x n rows x 64 (rTF of its L columns / U rows)
     cudaStream_t la_stream;  // low-priority stream of the lookahead schedule
     cudaEvent_t *la_events;  // fork/join events of the lookahead schedule
@@ -191,11 +192,6 @@ cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int 
 // list_ints ints) applied in order to the columns [c0, c1).
 cudaError_t launch_laswp_lists(float *AF, int64_t ldf, int c0, int c1, const int32_t *lists, int list_ints, int ring,
                                int first, int count, cudaStream_t s);
-// U12 of the group of G block rows starting at c0 for the columns [cb, ce), with
-// the group's own block steps between them; rTF(U) of block t into operand slot t
-// of Bgrp (slots of bslot bytes, row c - cb for column c).
-cudaError_t launch_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf, void *Bgrp,
-                              int64_t bslot, cudaStream_t s);
 cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
                         cudaStream_t s);
 cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
@@ -209,6 +205,13 @@ cudaError_t launch_gemm_tc_group(float *AF, int64_t ldf, int c0, int G, int r0, 
                                  int s0, int s1, ir_dtype tf, const void *Agrp, int64_t a_rows, const void *Bgrp,
                                  int64_t b_rows, int bbase, int sms, int max_ctas, DevScalars *dev,
                                  cudaStream_t s);
+// U12 of the group of G block rows starting at c0 for the columns [cb, ce), with
+// the group's own block steps between them on the tensor cores (k_gemm_tc.cu): L
+// from the packed slots Agrp (a_rows rows each), rTF(U) of block t into slot t of
+// Bgrp (b_rows rows each, row c - bbase for column c).
+cudaError_t launch_u12_group_tc(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf,
+                                const void *Agrp, int64_t a_rows, void *Bgrp, int64_t b_rows, int bbase,
+                                DevScalars *dev, cudaStream_t s);
 // rTF of the factor columns [c0, c0 + 64 G), rows [r0, r1), into G slots of `rows` rows.
 cudaError_t launch_pack_slots(const float *AF, int64_t ldf, int c0, int G, int r0, int r1, int64_t rows, ir_dtype tf,
                               void *out, int sms, cudaStream_t s);
@@ -246,7 +249,8 @@ cudaError_t launch_residual_multi(int64_t n, ir_dtype tw, const void *A, int64_t
 // to the 2-byte array F16 (row stride ldf); overflow raises dev->nonfinite.
 cudaError_t launch_store_tf(float *AF, int64_t ldf, int n, ir_dtype tf, void *F16, DevScalars *dev, int sms,
                             cudaStream_t s);
-// Mixed precision solve pair (k_trsv64.cu): x += s U^{-1} L^{-1} P r in binary64
+// Mixed precision solve pair (k_trsv64.cu): x += s U^{-1} L^{-1} P r in binary64,
+// blocks of kMpsB rows
 // on the binary32 factors; ||d||, ||x|| into dev.
 cudaError_t launch_mps_pair(const float *AF, int64_t ldf, int n, const int32_t *perm, const double *r, double *x,
                             double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s);

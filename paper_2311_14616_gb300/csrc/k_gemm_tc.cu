@@ -101,7 +101,10 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap *map, int c0, int
 constexpr int kCBoxBytes = BM * 32 * 4;       // one 128-row x 32-column binary32 box = 16 KB
 constexpr int kCBufBytes = 4 * kCBoxBytes;    // a 128 x 128 C tile = 64 KB
 
-template <int KATOMS, int STAGES, int CBUFS>   // 128-byte K atoms per slot row: 2 for TF32, 1 for 16-bit
+// KATOMS: 128-byte K atoms per slot row (2 for TF32, 1 for 16-bit).  GROUP: the
+// launch applies a group's slots to the far columns; the code is the same, the
+// separate instantiation lets launch lists and profiles tell the two apart.
+template <int KATOMS, int STAGES, int CBUFS, bool GROUP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_gemm_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
               const __grid_constant__ CUtensorMap tmC, TcParams p) {
@@ -352,12 +355,265 @@ __global__ void __launch_bounds__(256) k_pack_slots(const float *AF, int64_t ldf
     }
 }
 
+// U12 of a group's rows on the tensor cores (the group's end, before the update
+// of the rows below the group).  For the far columns and the group's 64-row
+// blocks c = 0 .. G-1 in order:
+//     C_c <- fl32(C_c - D_{c,a}),  D_{c,a} = rTF(L_{c,a}) rTF(U_a),  a = 0 .. c-1
+// (each D a binary32 tensor-core sum of one block step's 64 products, as in the
+// right-looking LU restricted to the group's rows), then U_c = L_cc^{-1} C_c by
+// the binary32 fmaf chains of the unblocked LU (unit lower triangle, ascending
+// k).  U_c goes back to A_F and, rounded to TF, into operand slot c, from which
+// the later blocks of the group and the update of the rows below read it.
+//
+// The MMA computes the transpose D^T = rTF(U_a)^T rTF(L_{c,a})^T: M = 128 far
+// columns (one per TMEM lane and per epilogue thread), N = the 64 rows of block
+// c, K = 64; A = slot a of the U slots (a column's 64 K values contiguous), B =
+// slot a of the L slots (a row's 64 K values contiguous): the K-major slot
+// layouts of the group update.
+//   warp 0     TMA producer: per pair (c, a) the U tile (128 x 64) and the L
+//              tile (64 x 64) of slot a into one stage; before the first pair
+//              that needs U_a it waits until the epilogue has published U_a
+//   warp 1     TMEM (8 accumulators x 64 columns); MMAs, one accumulator per pair
+//   warps 2-5  one far column per thread: C_c into registers, the pairs'
+//              accumulators subtracted in order, the triangular solve, stores
+// One CTA per 128 far columns.  Every wait is bounded; after a timeout the
+// epilogue still runs its loops (no barrier is skipped) without waiting.
+constexpr int kU12Acc = 8;                 // accumulators of 64 TMEM columns
+constexpr int kU12Threads = 192;
+constexpr int kLAtomBytes = 64 * 128;      // one 64-row x 128-byte swizzle tile = 8 KB
+constexpr int kLtLd = K + 4;               // row stride of the staged diagonal block
+
+struct U12Params {
+    float *AF;
+    int64_t ldf;
+    int c0, G;              // the group's first column and its number of 64-row blocks
+    int cb, ce;             // far columns [cb, ce)
+    int bbase;              // slot row of column c in the U slots: c - bbase
+    char *bop;              // U slots (bslot bytes apart), written by the epilogue
+    int64_t bslot;
+    ir_dtype tf;
+    unsigned idesc;
+    int *timeout;
+};
+
+template <int KATOMS, int STAGES>
+__global__ void __launch_bounds__(kU12Threads, 1)
+    k_u12_group_tc(const __grid_constant__ CUtensorMap tmU, const __grid_constant__ CUtensorMap tmL, U12Params p) {
+    constexpr bool kTF32 = (KATOMS == 2);
+    constexpr int kAtomElems = kTF32 ? 32 : 64;
+    constexpr int kKSteps = 128 / 32;
+    constexpr unsigned kStageBytes = KATOMS * (kAtomBytes + kLAtomBytes);
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const unsigned sbase = (smem_u32(smem_raw) + 1023u) & ~1023u;
+    unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
+    const unsigned sU = sbase;                                   // STAGES x KATOMS x 16 KB
+    const unsigned sL = sbase + STAGES * KATOMS * kAtomBytes;    // STAGES x KATOMS x 8 KB
+    float *Lt = reinterpret_cast<float *>(gbase + STAGES * KATOMS * (kAtomBytes + kLAtomBytes));  // [K][kLtLd]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Lt + K * kLtLd);
+    const unsigned bar0 = smem_u32(bars);
+    auto full_bar = [&](int s) { return bar0 + 8u * s; };
+    auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
+    auto accf_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + b); };
+    auto acce_bar = [&](int b) { return bar0 + 8u * (2 * STAGES + kU12Acc + b); };
+    const unsigned uready_bar = bar0 + 8u * (2 * STAGES + 2 * kU12Acc);
+    const unsigned drain_bar = uready_bar + 8u;
+    unsigned *tmem_slot = reinterpret_cast<unsigned *>(bars + 2 * STAGES + 2 * kU12Acc + 2);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; ++s) {
+            mbar_init(full_bar(s), 1);
+            mbar_init(empty_bar(s), 1);
+        }
+        for (int b = 0; b < kU12Acc; ++b) {
+            mbar_init(accf_bar(b), 1);
+            mbar_init(acce_bar(b), 128);
+        }
+        mbar_init(uready_bar, 128);
+        mbar_init(drain_bar, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kU12Acc * 64)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const unsigned tmem_base = *tmem_slot;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int s = 0, known = 0;
+            unsigned ph = 0;
+            unsigned last_ph[STAGES];
+            bool issued[STAGES];
+            for (int q = 0; q < STAGES; ++q) issued[q] = false;
+            const int urow = blockIdx.x * BM + (p.cb - p.bbase);
+            bool ok = true;
+            for (int c = 1; ok && c < p.G; ++c)
+                for (int a = 0; a < c; ++a) {
+                    if (a >= known) {      // U_a has to be published first
+                        if (!mbar_wait(uready_bar, (unsigned)a & 1u, abort_flag, p.timeout)) { ok = false; break; }
+                        known = a + 1;
+                    }
+                    if (!mbar_wait(empty_bar(s), ph ^ 1u, abort_flag, p.timeout)) { ok = false; break; }
+                    mbar_arrive_expect_tx(full_bar(s), kStageBytes);
+#pragma unroll
+                    for (int q = 0; q < KATOMS; ++q) {
+                        tma_load_3d(sU + (s * KATOMS + q) * kAtomBytes, &tmU, q * kAtomElems, urow, a, full_bar(s));
+                        tma_load_3d(sL + (s * KATOMS + q) * kLAtomBytes, &tmL, q * kAtomElems, K * c, a, full_bar(s));
+                    }
+                    last_ph[s] = ph;
+                    issued[s] = true;
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                }
+            if (*abort_flag) {
+                volatile int no_abort = 0;
+                for (int q = 0; q < STAGES; ++q)
+                    if (issued[q]) mbar_wait(full_bar(q), last_ph[q], &no_abort, nullptr);
+            }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int s = 0;
+            unsigned ph = 0, qa = 0;
+            bool ok = true;
+            for (int c = 1; ok && c < p.G; ++c)
+                for (int a = 0; a < c; ++a, ++qa) {
+                    const int ab = (int)(qa % kU12Acc);
+                    if (!mbar_wait(acce_bar(ab), ((qa / kU12Acc) & 1u) ^ 1u, abort_flag, p.timeout)) { ok = false; break; }
+                    tc_fence_after();
+                    if (!mbar_wait(full_bar(s), ph, abort_flag, p.timeout)) { ok = false; break; }
+                    tc_fence_after();
+                    const unsigned dt = tmem_base + (unsigned)(ab * 64);
+#pragma unroll
+                    for (int q = 0; q < KATOMS; ++q)
+#pragma unroll
+                        for (int kk = 0; kk < kKSteps; ++kk) {
+                            const uint64_t ad = make_desc(sU + (s * KATOMS + q) * kAtomBytes + kk * 32);
+                            const uint64_t bd = make_desc(sL + (s * KATOMS + q) * kLAtomBytes + kk * 32);
+                            mma<kTF32>(dt, ad, bd, p.idesc, (q | kk) != 0);
+                        }
+                    mma_commit(empty_bar(s));
+                    if (++s == STAGES) { s = 0; ph ^= 1u; }
+                    mma_commit(accf_bar(ab));
+                }
+            if (*abort_flag) {
+                volatile int no_abort = 0;
+                mma_commit(drain_bar);
+                mbar_wait(drain_bar, 0u, &no_abort, nullptr);
+            }
+        }
+    } else {
+        // warps 2..5: TMEM lane quarter warp % 4; thread = far column x of the CTA
+        const int quarter = warp & 3;
+        const int x = quarter * 32 + lane;
+        const int ep = threadIdx.x - 64;                    // 0 .. 127
+        const int col = p.cb + blockIdx.x * BM + x;
+        const bool on = col < p.ce;
+        const int esz = (p.tf == IR_TF32) ? 4 : 2;
+        unsigned qa = 0;
+        for (int c = 0; c < p.G; ++c) {
+            const int rc = p.c0 + K * c;
+            float u[K];
+#pragma unroll
+            for (int i = 0; i < K; ++i) u[i] = on ? p.AF[(int64_t)(rc + i) * p.ldf + col] : 0.f;
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // the previous block's solve is done with Lt
+            // Lt[m][k] = l_km of the diagonal block (binary32)
+#pragma unroll
+            for (int i = 0; i < K * K / 4 / 128; ++i) {
+                const int e = ep + 128 * i, k = e % K, m4 = e / K;
+                const float4 v = *reinterpret_cast<const float4 *>(p.AF + (int64_t)(rc + k) * p.ldf + rc + 4 * m4);
+                Lt[(4 * m4 + 0) * kLtLd + k] = v.x;
+                Lt[(4 * m4 + 1) * kLtLd + k] = v.y;
+                Lt[(4 * m4 + 2) * kLtLd + k] = v.z;
+                Lt[(4 * m4 + 3) * kLtLd + k] = v.w;
+            }
+            for (int a = 0; a < c; ++a, ++qa) {
+                const int ab = (int)(qa % kU12Acc);
+                mbar_wait(accf_bar(ab), (qa / kU12Acc) & 1u, abort_flag, p.timeout);
+                tc_fence_after();
+                float v0[32], v1[32];
+                const unsigned tl = tmem_base + ((unsigned)(quarter * 32) << 16) + (unsigned)(ab * 64);
+                tmem_ld32(tl, v0);
+                tmem_ld32(tl + 32, v1);
+                tc_fence_before();
+                mbar_arrive(acce_bar(ab));
+#pragma unroll
+                for (int q = 0; q < 32; ++q) {
+                    u[q] -= v0[q];
+                    u[32 + q] -= v1[q];
+                }
+            }
+            asm volatile("bar.sync 1, 128;" ::: "memory");   // Lt is complete
+#pragma unroll
+            for (int m = 0; m < K - 1; ++m) {
+                const float um = u[m];
+                const float4 *l4 = reinterpret_cast<const float4 *>(Lt + m * kLtLd);
+#pragma unroll
+                for (int k4 = (m + 1) / 4; k4 < K / 4; ++k4) {
+                    const float4 l = l4[k4];
+                    if (4 * k4 + 0 > m) u[4 * k4 + 0] = fmaf(-l.x, um, u[4 * k4 + 0]);
+                    if (4 * k4 + 1 > m) u[4 * k4 + 1] = fmaf(-l.y, um, u[4 * k4 + 1]);
+                    if (4 * k4 + 2 > m) u[4 * k4 + 2] = fmaf(-l.z, um, u[4 * k4 + 2]);
+                    if (4 * k4 + 3 > m) u[4 * k4 + 3] = fmaf(-l.w, um, u[4 * k4 + 3]);
+                }
+            }
+            if (on) {
+#pragma unroll
+                for (int i = 0; i < K; ++i) p.AF[(int64_t)(rc + i) * p.ldf + col] = u[i];
+                char *dst = p.bop + (int64_t)c * p.bslot + (int64_t)(col - p.bbase) * K * esz;
+                if (p.tf == IR_TF32) {
+#pragma unroll
+                    for (int i = 0; i < K; i += 4) {
+                        uint32_t r4[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r4[h]) : "f"(u[i + h]));
+                        reinterpret_cast<uint4 *>(dst)[i / 4] = make_uint4(r4[0], r4[1], r4[2], r4[3]);
+                    }
+                } else if (p.tf == IR_BF16) {
+#pragma unroll
+                    for (int i = 0; i < K; i += 8) {
+                        __nv_bfloat162 p2[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) p2[h] = __floats2bfloat162_rn(u[i + 2 * h], u[i + 2 * h + 1]);
+                        reinterpret_cast<uint4 *>(dst)[i / 8] = *reinterpret_cast<uint4 *>(p2);
+                    }
+                } else {
+#pragma unroll
+                    for (int i = 0; i < K; i += 8) {
+                        __half2 p2[4];
+#pragma unroll
+                        for (int h = 0; h < 4; ++h) p2[h] = __floats2half2_rn(u[i + 2 * h], u[i + 2 * h + 1]);
+                        reinterpret_cast<uint4 *>(dst)[i / 8] = *reinterpret_cast<uint4 *>(p2);
+                    }
+                }
+            }
+            // the U slot rows are read back by TMA (async proxy) for the later blocks
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            mbar_arrive(uready_bar);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(kU12Acc * 64)
+                     : "memory");
+    }
+}
+
 using EncodeTiledFn = TensorMapEncodeFn;
 EncodeTiledFn get_encoder() { return tensor_map_encoder(); }
 
 // Operand slots: `slots` x rows x K, K contiguous (K-major); box = one 128-byte
-// K atom x 128 rows x 1 slot.
-bool make_slot_map(CUtensorMap *m, const void *base, int64_t rows, int slots, ir_dtype tf) {
+// K atom x box_rows rows x 1 slot.
+bool make_slot_map(CUtensorMap *m, const void *base, int64_t rows, int slots, ir_dtype tf, int box_rows = BM) {
     EncodeTiledFn enc = get_encoder();
     if (!enc) return false;
     const int esz = (tf == IR_TF32) ? 4 : 2;
@@ -366,7 +622,7 @@ bool make_slot_map(CUtensorMap *m, const void *base, int64_t rows, int slots, ir
                                                      : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
     cuuint64_t dims[3] = {(cuuint64_t)K, (cuuint64_t)rows, (cuuint64_t)slots};
     cuuint64_t strides[2] = {(cuuint64_t)K * esz, (cuuint64_t)rows * K * esz};
-    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)BM, 1};
+    cuuint32_t box[3] = {(cuuint32_t)(128 / esz), (cuuint32_t)box_rows, 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(m, dt, 3, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -390,9 +646,9 @@ bool make_c_map(CUtensorMap *m, float *base, int rows, int cols, int64_t ld) {
 // Instruction descriptor for kind::tf32 / kind::f16: D = F32 (bits 4-5 = 1),
 // A/B format (bits 7-9 / 10-12: F16 0, BF16 1, TF32 2), both K-major,
 // N >> 3 in bits 17-22, M >> 4 in bits 24-28.
-unsigned make_idesc(ir_dtype tf) {
+unsigned make_idesc(ir_dtype tf, int n_cols = BN) {
     const unsigned fmt = (tf == IR_TF32) ? 2u : (tf == IR_BF16) ? 1u : 0u;
-    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(BN >> 3) << 17) | ((unsigned)(BM >> 4) << 24);
+    return (1u << 4) | (fmt << 7) | (fmt << 10) | ((unsigned)(n_cols >> 3) << 17) | ((unsigned)(BM >> 4) << 24);
 }
 
 template <int KATOMS, int STAGES, int CBUFS>
@@ -402,6 +658,15 @@ constexpr size_t smem_bytes() {
 // 3 stages of one K atom (32 KB for A and B) and 2 C buffers (64 KB each)
 static_assert(smem_bytes<1, 3, 2>() <= 232448, "16-bit configuration exceeds shared memory");
 static_assert(smem_bytes<2, 3, 2>() <= 232448, "TF32 configuration exceeds shared memory");
+
+
+template <int KATOMS, int STAGES>
+constexpr size_t u12_smem_bytes() {
+    return 1024 + (size_t)STAGES * KATOMS * (kAtomBytes + kLAtomBytes) + (size_t)K * kLtLd * 4 +
+           8 * (2 * STAGES + 2 * kU12Acc + 2) + 16;
+}
+static_assert(u12_smem_bytes<1, 4>() <= 232448 && u12_smem_bytes<2, 3>() <= 232448,
+              "group U12 configuration exceeds shared memory");
 
 // Launch one update of C (rows x cols, binary32, row stride ldf) by the slots
 // [s0, s1) of the operand maps; a_row0 / b_row0: operand rows of C's first
@@ -455,25 +720,21 @@ cudaError_t launch_slots(float *C, int64_t ldf, int rows, int cols, const CUtens
         cfg.gridDim = dim3(8 * clusters, 1, 1);
         return cudaLaunchKernelEx(&cfg, kern, ta, tb, tc, p);
     };
-    if (tf == IR_TF32) {
-        static bool attr = false;
-        constexpr size_t sm = smem_bytes<2, 3, 2>();
+    auto go = [&](auto kern, size_t smem, bool &attr) -> cudaError_t {
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<2, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
             attr = true;
         }
-        return launch(k_gemm_tc<2, 3, 2>, sm);
-    } else {
-        static bool attr = false;
-        constexpr size_t sm = smem_bytes<1, 3, 2>();
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute(k_gemm_tc<1, 3, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        return launch(k_gemm_tc<1, 3, 2>, sm);
-    }
+        return launch(kern, smem);
+    };
+    const bool group = s1 - s0 > 1;
+    static bool a0 = false, a1 = false, a2 = false, a3 = false;
+    if (tf == IR_TF32)
+        return group ? go(k_gemm_tc<2, 3, 2, true>, smem_bytes<2, 3, 2>(), a0)
+                     : go(k_gemm_tc<2, 3, 2, false>, smem_bytes<2, 3, 2>(), a1);
+    return group ? go(k_gemm_tc<1, 3, 2, true>, smem_bytes<1, 3, 2>(), a2)
+                 : go(k_gemm_tc<1, 3, 2, false>, smem_bytes<1, 3, 2>(), a3);
 }
 
 }  // namespace
@@ -508,6 +769,54 @@ cudaError_t launch_gemm_tc_group(float *AF, int64_t ldf, int c0, int G, int r0, 
         return cudaErrorInvalidValue;
     return launch_slots(AF + (int64_t)r0 * ldf + cb, ldf, r1 - r0, ce - cb, ta, tb, r0 - c0, cb - bbase, s0, s1, tf,
                         sms, max_ctas, dev, s);
+}
+
+// U12 of the group's rows on the tensor cores (see k_u12_group_tc): far columns
+// [cb, ce); Agrp: the group's L slots (slot row i - c0 for matrix row i, a_rows
+// rows per slot); Bgrp: the U slots (slot row c - bbase for column c, b_rows rows
+// per slot, written here).
+cudaError_t launch_u12_group_tc(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf,
+                                const void *Agrp, int64_t a_rows, void *Bgrp, int64_t b_rows, int bbase,
+                                DevScalars *dev, cudaStream_t s) {
+    if (ce <= cb || G <= 0) return cudaSuccess;
+    if (cb < bbase || ce - bbase > b_rows || (int64_t)K * G > a_rows) return cudaErrorInvalidValue;
+    CUtensorMap tu, tl;
+    if (!make_slot_map(&tu, Bgrp, b_rows, G, tf) || !make_slot_map(&tl, Agrp, a_rows, G, tf, K))
+        return cudaErrorInvalidValue;
+    U12Params p;
+    p.AF = AF;
+    p.ldf = ldf;
+    p.c0 = c0;
+    p.G = G;
+    p.cb = cb;
+    p.ce = ce;
+    p.bbase = bbase;
+    p.bop = static_cast<char *>(Bgrp);
+    p.bslot = b_rows * K * (int64_t)((tf == IR_TF32) ? 4 : 2);
+    p.tf = tf;
+    p.idesc = make_idesc(tf, K);
+    p.timeout = &dev->timeout;
+    const int grid = (ce - cb + BM - 1) / BM;
+    static bool a16 = false, a32 = false;
+    count_launch();
+    if (tf == IR_TF32) {
+        constexpr size_t sm = u12_smem_bytes<2, 3>();
+        if (!a32) {
+            cudaError_t e = cudaFuncSetAttribute(k_u12_group_tc<2, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            a32 = true;
+        }
+        k_u12_group_tc<2, 3><<<grid, kU12Threads, sm, s>>>(tu, tl, p);
+    } else {
+        constexpr size_t sm = u12_smem_bytes<1, 4>();
+        if (!a16) {
+            cudaError_t e = cudaFuncSetAttribute(k_u12_group_tc<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            a16 = true;
+        }
+        k_u12_group_tc<1, 4><<<grid, kU12Threads, sm, s>>>(tu, tl, p);
+    }
+    return cudaGetLastError();
 }
 
 // rTF of the factor columns [c0, c0 + 64 G), rows [r0, r1), into the G slots of

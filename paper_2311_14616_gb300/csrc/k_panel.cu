@@ -409,33 +409,6 @@ __global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int
     lu::trsm64(AF, ldf, cb + blockIdx.x * kNarrowCols, ce, j, tf, Bop, Lt);
 }
 
-// U12 of a group's rows for the far columns [cb, ce) of the tensor-core LU,
-// one CTA per 64 columns, the group's G block rows in order: for block t, the
-// binary32 U12 solve (lu::trsm64, writing rTF(U) into operand slot t), then the
-// group's later block rows take block t's update (binary32 sum of the TF-rounded
-// products, subtracted) -- the right-looking LU's block steps restricted to the
-// group's rows.  bop0: slot 0's base shifted so that trsm64's operand row
-// c - (j + 64) lands at row c - cb; slot t is bslot bytes further.
-__global__ void __launch_bounds__(256) k_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce,
-                                                    ir_dtype tf, char *bop0, int64_t bslot) {
-    pdl_trigger();
-    pdl_wait();
-    __shared__ __align__(16) float Lt[NB][lu::kLd];   // trsm64's L11, then the update's L tile
-    __shared__ __align__(16) float Bs[NB][lu::kLd];
-    const int col0 = cb + blockIdx.x * kNarrowCols;
-    const size_t esz = (tf == IR_TF32) ? 4 : 2;
-    for (int t = 0; t < G; ++t) {
-        const int jt = c0 + NB * t;
-        char *bt = bop0 + t * bslot + (int64_t)(NB * t) * NB * (int64_t)esz;
-        lu::trsm64(AF, ldf, col0, ce, jt, tf, bt, Lt);
-        __syncthreads();                                   // this block row's U is in A_F
-        for (int t2 = t + 1; t2 < G; ++t2) {
-            lu::gemm_tile64_tf(AF, ldf, jt, col0, ce, c0 + NB * t2, tf, Lt, Bs);
-            __syncthreads();                               // the tiles are restaged next
-        }
-    }
-}
-
 __global__ void k_iota(int n, int32_t *perm) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) perm[i] = i;
 }
@@ -516,24 +489,6 @@ cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype 
     cfg.attrs = attr;
     cfg.numAttrs = set_pdl(&attr[0]);
     return cudaLaunchKernelEx(&cfg, k_trsm_narrow, AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
-}
-
-cudaError_t launch_trsm_group(float *AF, int64_t ldf, int c0, int G, int cb, int ce, ir_dtype tf, void *Bgrp,
-                              int64_t bslot, cudaStream_t s) {
-    const int ncols = ce - cb;
-    if (ncols <= 0 || G <= 0) return cudaSuccess;
-    count_launch();
-    // slot 0's operand row for column c must be c - cb: trsm64 writes row c - (c0 + 64), so shift by cb - c0 - 64
-    const size_t esz = (tf == IR_TF32) ? 4 : 2;
-    char *bop0 = static_cast<char *>(Bgrp) - (int64_t)(cb - (c0 + NB)) * NB * (int64_t)esz;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((ncols + kNarrowCols - 1) / kNarrowCols, 1, 1);
-    cfg.blockDim = dim3(256, 1, 1);
-    cfg.stream = s;
-    cudaLaunchAttribute attr[1];
-    cfg.attrs = attr;
-    cfg.numAttrs = set_pdl(&attr[0]);
-    return cudaLaunchKernelEx(&cfg, k_trsm_group, AF, ldf, c0, G, cb, ce, tf, bop0, bslot);
 }
 
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s) {

@@ -164,62 +164,5 @@ __device__ __forceinline__ void gemm_tile64(float *AF, int64_t ldf, int n, int j
     }
 }
 
-// C <- C - fl32(sum_k rTF(l_ik) rTF(u_kc)) on the 64 x 64 tile of rows i0 ..
-// i0 + 63 and columns cb .. cb + 63 (below ce), K = the 64 columns j .. j + 63:
-// one block step of the tensor-core LU's update with binary32 accumulation, the
-// products summed from zero by fmaf in ascending k, then subtracted from C.
-// Same thread layout and shared tiles as gemm_tile64.
-__device__ __forceinline__ void gemm_tile64_tf(float *AF, int64_t ldf, int j, int cb, int ce, int i0, ir_dtype tf,
-                                               float (*As)[kLd], float (*Bs)[kLd]) {
-    const int t = threadIdx.x, tx = t & 15, ty = t >> 4;
-    {
-        constexpr int R = NB * NB / 4 / 256;
-        float4 va[R], vb[R];
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int e = t + q * 256, ra = e % NB, ka = (e / NB) * 4, i = i0 + ra;
-            const int rb = e >> 4, cq = (e & 15) * 4, c = cb + cq;
-            va[q] = *reinterpret_cast<const float4 *>(AF + (int64_t)i * ldf + j + ka);
-            vb[q] = (c < ce) ? *reinterpret_cast<const float4 *>(AF + (int64_t)(j + rb) * ldf + c)
-                             : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int q = 0; q < R; ++q) {
-            const int e = t + q * 256, ra = e % NB, ka = (e / NB) * 4, rb = e >> 4, cq = (e & 15) * 4;
-            As[ka + 0][ra] = round_tf(va[q].x, tf);
-            As[ka + 1][ra] = round_tf(va[q].y, tf);
-            As[ka + 2][ra] = round_tf(va[q].z, tf);
-            As[ka + 3][ra] = round_tf(va[q].w, tf);
-            *reinterpret_cast<float4 *>(&Bs[rb][cq]) = make_float4(round_tf(vb[q].x, tf), round_tf(vb[q].y, tf),
-                                                                  round_tf(vb[q].z, tf), round_tf(vb[q].w, tf));
-        }
-    }
-    float acc[4][4];
-#pragma unroll
-    for (int r = 0; r < 4; ++r)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[r][q] = 0.f;
-    __syncthreads();
-#pragma unroll 8
-    for (int k = 0; k < NB; ++k) {
-        const float4 a = *reinterpret_cast<const float4 *>(&As[k][ty * 4]);
-        const float4 b = *reinterpret_cast<const float4 *>(&Bs[k][tx * 4]);
-        const float ar[4] = {a.x, a.y, a.z, a.w}, br[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) acc[r][q] = fmaf(ar[r], br[q], acc[r][q]);
-    }
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-        const int i = i0 + ty * 4 + r, c = cb + tx * 4;
-        if (c < ce) {
-            float4 *p = reinterpret_cast<float4 *>(AF + (int64_t)i * ldf + c);
-            const float4 v = *p;
-            *p = make_float4(v.x - acc[r][0], v.y - acc[r][1], v.z - acc[r][2], v.w - acc[r][3]);
-        }
-    }
-}
-
 }  // namespace lu
 }  // namespace ir
