@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--order", dest="n", type=int, default=N_DEFAULT, help="order N of the headline system")
+    ap.add_argument("--group", type=int, default=0,
+                    help="fixed group size of the tensor-core LU for the headline (0: autotuned schedule)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
@@ -516,7 +518,8 @@ def main():
         os.environ.setdefault("OMP_NUM_THREADS", str(cpu_cores()))
 
     # --- headline: TF = binary16 (scaled), tensor-core trailing update
-    fact = ctx.factor(A_d, tf="f16", autotune=True)      # schedule timed on this A before the run
+    tune = args.group == 0
+    fact = ctx.factor(A_d, tf="f16", autotune=tune, group=args.group)   # schedule timed on this A before the run
     sched16 = fact.schedule()
     x16 = torch.empty_like(b_d)
     term = ir.default_term()
@@ -541,7 +544,7 @@ def main():
     x16h = x16.double().cpu().numpy()
 
     # --- the same system with bfloat16 factors (unscaled)
-    factb = ctx.factor(A_d, tf="bf16", autotune=True)
+    factb = ctx.factor(A_d, tf="bf16", autotune=tune, group=args.group)
     xb = torch.empty_like(b_d)
 
     def stepb():
@@ -659,7 +662,7 @@ def main():
     cfg = headline_config(n)
     cfg.update({"parallelism": "replicas" if ws > 1 else "single",
                 "schedule": {"nb": sched16[0], "panel_reserve_sms": sched16[1], "group": sched16[2],
-                             "autotuned": True}})
+                             "autotuned": tune}})
     out = {
         "metric": "ir_solve_ms", "value": value, "unit": "ms", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t16, "higher_is_better": False, "scaling": "weak",

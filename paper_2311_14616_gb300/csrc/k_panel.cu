@@ -29,12 +29,14 @@ constexpr int NW = T / 32;
 // rows and tracks their current positions, so an interchange is a few integer
 // compares and the panel's net permutation is known at the end.
 //
-// Candidate exchange: at step k every warp stages its best row as a 272-byte
-// record (|a| bits, position, fl(1/a), the 64 row values, pad) and the CTA's
-// best record is pushed, 17 chunks of 16 bytes per destination, each stored by
-// its own thread with st.async, into slot [k & 1][its rank] of every CTA of
-// the cluster, counted on the receiver's mbarrier.  A receiver waits
-// (bounded) for all records of the step.
+// Candidate exchange: at step k every warp stages its best row as a record
+// (|a| bits, position, fl(1/a), the row's 64 - k live values; at most 272
+// bytes) and the CTA's best record is pushed, in chunks of 16 bytes (17 at
+// step 0, one fewer every four steps), each stored by its own thread with
+// st.async, into slot [k & 1][its rank] of every CTA of the cluster, counted
+// on the receiver's mbarrier.  A receiver waits (bounded) for all records of
+// the step.  Values past the live width are never sent: the receivers' update
+// may read stale ones there, but only into window entries that are dead.
 constexpr int kRec = 68;                     // floats per record
 constexpr int kChunks = kRec / 4;            // 16-byte chunks per record
 struct PanelSmem {
@@ -73,14 +75,18 @@ __device__ __forceinline__ void store_op_chunk(void *op, int64_t row, int q, flo
     }
 }
 
-// Stage one row window as a candidate record: |a| bits, position, fl(1/a),
-// the 64 values (record[3 + i] = a[i]), pad.
-__device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], unsigned key, int pos) {
+// 16-byte chunks of step k's record: the header (3 floats) and the 64 - k live values.
+__device__ __forceinline__ int rec_chunks(int k) { return (70 - k) / 4; }
+
+// Stage the first nch chunks of a row window as a candidate record: |a| bits,
+// position, fl(1/a), the values (record[3 + i] = a[i]).
+__device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], unsigned key, int pos, int nch) {
     float4 *s4 = reinterpret_cast<float4 *>(st);
     s4[0] = make_float4(__uint_as_float(key), __int_as_float(pos), (a[0] != 0.f) ? __frcp_rn(a[0]) : 0.f, a[0]);
 #pragma unroll
-    for (int q = 0; q < 15; ++q) s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
-    s4[16] = make_float4(a[61], a[62], a[63], 0.f);
+    for (int q = 0; q < 15; ++q)
+        if (1 + q < nch) s4[1 + q] = make_float4(a[4 * q + 1], a[4 * q + 2], a[4 * q + 3], a[4 * q + 4]);
+    if (16 < nch) s4[16] = make_float4(a[61], a[62], a[63], 0.f);
 }
 
 // One cluster factors the panel AF[j:n, j:j+nbp].  Thread t of CTA c keeps
@@ -91,7 +97,8 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 // candidate (largest |a|, ties to the lowest current position: redux.sync)
 // staged as a record -> the CTA's best record pushed to every CTA (st.async,
 // one thread per 16-byte chunk and destination) -> bounded wait on the local
-// mbarrier -> every warp picks the pivot row from the received headers ->
+// mbarrier -> every warp picks the pivot row from the received headers (a
+// single-CTA cluster takes its best record directly) ->
 // positions k and p swap labels -> scaling by the pivot's reciprocal and
 // rank-1 update of the rows that are not pivot rows (both rows of a thread
 // share the loads of the pivot row).  The column loop touches no global
@@ -100,6 +107,7 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 // staged at that step.  Rows that moved are listed as (destination, origin)
 // pairs in swap_list (count in swap_list[0]) for the interchanges of the
 // other columns, and perm is composed with the panel's permutation.
+template <bool kSingle>     // kSingle: a cluster of one CTA (no exchange)
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
             int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
@@ -114,7 +122,7 @@ __global__ void __launch_bounds__(T, 1)
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int home0 = (int)crank * RPC + t, home1 = home0 + T;   // start positions, relative to j
     const bool valid0 = j + home0 < n, valid1 = j + home1 < n;
-    const unsigned step_bytes = csize * (unsigned)(kRec * 4);
+    auto step_bytes = [&](int k) { return csize * 16u * (unsigned)rec_chunks(k); };
     const int nsend = (int)csize * kChunks;                       // record chunks to store per step
 
     int pos0 = home0, pos1 = home1;     // current positions, relative to j
@@ -126,8 +134,10 @@ __global__ void __launch_bounds__(T, 1)
         mbar_init_p(smem_u32(&sm.recv_bar[0]), 1);
         mbar_init_p(smem_u32(&sm.recv_bar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        mbar_expect_arrive(smem_u32(&sm.recv_bar[0]), step_bytes);
-        if (nbp > 1) mbar_expect_arrive(smem_u32(&sm.recv_bar[1]), step_bytes);
+        if (!kSingle) {      // a single CTA exchanges nothing
+            mbar_expect_arrive(smem_u32(&sm.recv_bar[0]), step_bytes(0));
+            if (nbp > 1) mbar_expect_arrive(smem_u32(&sm.recv_bar[1]), step_bytes(1));
+        }
     }
     float a0[NB], a1[NB];
     {
@@ -176,57 +186,66 @@ __global__ void __launch_bounds__(T, 1)
         // the warp's candidate, staged as a record
         const bool c0 = valid0 && kp0 == nbp, c1 = valid1 && kp1 == nbp;
         float *st = sm.stage[buf][warp];
+        const int nch = rec_chunks(k);
         if (tc && tpos == mpos) {
             if (use1)
-                stage_record(st, a1, kmax, mpos);
+                stage_record(st, a1, kmax, mpos, nch);
             else
-                stage_record(st, a0, kmax, mpos);
+                stage_record(st, a0, kmax, mpos, nch);
         }
         if (lane == 0 && mpos == INT_MAX) {
             st[0] = 0.f;
             st[1] = __int_as_float(INT_MAX);
         }
         __syncthreads();
-        // 2. the CTA's best record, pushed to every CTA of the cluster: chunk
-        //    i % 17 of it into CTA i / 17 for i = t, t + T, ... (st.async, counted
-        //    on the receiver's mbarrier)
-        {
-            const unsigned wk = lane < NW ? __float_as_uint(sm.stage[buf][lane][0]) : 0u;
-            const int wp = lane < NW ? __float_as_int(sm.stage[buf][lane][1]) : INT_MAX;
-            const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
-            const int bp = __reduce_min_sync(0xffffffffu, (wp != INT_MAX && wk == bk) ? wp : INT_MAX);
-            const unsigned who = __ballot_sync(0xffffffffu, lane < NW && wp == bp);
-            const int w = who ? __ffs(who) - 1 : 0;
+        // 2. the CTA's best record (the best of its warps' records)
+        const unsigned wk = lane < NW ? __float_as_uint(sm.stage[buf][lane][0]) : 0u;
+        const int wp = lane < NW ? __float_as_int(sm.stage[buf][lane][1]) : INT_MAX;
+        const unsigned bk = __reduce_max_sync(0xffffffffu, wk);
+        const int bp = __reduce_min_sync(0xffffffffu, (wp != INT_MAX && wk == bk) ? wp : INT_MAX);
+        const unsigned who = __ballot_sync(0xffffffffu, lane < NW && wp == bp);
+        const int w = who ? __ffs(who) - 1 : 0;
+        const float *u;     // u[3 + i] = pivot row, column j + k + i
+        int ppos;
+        if constexpr (kSingle) {
+            // a single CTA: its best record is the pivot row
+            ppos = bp;
+            u = sm.stage[buf][w];
+        } else {
+            // pushed to every CTA of the cluster: chunk i % 17 of it (if live)
+            // into CTA i / 17 for i = t, t + T, ... (st.async, counted on the
+            // receiver's mbarrier)
             for (int snd = t; snd < nsend; snd += T) {
                 const int dst = snd / kChunks, ch = snd % kChunks;
+                if (ch >= nch) continue;
                 const float4 v = reinterpret_cast<const float4 *>(sm.stage[buf][w])[ch];
                 const unsigned slot = recv_addr + (unsigned)(((buf * kPanelMaxCluster + (int)crank) * kRec + 4 * ch) * 4);
                 st_async_v4(map_cta(slot, (unsigned)dst), v, map_cta(bar_addr + 8u * buf, (unsigned)dst));
             }
-        }
-        // 3. every warp waits (bounded) for the records of all CTAs of this step
-        const unsigned par = (unsigned)(k >> 1) & 1u;
-        if (lane == 0 && !sm.abort_flag) {
-            while (!mbar_try_wait_cluster(bar_addr + 8u * buf, par)) {
-                if (globaltimer() > deadline) {      // give up: report, carry on without waiting
-                    sm.abort_flag = 1;
-                    atomicExch(&dev->timeout, 1);
-                    break;
+            // 3. every warp waits (bounded) for the records of all CTAs of this step
+            const unsigned par = (unsigned)(k >> 1) & 1u;
+            if (lane == 0 && !sm.abort_flag) {
+                while (!mbar_try_wait_cluster(bar_addr + 8u * buf, par)) {
+                    if (globaltimer() > deadline) {      // give up: report, carry on without waiting
+                        sm.abort_flag = 1;
+                        atomicExch(&dev->timeout, 1);
+                        break;
+                    }
                 }
             }
+            __syncwarp();
+            // re-arm this buffer for step k + 2 (before this CTA sends its next record)
+            if (t == 0 && k + 2 < nbp && !sm.abort_flag) mbar_expect_arrive(bar_addr + 8u * buf, step_bytes(k + 2));
+            // 4. the pivot row, picked by every warp from the received headers
+            const float *rb = sm.recv[buf][0];
+            const unsigned ck = lane < (int)csize ? __float_as_uint(rb[lane * kRec]) : 0u;
+            const int cp = lane < (int)csize ? __float_as_int(rb[lane * kRec + 1]) : INT_MAX;
+            const unsigned ckmax = __reduce_max_sync(0xffffffffu, ck);
+            ppos = __reduce_min_sync(0xffffffffu, (cp != INT_MAX && ck == ckmax) ? cp : INT_MAX);
+            const unsigned cwho = __ballot_sync(0xffffffffu, lane < (int)csize && cp == ppos);
+            const int wc = cwho ? __ffs(cwho) - 1 : 0;
+            u = rb + wc * kRec;
         }
-        __syncwarp();
-        // re-arm this buffer for step k + 2 (before this CTA sends its next record)
-        if (t == 0 && k + 2 < nbp && !sm.abort_flag) mbar_expect_arrive(bar_addr + 8u * buf, step_bytes);
-        // 4. the pivot row, picked by every warp from the received headers
-        const float *rb = sm.recv[buf][0];
-        const unsigned ck = lane < (int)csize ? __float_as_uint(rb[lane * kRec]) : 0u;
-        const int cp = lane < (int)csize ? __float_as_int(rb[lane * kRec + 1]) : INT_MAX;
-        const unsigned ckmax = __reduce_max_sync(0xffffffffu, ck);
-        const int ppos = __reduce_min_sync(0xffffffffu, (cp != INT_MAX && ck == ckmax) ? cp : INT_MAX);
-        const unsigned cwho = __ballot_sync(0xffffffffu, lane < (int)csize && cp == ppos);
-        const int wc = cwho ? __ffs(cwho) - 1 : 0;
-        const float *u = rb + wc * kRec;                // u[3 + i] = pivot row, column j + k + i
         const float piv = u[3];
         const float r = u[2];
         if (t == 0) {
@@ -420,10 +439,12 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
                          void *Aop, cudaStream_t s) {
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
-        if (e != cudaSuccess) return e;
-        e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelDynSmem);
-        if (e != cudaSuccess) return e;
+        for (auto kern : {k_panel<false>, k_panel<true>}) {
+            cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelDynSmem);
+            if (e != cudaSuccess) return e;
+        }
         attr_done = true;
     }
     int M = n - j;
@@ -443,8 +464,8 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
     cfg.numAttrs = 1 + set_pdl(&attr[1]);
     int has_trailing = (j + NB < n) ? 1 : 0;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, k_panel, AF, ldf, n, j, nbp, ipiv, perm, swap_list, dev, tf, Aop,
-                              has_trailing);
+    return cudaLaunchKernelEx(&cfg, C == 1 ? k_panel<true> : k_panel<false>, AF, ldf, n, j, nbp, ipiv, perm,
+                              swap_list, dev, tf, Aop, has_trailing);
 }
 
 cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b, const int32_t *swap_list,
