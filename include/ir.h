@@ -154,7 +154,13 @@ ir_status ir_refactor(ir_fact *fact, const void *B, int64_t ldb, void *stream);
  *   term may be NULL (defaults).  rep may be NULL.
  * Returns IR_ESINGULAR / IR_ENONFINITE when the factorization failed (rep
  * then carries info), IR_ENONFINITE for a non-finite b, IR_ETIMEOUT when a
- * device wait gave up.  The call synchronizes `stream` once per iteration. */
+ * device wait gave up.  The refinement loop runs on the device: the call
+ * enqueues term->litmax corrections at once, each followed by a one-thread
+ * kernel that applies the termination test of Sec. 5.1 to the device-side
+ * histories; once it has decided, the remaining corrections' kernels return
+ * without work.  The call synchronizes `stream` twice: once to read the
+ * factorization's outcome before enqueueing, once at the end to read the
+ * loop's result.  x is not written when the call fails. */
 ir_status ir_solve(ir_fact *fact, const void *b, void *x, const ir_term *term,
                    void *stream, ir_report *rep);
 

@@ -29,12 +29,12 @@ namespace {
 enum Kind {
     KC_CAST, KC_MAXABS, KC_IOTA, KC_PANEL, KC_LASWP, KC_TRSM, KC_GEMM_SIMT, KC_GEMM_TC,
     KC_DIAGINV, KC_INIT, KC_TRSV, KC_RESID, KC_STOREX, KC_BATCHED, KC_GM_ORTH, KC_GM_UPDATE, KC_NORM1, KC_BI_STEP,
-    KC_GEMM_TC_GROUP, KC_PACK, KC_TRSV64, KC_STORE, KC_U12_GROUP, KC_N
+    KC_GEMM_TC_GROUP, KC_PACK, KC_TRSV64, KC_STORE, KC_U12_GROUP, KC_TERM, KC_N
 };
 const char *kKindNames[KC_N] = {"cast", "maxabs", "iota", "panel", "laswp", "trsm", "gemm_simt",
                                 "gemm_tc", "diag_inv", "init_rb", "trsv_pair", "residual", "store_x",
                                 "batched", "gm_orth", "krylov_update", "norm1", "bi_step",
-                                "gemm_tc_group", "pack", "trsv_pair_f64", "store_tf", "u12_group"};
+                                "gemm_tc_group", "pack", "trsv_pair_f64", "store_tf", "u12_group", "term"};
 struct ProfRec {
     int kind;
     cudaEvent_t a, b;
@@ -163,6 +163,8 @@ void free_fact(ir_fact *f) {
     cudaFree(f->r);
     cudaFree(f->dev);
     if (f->host_dev) cudaFreeHost(f->host_dev);
+    cudaFree(f->loop);
+    if (f->host_loop) cudaFreeHost(f->host_loop);
     cudaFree(f->gm_V);
     cudaFree(f->gm_W);
     cudaFree(f->gm_st);
@@ -231,8 +233,10 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     AL(f->x, nn * sizeof(double));
     AL(f->r, nn * sizeof(double));
     AL(f->dev, sizeof(DevScalars));
+    AL(f->loop, sizeof(SolveLoop));
 #undef AL
-    if (cudaMallocHost((void **)&f->host_dev, sizeof(DevScalars)) != cudaSuccess) {
+    if (cudaMallocHost((void **)&f->host_dev, sizeof(DevScalars)) != cudaSuccess ||
+        cudaMallocHost((void **)&f->host_loop, sizeof(SolveLoop)) != cudaSuccess) {
         st = IR_ENOMEM;
         goto fail;
     }
@@ -374,8 +378,7 @@ ir_status enqueue_factor_grouped(ir_fact *f, cudaStream_t s) {
                 }
                 const int nx0 = j + NB, nx1 = (j + 2 * NB < n) ? j + 2 * NB : n;
                 // s1: the next block column
-                RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, nx0, nx1, 0, 0, sl, s));
-                RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, s));
+                RUN(KC_TRSM, s, launch_laswp_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, sl, s));
                 RUN(KC_GEMM_TC, s, launch_gemm_tc(f->AF, ldf, n, j, NB, nx0, nx1, f->TF, aop, bop, sms, 0, f->dev, s));
                 // s2: the rest of the near columns
                 CK(cudaStreamWaitEvent(s2, evP, 0));
@@ -503,8 +506,7 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
             }
             const int nx0 = j + NB, nx1 = (j + 2 * NB < n) ? j + 2 * NB : n;
             // s1: the next block column
-            RUN(KC_LASWP, s, launch_laswp(f->AF, ldf, nx0, nx1, 0, 0, sl, s));
-            RUN(KC_TRSM, s, launch_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, s));
+            RUN(KC_TRSM, s, launch_laswp_trsm(f->AF, ldf, nx0, nx1, j, f->TF, bop, sl, s));
             if (f->TF == IR_F32)
                 RUN(KC_GEMM_SIMT, s, launch_gemm_simt(f->AF, ldf, n, j, NB, nx0, nx1, 0, s));
             else
@@ -588,29 +590,21 @@ ir_status read_dev(ir_fact *f, cudaStream_t s) {
     return IR_OK;
 }
 
-// Termination test of Sec. 5.1 after the k-th residual (rh[0..k], dh[0..k-1]).
-// Returns -1 to continue, else an ir_solve_status.
-// rmax_r: the factor of the residual-stagnation test (t->Rmax for IR).  With
-// t->mode = 1 the small-residual test is the backward-error test (eq. term),
-// anorm = ||A||_1, xnorm = ||x||_inf of the current iterate.
+// Termination test of Sec. 5.1 after the k-th residual (the rule shared with
+// the device loop, ir_internal.cuh): -1 to continue, else an ir_solve_status.
 int term_decide(const double *rh, const double *dh, int k, double bnorm, double eps_w,
                 const ir_term *t, bool tr_wider, double rmax_r, double anorm, double xnorm) {
-    const double rn = rh[k];
-    if (!std::isfinite(rn)) return IR_DIVERGED;
-    if (rn == 0.0) return IR_CONVERGED;    // exact solution: r / ||r|| (eq. vdlow) is undefined next
-    if (tr_wider) {
-        if (k >= 2 && dh[k - 1] >= t->Rmax * dh[k - 2]) return IR_STAGNATED;   // eq. (wilkterm)
-    } else {
-        if (t->mode == 1) {
-            if (rn <= t->Ce * eps_w * (bnorm + anorm * xnorm)) return IR_CONVERGED;   // eq. (term)
-        } else {
-            const double tol = t->abs_rel_tol > 0 ? t->abs_rel_tol : t->Cr * eps_w;
-            if (rn <= tol * bnorm) return IR_CONVERGED;                       // eq. (residterm)
-        }
-        if (k >= 1 && rn >= rmax_r * rh[k - 1]) return IR_STAGNATED;          // eq. (stag)
-    }
-    if (k >= t->litmax) return IR_MAXIT;
-    return -1;
+    TermArgs ta;
+    ta.Cr = t->Cr;
+    ta.Ce = t->Ce;
+    ta.Rmax = t->Rmax;
+    ta.rmax_r = rmax_r;
+    ta.abs_rel_tol = t->abs_rel_tol;
+    ta.eps_w = eps_w;
+    ta.litmax = t->litmax;
+    ta.mode = t->mode;
+    ta.tr_wider = tr_wider ? 1 : 0;
+    return term_rule(rh, dh, k, bnorm, ta, anorm, xnorm);
 }
 
 }  // namespace
@@ -966,60 +960,62 @@ ir_status ir_solve(ir_fact *f, const void *b, void *x, const ir_term *term, void
                        cudaMemcpyDeviceToDevice, s));
     if (t.mode == 1 && !f->anorm_valid)
         RUN(KC_NORM1, s, launch_norm1(n, f->TW, f->A, f->lda, &f->dev->anorm_bits, s));
-    st = read_dev(f, s);
-    if (st != IR_OK) return st;
-    if (f->host_dev->nonfinite) {
-        // b (or A's norm) is not finite: the flag belongs to this call, not to the factorization
-        CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));
-        R.status = IR_FAILED;
-        if (rep) *rep = R;
-        return IR_ENONFINITE;
-    }
-    if (t.mode == 1) f->anorm_valid = 1;
-    const double anorm = bits_to_double(f->host_dev->anorm_bits);
-    const double bnorm = bits_to_double(f->host_dev->bnorm_bits);
-    R.rhist[0] = bnorm;
-    const bool tr_wider = (f->TW == IR_F32);
-    const double eps_w = eps_of(f->TW);
-    int k = 0;
-    int status = (bnorm == 0.0) ? IR_CONVERGED : -1;
+    // The refinement loop runs on the device: litmax corrections are enqueued at
+    // once, each followed by the termination test (k_loop_step); once it has
+    // decided, the remaining kernels return at once.  One read-back at the end.
+    TermArgs ta;
+    ta.Cr = t.Cr;
+    ta.Ce = t.Ce;
+    ta.Rmax = t.Rmax;
+    ta.rmax_r = t.Rmax;
+    ta.abs_rel_tol = t.abs_rel_tol;
+    ta.eps_w = eps_of(f->TW);
+    ta.litmax = t.litmax;
+    ta.mode = t.mode;
+    ta.tr_wider = (f->TW == IR_F32) ? 1 : 0;
     const bool mps64 = f->onthefly && f->TW == IR_F64;
     if (f->onthefly && !mps64) {
         // TW = binary32: r rounded to binary32, binary32 solves with unit scale
         static const double one = 1.0;
         CK(cudaMemcpyAsync(&f->dev->one_bits, &one, sizeof(double), cudaMemcpyHostToDevice, s));
     }
-    while (status < 0) {
+    RUN(KC_TERM, s, launch_loop_start(f->dev, f->loop, ta, s));
+    const int *done = &f->loop->done;
+    for (int it = 0; it < t.litmax; ++it) {
         f->epoch += 1;
-        CK(cudaMemsetAsync(&f->dev->dnorm_bits, 0, 2 * sizeof(unsigned long long), s));   // dnorm, xnorm
         if (mps64)
             RUN(KC_TRSV64, s, launch_mps_pair(f->AF, f->ldf, (int)n, f->perm, f->r, f->x, f->y64, f->z64,
-                                              f->mps_flags, f->epoch, f->dev, s));
+                                              f->mps_flags, f->epoch, f->dev, s, done));
         else
             RUN(KC_TRSV, s, launch_trsv_pair(f->AF, f->ldf, (int)n, f->Linv, f->Uinv, f->blk_subst, f->perm, f->r,
                                              nullptr, nullptr, f->x, f->tags, f->epoch, f->dev, s, nullptr,
-                                             nullptr, nullptr, f->onthefly != 0, f->AF16, f->TF));
+                                             nullptr, done, f->onthefly != 0, f->AF16, f->TF));
         RUN(KC_RESID, s, launch_residual(n, f->TW, f->A, f->lda, b, f->x, f->r, f->ctx->partials,
-                           f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s));
-        st = read_dev(f, s);
-        if (st != IR_OK) return st;
-        if (f->host_dev->timeout) {
-            snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the triangular solve timed out");
-            return IR_ETIMEOUT;
-        }
-        ++k;
-        R.dhist[k - 1] = bits_to_double(f->host_dev->dnorm_bits);
-        R.rhist[k] = bits_to_double(f->host_dev->rnorm_bits);
-        status = term_decide(R.rhist, R.dhist, k, bnorm, eps_w, &t, tr_wider, t.Rmax, anorm,
-                             bits_to_double(f->host_dev->xnorm_bits));
+                           f->ctx->partials_cap, &f->dev->rnorm_bits, f->ctx->sms, s, done));
+        RUN(KC_TERM, s, launch_loop_step(f->dev, f->loop, ta, s));
     }
-    RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s));
-    R.iters = k;
-    R.status = (ir_solve_status)status;
-    if (rep) {
-        CK(cudaStreamSynchronize(s));
-        *rep = R;
+    // x is written unless the solve failed (b not finite, or a wait timed out)
+    RUN(KC_STOREX, s, launch_store_x(n, f->TW, f->x, x, s, &f->loop->err));
+    CK(cudaMemcpyAsync(f->host_loop, f->loop, sizeof(SolveLoop), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    const SolveLoop &L = *f->host_loop;
+    if (L.err == kLoopNonfinite) {
+        // b (or A's norm) is not finite: the flag belongs to this call, not to the factorization
+        CK(cudaMemsetAsync(&f->dev->nonfinite, 0, sizeof(int), s));
+        R.status = IR_FAILED;
+        if (rep) *rep = R;
+        return IR_ENONFINITE;
     }
+    if (L.err == kLoopTimeout) {
+        snprintf(g_last_error, sizeof g_last_error, "a bounded wait in the triangular solve timed out");
+        return IR_ETIMEOUT;
+    }
+    if (t.mode == 1) f->anorm_valid = 1;
+    R.iters = L.k;
+    R.status = (ir_solve_status)L.status;
+    for (int i = 0; i <= L.k && i < IR_MAX_HIST; ++i) R.rhist[i] = L.rhist[i];
+    for (int i = 0; i < L.k && i < IR_MAX_HIST; ++i) R.dhist[i] = L.dhist[i];
+    if (rep) *rep = R;
     return IR_OK;
 }
 

@@ -46,6 +46,68 @@ struct DevScalars {
     unsigned int ticket[2];          // CTA ticket counters of the two solves
 };
 
+// State of one refinement loop run on the device (ir_solve): the termination
+// test of Sec. 5.1 is evaluated by a one-thread kernel after every residual, so
+// a whole solve is enqueued at once and the host reads this back at the end.
+struct SolveLoop {
+    int status;      // -1 while refining, else an ir_solve_status
+    int k;           // corrections applied
+    int done;        // 1: the remaining iterations' kernels return at once
+    int err;         // 0, kLoopNonfinite (b or ||A||_1 not finite) or kLoopTimeout
+    double rhist[IR_MAX_HIST];
+    double dhist[IR_MAX_HIST];
+};
+constexpr int kLoopNonfinite = 1, kLoopTimeout = 2;
+
+// The termination test's parameters (ir_term with the precision's unit roundoff).
+struct TermArgs {
+    double Cr, Ce, Rmax, abs_rel_tol, eps_w, rmax_r;
+    int litmax, mode, tr_wider;
+};
+
+// Termination test of Sec. 5.1 after the k-th residual (rh[0..k], dh[0..k-1]):
+// -1 to continue, else an ir_solve_status.  rmax_r: the factor of the
+// residual-stagnation test.  With mode = 1 the small-residual test is the
+// backward-error test (eq. term), anorm = ||A||_1, xnorm = ||x||_inf.  Every
+// product and sum is rounded on its own (no fused multiply-add), so host and
+// device decide alike.
+__host__ __device__ inline double term_mul(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dmul_rn(a, b);
+#else
+    volatile double p = a * b;
+    return p;
+#endif
+}
+__host__ __device__ inline double term_add(double a, double b) {
+#ifdef __CUDA_ARCH__
+    return __dadd_rn(a, b);
+#else
+    volatile double q = a + b;
+    return q;
+#endif
+}
+__host__ __device__ inline int term_rule(const double *rh, const double *dh, int k, double bnorm,
+                                         const TermArgs &t, double anorm, double xnorm) {
+    const double rn = rh[k];
+    if (!isfinite(rn)) return IR_DIVERGED;
+    if (rn == 0.0) return IR_CONVERGED;    // exact solution: r / ||r|| (eq. vdlow) is undefined next
+    if (t.tr_wider) {
+        if (k >= 2 && dh[k - 1] >= term_mul(t.Rmax, dh[k - 2])) return IR_STAGNATED;   // eq. (wilkterm)
+    } else {
+        if (t.mode == 1) {
+            const double be = term_mul(term_mul(t.Ce, t.eps_w), term_add(bnorm, term_mul(anorm, xnorm)));
+            if (rn <= be) return IR_CONVERGED;                                        // eq. (term)
+        } else {
+            const double tol = t.abs_rel_tol > 0 ? t.abs_rel_tol : term_mul(t.Cr, t.eps_w);
+            if (rn <= term_mul(tol, bnorm)) return IR_CONVERGED;                      // eq. (residterm)
+        }
+        if (k >= 1 && rn >= term_mul(t.rmax_r, rh[k - 1])) return IR_STAGNATED;       // eq. (stag)
+    }
+    if (k >= t.litmax) return IR_MAXIT;
+    return -1;
+}
+
 // Scalars of a block of up to 4 right-hand sides refined together (ir_solve_many).
 struct MultiScalars {
     unsigned long long rho[4];     // ||r_j||_inf (the scale of the next solve, then rhist)
@@ -144,6 +206,8 @@ struct ir_fact {
     ir::DevScalars *dev;
     int anorm_valid;         // dev->anorm_bits holds ||A||_1 of the current A
     ir::DevScalars *host_dev;  // pinned mirror
+    ir::SolveLoop *loop;       // device-side refinement loop of ir_solve
+    ir::SolveLoop *host_loop;  // pinned mirror
     // the factorization's launch sequence as a CUDA graph (captured for one A)
     cudaStream_t cap_stream;
     cudaGraphExec_t graph;
@@ -181,7 +245,13 @@ cudaError_t launch_norm1(int64_t n, ir_dtype tw, const void *A, int64_t lda, uns
                          cudaStream_t s);
 cudaError_t launch_init_rb(int64_t n, ir_dtype tw, const void *b, double *r, double *x,
                            DevScalars *dev, cudaStream_t s);
-cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s);
+cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s,
+                           const int *skip = nullptr);
+// The device-side refinement loop (k_resid.cu): loop_start after x = 0, r = b
+// (rhist[0] = ||b||, the flags of b and ||A||_1); loop_step after each residual
+// (appends ||d||, ||r||, decides, clears ||d|| and ||x|| for the next step).
+cudaError_t launch_loop_start(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s);
+cudaError_t launch_loop_step(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s);
 
 cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
                          int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
@@ -194,6 +264,9 @@ cudaError_t launch_laswp_lists(float *AF, int64_t ldf, int c0, int c1, const int
                                int first, int count, cudaStream_t s);
 cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
                         cudaStream_t s);
+// The panel's row interchanges on the columns [cb, ce), then their U12 (one launch).
+cudaError_t launch_laswp_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
+                              const int32_t *swap_list, cudaStream_t s);
 cudaError_t launch_gemm_simt(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
                              int max_ctas, cudaStream_t s);
 cudaError_t launch_gemm_tc(float *AF, int64_t ldf, int n, int j, int nb, int cb, int ce,
@@ -253,7 +326,8 @@ cudaError_t launch_store_tf(float *AF, int64_t ldf, int n, ir_dtype tf, void *F1
 // blocks of kMpsB rows
 // on the binary32 factors; ||d||, ||x|| into dev.
 cudaError_t launch_mps_pair(const float *AF, int64_t ldf, int n, const int32_t *perm, const double *r, double *x,
-                            double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s);
+                            double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s,
+                            const int *skip = nullptr);
 // One thread runs the solves' bounded tag wait on tags[0] for a tag that is
 // never written, with the limit limit_ns; it sets *timeout when it gives up.
 cudaError_t launch_wait_probe(const unsigned long long *tags, unsigned tag, unsigned long long limit_ns,

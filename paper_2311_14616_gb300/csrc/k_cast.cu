@@ -119,7 +119,8 @@ __global__ void k_init_rb(int64_t n, const TW *b, double *r, double *x, DevScala
 }
 
 template <typename TW>
-__global__ void k_store_x(int64_t n, const double *x, TW *out) {
+__global__ void k_store_x(int64_t n, const double *x, TW *out, const int *skip) {
+    if (skip && *skip) return;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x)
         out[i] = static_cast<TW>(x[i]);
@@ -204,14 +205,14 @@ cudaError_t launch_init_rb(int64_t n, ir_dtype tw, const void *b, double *r, dou
     return cudaGetLastError();
 }
 
-cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s) {
+cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, cudaStream_t s, const int *skip) {
     if (n == 0) return cudaSuccess;
     int g = grid_for(n, 256, 1024);
     count_launch();
     if (tw == IR_F64)
-        k_store_x<double><<<g, 256, 0, s>>>(n, x, (double *)out);
+        k_store_x<double><<<g, 256, 0, s>>>(n, x, (double *)out, skip);
     else
-        k_store_x<float><<<g, 256, 0, s>>>(n, x, (float *)out);
+        k_store_x<float><<<g, 256, 0, s>>>(n, x, (float *)out, skip);
     return cudaGetLastError();
 }
 

@@ -420,6 +420,37 @@ __global__ void __launch_bounds__(kLaswpT) k_laswp_lists(float *AF, int64_t ldf,
 // U12 = L11^{-1} A12 for the block row j..j+NB and the columns [cb, ce): one
 // CTA of 256 threads per 64 columns (lu::trsm64).
 constexpr int kNarrowCols = 64;
+
+// The same after the panel's row interchanges on the CTA's own 64 columns
+// (the next block column of the lookahead chain: one launch instead of two).
+// Interchanges as k_laswp: all sources of a column are read before any of its
+// destinations is written; the shared staging is reused for L11 afterwards.
+__global__ void __launch_bounds__(256) k_laswp_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
+                                                    void *Bop, const int32_t *swap_list) {
+    pdl_trigger();
+    pdl_wait();
+    __shared__ int sd[2 * NB], ss[2 * NB];
+    __shared__ __align__(16) float stage[2 * NB * kNarrowCols];   // interchange values, then L11
+    const int c0 = cb + blockIdx.x * kNarrowCols;
+    const int cnt = swap_list[0];
+    for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+        sd[e] = swap_list[1 + 2 * e];
+        ss[e] = swap_list[2 + 2 * e];
+    }
+    __syncthreads();
+    {
+        // thread t: column t % 64, list entries t / 64, t / 64 + 4, ...
+        const int cc = threadIdx.x % kNarrowCols, e0 = threadIdx.x / kNarrowCols;
+        const int c = c0 + cc;
+        if (c < ce)
+            for (int e = e0; e < cnt; e += 256 / kNarrowCols) stage[e * kNarrowCols + cc] = AF[(int64_t)ss[e] * ldf + c];
+        __syncthreads();
+        if (c < ce)
+            for (int e = e0; e < cnt; e += 256 / kNarrowCols) AF[(int64_t)sd[e] * ldf + c] = stage[e * kNarrowCols + cc];
+        __syncthreads();     // the interchanged rows are in A_F before trsm64 reads them
+    }
+    lu::trsm64(AF, ldf, c0, ce, j, tf, Bop, reinterpret_cast<float (*)[lu::kLd]>(stage));
+}
 __global__ void __launch_bounds__(256) k_trsm_narrow(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf,
                                                      void *Bop) {
     pdl_trigger();
@@ -510,6 +541,21 @@ cudaError_t launch_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype 
     cfg.attrs = attr;
     cfg.numAttrs = set_pdl(&attr[0]);
     return cudaLaunchKernelEx(&cfg, k_trsm_narrow, AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop);
+}
+
+cudaError_t launch_laswp_trsm(float *AF, int64_t ldf, int cb, int ce, int j, ir_dtype tf, void *Bop,
+                              const int32_t *swap_list, cudaStream_t s) {
+    const int ncols = ce - cb;
+    if (ncols <= 0) return cudaSuccess;
+    count_launch();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ncols + kNarrowCols - 1) / kNarrowCols, 1, 1);
+    cfg.blockDim = dim3(256, 1, 1);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    cfg.attrs = attr;
+    cfg.numAttrs = set_pdl(&attr[0]);
+    return cudaLaunchKernelEx(&cfg, k_laswp_trsm, AF, ldf, cb, ce, j, tf, tf == IR_F32 ? nullptr : Bop, swap_list);
 }
 
 cudaError_t launch_iota(int n, int32_t *perm, cudaStream_t s) {

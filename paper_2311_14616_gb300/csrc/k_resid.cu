@@ -247,4 +247,61 @@ cudaError_t launch_residual_multi(int64_t n, ir_dtype tw, const void *A, int64_t
     return cudaGetLastError();
 }
 
+// ---- the refinement loop on the device (Algorithm IR's "while ||r|| is too
+// large"; the termination test of Sec. 5.1) --------------------------------
+namespace {
+
+__device__ __forceinline__ double bits_value(unsigned long long b) { return __longlong_as_double((long long)b); }
+
+// After x = 0, r = b: rhist[0] = ||b||; a non-finite b (or ||A||_1) ends the
+// solve before any correction; ||b|| = 0 ends it converged.
+__global__ void k_loop_start(DevScalars *dev, SolveLoop *loop, TermArgs t) {
+    const double bnorm = bits_value(dev->bnorm_bits);
+    loop->k = 0;
+    loop->rhist[0] = bnorm;
+    loop->err = dev->nonfinite ? kLoopNonfinite : 0;
+    loop->status = loop->err ? IR_FAILED : (bnorm == 0.0 ? IR_CONVERGED : -1);
+    loop->done = loop->status >= 0 ? 1 : 0;
+    dev->dnorm_bits = 0;
+    dev->xnorm_bits = 0;
+}
+
+// After the k-th residual: ||d|| and ||r|| appended, the test decides.
+__global__ void k_loop_step(DevScalars *dev, SolveLoop *loop, TermArgs t) {
+    if (loop->done) return;
+    if (dev->timeout) {                 // a bounded wait gave up: the iterate is not to be trusted
+        loop->err = kLoopTimeout;
+        loop->status = IR_FAILED;
+        loop->done = 1;
+        return;
+    }
+    const int k = loop->k + 1;
+    loop->k = k;
+    loop->dhist[k - 1] = bits_value(dev->dnorm_bits);
+    loop->rhist[k] = bits_value(dev->rnorm_bits);
+    const int st = term_rule(loop->rhist, loop->dhist, k, loop->rhist[0], t, bits_value(dev->anorm_bits),
+                             bits_value(dev->xnorm_bits));
+    loop->status = st;
+    if (st >= 0) {
+        loop->done = 1;
+    } else {
+        dev->dnorm_bits = 0;
+        dev->xnorm_bits = 0;
+    }
+}
+
+}  // namespace
+
+cudaError_t launch_loop_start(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s) {
+    count_launch();
+    k_loop_start<<<1, 1, 0, s>>>(dev, loop, t);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_loop_step(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s) {
+    count_launch();
+    k_loop_step<<<1, 1, 0, s>>>(dev, loop, t);
+    return cudaGetLastError();
+}
+
 }  // namespace ir

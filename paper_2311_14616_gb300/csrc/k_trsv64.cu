@@ -168,7 +168,8 @@ __device__ __forceinline__ void stage_tri(const float *AF, int64_t ldf, int n, i
 // y = L^{-1} P r: v_i = r[perm[i]] (binary64, unscaled).
 __global__ void __launch_bounds__(TT, 1) k_mps_lower(const float *AF, int64_t ldf, int n, int nblk,
                                                      const int32_t *perm, const double *r, double *y, int *yflag,
-                                                     int tag, DevScalars *dev) {
+                                                     int tag, DevScalars *dev, const int *skip) {
+    if (skip && *skip) return;      // uniform: written by an earlier launch
     extern __shared__ __align__(16) unsigned char mps_smem[];
     Mps64Smem &sm = *reinterpret_cast<Mps64Smem *>(mps_smem);
     __shared__ int s_bi;
@@ -193,7 +194,9 @@ __global__ void __launch_bounds__(TT, 1) k_mps_lower(const float *AF, int64_t ld
 
 // z = U^{-1} y, d = s z, x += d, ||d||_inf and ||x||_inf into dev.
 __global__ void __launch_bounds__(TT, 1) k_mps_upper(const float *AF, int64_t ldf, int n, int nblk, const double *y,
-                                                     double *z, int *zflag, int tag, double *x, DevScalars *dev) {
+                                                     double *z, int *zflag, int tag, double *x, DevScalars *dev,
+                                                     const int *skip) {
+    if (skip && *skip) return;
     extern __shared__ __align__(16) unsigned char mps_smem[];
     Mps64Smem &sm = *reinterpret_cast<Mps64Smem *>(mps_smem);
     __shared__ int s_bi;
@@ -246,7 +249,8 @@ __global__ void __launch_bounds__(TT, 1) k_mps_upper(const float *AF, int64_t ld
 // y64, z64: nblk * kMpsB binary64 each (nblk = ceil(n / kMpsB)); flags: 2 nblk
 // ints; tag: a value no earlier solve on these flags has written (the epoch).
 cudaError_t launch_mps_pair(const float *AF, int64_t ldf, int n, const int32_t *perm, const double *r, double *x,
-                            double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s) {
+                            double *y64, double *z64, int *flags, unsigned tag, DevScalars *dev, cudaStream_t s,
+                            const int *skip) {
     if (n == 0) return cudaSuccess;
     static bool attr = false;
     if (!attr) {
@@ -261,11 +265,11 @@ cudaError_t launch_mps_pair(const float *AF, int64_t ldf, int n, const int32_t *
     if (e != cudaSuccess) return e;
     const int itag = (int)(tag & 0x7FFFFFFFu);
     count_launch();
-    k_mps_lower<<<nblk, TT, kMpsSmem, s>>>(AF, ldf, n, nblk, perm, r, y64, flags, itag, dev);
+    k_mps_lower<<<nblk, TT, kMpsSmem, s>>>(AF, ldf, n, nblk, perm, r, y64, flags, itag, dev, skip);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     count_launch();
-    k_mps_upper<<<nblk, TT, kMpsSmem, s>>>(AF, ldf, n, nblk, y64, z64, flags + nblk, itag, x, dev);
+    k_mps_upper<<<nblk, TT, kMpsSmem, s>>>(AF, ldf, n, nblk, y64, z64, flags + nblk, itag, x, dev, skip);
     return cudaGetLastError();
 }
 
