@@ -137,7 +137,12 @@ void ir_finalize(ir_ctx *ctx);
 
 /* mplu (Sec. 2.4): round A to TF (A_F = I_W^F(s A), Sec. 1) into a library-
  * owned copy and factor it by LU with partial pivoting.
- *   n >= 0, A: n x n in TW, column-major, lda >= max(1, n).
+ *   0 <= n <= 77824, A: n x n in TW, column-major, lda >= max(1, n); a larger
+ *   n gives IR_EUNSUPPORTED.  Up to n = 8192 every panel is factored by one
+ *   thread-block cluster; a taller panel by one cooperative launch of up to one
+ *   CTA per SM (512 rows each), whose CTAs exchange each column's pivot
+ *   candidates through global memory; such a factorization is not replayed
+ *   from a CUDA graph.
  * The handle BORROWS A for the residuals of ir_solve: A must stay alive and
  * unmodified until ir_fact_destroy or ir_refactor (the MPArray shares A's
  * storage, Sec. 2.5).  Asynchronous; a zero pivot or a non-finite copy is

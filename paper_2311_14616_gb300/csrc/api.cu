@@ -164,6 +164,8 @@ void free_fact(ir_fact *f) {
     cudaFree(f->dev);
     if (f->host_dev) cudaFreeHost(f->host_dev);
     cudaFree(f->loop);
+    cudaFree(f->panel_grec);
+    cudaFree(f->panel_gcnt);
     if (f->host_loop) cudaFreeHost(f->host_loop);
     cudaFree(f->gm_V);
     cudaFree(f->gm_W);
@@ -234,6 +236,10 @@ ir_status alloc_fact(ir_ctx *ctx, int64_t n, const ir_opts *o, ir_fact **out) {
     AL(f->r, nn * sizeof(double));
     AL(f->dev, sizeof(DevScalars));
     AL(f->loop, sizeof(SolveLoop));
+    if (nn > (int64_t)kPanelRows * kPanelMaxCluster) {
+        AL(f->panel_grec, (size_t)2 * kPanelMaxGrid * kPanelGridRec * sizeof(float));
+        AL(f->panel_gcnt, (size_t)kPanelGridCounters * sizeof(unsigned));
+    }
 #undef AL
     if (cudaMallocHost((void **)&f->host_dev, sizeof(DevScalars)) != cudaSuccess ||
         cudaMallocHost((void **)&f->host_loop, sizeof(SolveLoop)) != cudaSuccess) {
@@ -363,7 +369,8 @@ ir_status enqueue_factor_grouped(ir_fact *f, cudaStream_t s) {
             int32_t *sl = f->swap_list + (step % (2 * kMaxGroup)) * kSwapListInts;
             void *aop = static_cast<char *>(f->Aop) + par * opsz;
             void *bop = static_cast<char *>(f->Bop) + par * opsz;
-            RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s));
+            RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s,
+                                          f->panel_grec, f->panel_gcnt));
             const bool trailing = j + nbp < n;
             const bool group_end = (j + NB >= c1) && near_end < n;   // far columns get the group's update now
             cudaStream_t sw = s;                                     // stream of this step's rest
@@ -493,7 +500,8 @@ ir_status enqueue_factor(ir_fact *f, cudaStream_t s) {
         int32_t *sl = f->swap_list + par * kSwapListInts;
         void *aop = f->Aop ? static_cast<char *>(f->Aop) + par * opsz : nullptr;
         void *bop = f->Bop ? static_cast<char *>(f->Bop) + par * opsz : nullptr;
-        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s));
+        RUN(KC_PANEL, s, launch_panel(f->AF, ldf, n, j, nbp, f->ipiv, f->perm, sl, f->dev, f->TF, aop, s,
+                                          f->panel_grec, f->panel_gcnt));
         const bool trailing = j + nbp < n;
         if (la) {
             cudaEvent_t evP = f->la_events[ev++];
@@ -551,7 +559,8 @@ bool graphs_enabled() {
 // CUDA graph on a private stream and replayed on the caller's stream; with
 // per-launcher profiling on, the launches are issued directly instead.
 ir_status run_factor(ir_fact *f, cudaStream_t s) {
-    if (g_prof.on || !graphs_enabled() || f->n == 0) return enqueue_factor(f, s);
+    // a factorization with cooperative panels (n > 8192) is enqueued directly
+    if (g_prof.on || !graphs_enabled() || f->n == 0 || f->panel_grec) return enqueue_factor(f, s);
     if (!f->graph || f->graph_A != f->A || f->graph_lda != f->lda) {
         if (f->graph) {
             cudaGraphExecDestroy(f->graph);

@@ -24,7 +24,10 @@ constexpr int kPanelNB = 64;      // panel width = outer block size
 constexpr int kPanelRows = 512;   // panel rows per CTA (two per thread)
 constexpr int kPanelThreads = 256;
 constexpr int kPanelMaxCluster = 16;
-constexpr int kMaxN = kPanelRows * kPanelMaxCluster;  // 8192 rows per panel cluster
+constexpr int kPanelMaxGrid = 152;  // CTAs of a panel taller than one cluster (one per SM, all resident)
+constexpr int kPanelGridCounters = kPanelNB + 1;   // arrival counters of such a panel: one per column + one
+constexpr int kPanelGridRec = 68;   // floats per exchanged pivot-candidate record
+constexpr int kMaxN = kPanelRows * kPanelMaxGrid;  // 77824 rows: the tallest panel
 constexpr int kMpsB = 64;         // row block of the mixed precision (binary64) solves
 constexpr int kMaxGroup = 16;     // block steps per group of the tensor-core LU (64 x 16 = 1024 columns)
 
@@ -207,6 +210,8 @@ struct ir_fact {
     int anorm_valid;         // dev->anorm_bits holds ||A||_1 of the current A
     ir::DevScalars *host_dev;  // pinned mirror
     ir::SolveLoop *loop;       // device-side refinement loop of ir_solve
+    float *panel_grec;         // pivot records of panels taller than one cluster (n > 8192)
+    unsigned *panel_gcnt;      // and their arrival counters
     ir::SolveLoop *host_loop;  // pinned mirror
     // the factorization's launch sequence as a CUDA graph (captured for one A)
     cudaStream_t cap_stream;
@@ -253,9 +258,13 @@ cudaError_t launch_store_x(int64_t n, ir_dtype tw, const double *x, void *out, c
 cudaError_t launch_loop_start(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s);
 cudaError_t launch_loop_step(DevScalars *dev, SolveLoop *loop, const TermArgs &t, cudaStream_t s);
 
+// Panel of the block step at column j.  Panels taller than one cluster holds
+// (more than kPanelRows * kPanelMaxCluster rows) exchange their pivot records
+// through grec (2 * kPanelMaxGrid * kPanelGridRec floats) and the counters gcnt
+// (kPanelGridCounters, zeroed here) in one cooperative launch.
 cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
                          int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
-                         void *Aop, cudaStream_t s);
+                         void *Aop, cudaStream_t s, float *grec = nullptr, unsigned *gcnt = nullptr);
 cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b,
                          const int32_t *swap_list, cudaStream_t s);
 // The interchange lists first .. first + count - 1 (of a ring of `ring` lists of

@@ -39,6 +39,7 @@ constexpr int NW = T / 32;
 // may read stale ones there, but only into window entries that are dead.
 constexpr int kRec = 68;                     // floats per record
 constexpr int kChunks = kRec / 4;            // 16-byte chunks per record
+static_assert(kRec == kPanelGridRec, "the grid exchange buffers hold records of kRec floats");
 struct PanelSmem {
     // records first, each 16-byte aligned (they are accessed as float4)
     alignas(16) float stage[2][NW][kRec];    // per-warp candidate records, by step parity
@@ -107,18 +108,59 @@ __device__ __forceinline__ void stage_record(float *st, const float (&a)[NB], un
 // staged at that step.  Rows that moved are listed as (destination, origin)
 // pairs in swap_list (count in swap_list[0]) for the interchanges of the
 // other columns, and perm is composed with the panel's permutation.
-template <bool kSingle>     // kSingle: a cluster of one CTA (no exchange)
+// The exchange of the CTAs' best records, by the panel's height:
+//   kModeCluster  2..16 CTAs of one thread-block cluster: st.async into every
+//                 CTA's shared memory (M <= 8192 rows)
+//   kModeSingle   one CTA: its best record is the pivot row (M <= 512)
+//   kModeGrid     up to one CTA per SM, launched cooperatively (all resident):
+//                 each CTA writes its record to global memory (grec, two slots
+//                 per CTA by step parity) and arrives on the step's counter
+//                 (gcnt[k], zeroed before the launch); each waits (bounded)
+//                 until all have arrived, reads the headers through L2 and
+//                 copies the winner's record into its shared memory (M > 8192)
+constexpr int kModeCluster = 0, kModeSingle = 1, kModeGrid = 2;
+
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier of a kModeGrid launch on counter *cnt (zeroed before the
+// launch, used once): bounded; on timeout the flags are raised and it returns.
+__device__ __forceinline__ void grid_barrier(unsigned *cnt, unsigned target, unsigned long long deadline,
+                                             volatile int *abort_flag, DevScalars *dev) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(cnt, 1u);
+        if (!*abort_flag) {
+            while (ld_acquire_gpu(cnt) < target) {
+                if (globaltimer() > deadline) {
+                    *abort_flag = 1;
+                    atomicExch(&dev->timeout, 1);
+                    break;
+                }
+            }
+        }
+    }
+    __syncthreads();
+}
+
+template <int kMode>
 __global__ void __launch_bounds__(T, 1)
     k_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv, int32_t *perm,
-            int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing) {
+            int32_t *swap_list, DevScalars *dev, ir_dtype tf, void *Aop, int has_trailing, float *grec,
+            unsigned *gcnt) {
+    constexpr bool kSingle = (kMode == kModeSingle), kGrid = (kMode == kModeGrid);
     pdl_trigger();
     pdl_wait();
     extern __shared__ __align__(16) unsigned char panel_smem[];
     PanelSmem &sm = *reinterpret_cast<PanelSmem *>(panel_smem);
     float *Ls = reinterpret_cast<float *>(panel_smem + sizeof(PanelSmem));   // [RPC][LS]
     float *Us = Ls + (size_t)RPC * LS;                                        // [NB][NB]
-    const unsigned crank = cluster_rank();
-    const unsigned csize = cluster_size();
+    const unsigned crank = kGrid ? blockIdx.x : cluster_rank();
+    const unsigned csize = kGrid ? gridDim.x : cluster_size();
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int home0 = (int)crank * RPC + t, home1 = home0 + T;   // start positions, relative to j
     const bool valid0 = j + home0 < n, valid1 = j + home1 < n;
@@ -134,7 +176,7 @@ __global__ void __launch_bounds__(T, 1)
         mbar_init_p(smem_u32(&sm.recv_bar[0]), 1);
         mbar_init_p(smem_u32(&sm.recv_bar[1]), 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        if (!kSingle) {      // a single CTA exchanges nothing
+        if (kMode == kModeCluster) {      // the other modes use no mbarrier
             mbar_expect_arrive(smem_u32(&sm.recv_bar[0]), step_bytes(0));
             if (nbp > 1) mbar_expect_arrive(smem_u32(&sm.recv_bar[1]), step_bytes(1));
         }
@@ -154,7 +196,10 @@ __global__ void __launch_bounds__(T, 1)
         for (int c = 0; c < NB; ++c)
             if (c >= nbp) a0[c] = a1[c] = 0.f;
     }
-    cluster_sync_all();   // every CTA is running and its mbarriers are armed
+    if constexpr (kGrid)
+        __syncthreads();
+    else
+        cluster_sync_all();   // every CTA is running and its mbarriers are armed
     const unsigned long long deadline = globaltimer() + kWaitLimitNs;   // for all waits of this launch
 
     const unsigned recv_addr = smem_u32(&sm.recv[0][0][0]);
@@ -211,6 +256,35 @@ __global__ void __launch_bounds__(T, 1)
             // a single CTA: its best record is the pivot row
             ppos = bp;
             u = sm.stage[buf][w];
+        } else if constexpr (kGrid) {
+            // the CTA's best record into its global slot, arrive, wait for all CTAs
+            float4 *gslot = reinterpret_cast<float4 *>(grec + ((size_t)buf * csize + crank) * kRec);
+            if (t < nch) gslot[t] = reinterpret_cast<const float4 *>(sm.stage[buf][w])[t];
+            grid_barrier(gcnt + k, csize, deadline, &sm.abort_flag, dev);
+            // the pivot: the best of all CTAs' headers (lane l reads CTAs l, l + 32, ...)
+            unsigned ck = 0u;
+            int cp = INT_MAX, cw = 0;
+            for (int q = lane; q < (int)csize; q += 32) {
+                const float *h = grec + ((size_t)buf * csize + q) * kRec;
+                const unsigned hk = __float_as_uint(__ldcg(h));
+                const int hp = __float_as_int(__ldcg(h + 1));
+                if (hp != INT_MAX && (cp == INT_MAX || hk > ck || (hk == ck && hp < cp))) {
+                    ck = hk;
+                    cp = hp;
+                    cw = q;
+                }
+            }
+            const unsigned ckmax = __reduce_max_sync(0xffffffffu, cp != INT_MAX ? ck : 0u);
+            ppos = __reduce_min_sync(0xffffffffu, (cp != INT_MAX && ck == ckmax) ? cp : INT_MAX);
+            const unsigned cwho = __ballot_sync(0xffffffffu, cp != INT_MAX && cp == ppos);
+            const int wc = __shfl_sync(0xffffffffu, cw, cwho ? __ffs(cwho) - 1 : 0);
+            // the winner's record into shared memory (every warp picked the same one)
+            float *rb = sm.recv[buf][0];
+            if (warp == 0 && lane < nch)
+                reinterpret_cast<float4 *>(rb)[lane] =
+                    __ldcg(reinterpret_cast<const float4 *>(grec + ((size_t)buf * csize + wc) * kRec) + lane);
+            __syncthreads();
+            u = rb;
         } else {
             // pushed to every CTA of the cluster: chunk i % 17 of it (if live)
             // into CTA i / 17 for i = t, t + T, ... (st.async, counted on the
@@ -326,7 +400,10 @@ __global__ void __launch_bounds__(T, 1)
         swap_list[2 + 2 * e] = j + home1;
         porg1 = perm[j + home1];
     }
-    cluster_sync_all();   // every perm read of the cluster is done; piv_log is complete
+    if constexpr (kGrid)    // every perm read of the grid is done; piv_log is complete
+        grid_barrier(gcnt + NB, csize, deadline, &sm.abort_flag, dev);
+    else
+        cluster_sync_all();   // every perm read of the cluster is done; piv_log is complete
     if (crank == 0) {
         for (int k = t; k < nbp; k += T) ipiv[j + k] = sm.piv_log[k];
         if (t == 0 && sm.zero_piv) atomicMin(&dev->info, sm.zero_piv);
@@ -362,7 +439,7 @@ __global__ void __launch_bounds__(T, 1)
             if (ops && pos >= NB) store_op_chunk(Aop, pos - NB, q, w, tf);
         }
     }
-    cluster_sync_all();   // no CTA leaves while its shared memory may be written
+    if constexpr (!kGrid) cluster_sync_all();   // no CTA leaves while its shared memory may be written
 }
 
 // Apply the panel's row permutation to the columns [c0a, c1a) and [c0b, c1b):
@@ -467,10 +544,10 @@ __global__ void k_iota(int n, int32_t *perm) {
 
 cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t *ipiv,
                          int32_t *perm, int32_t *swap_list, DevScalars *dev, ir_dtype tf,
-                         void *Aop, cudaStream_t s) {
+                         void *Aop, cudaStream_t s, float *grec, unsigned *gcnt) {
     static bool attr_done = false;
     if (!attr_done) {
-        for (auto kern : {k_panel<false>, k_panel<true>}) {
+        for (auto kern : {k_panel<kModeCluster>, k_panel<kModeSingle>, k_panel<kModeGrid>}) {
             cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
             if (e != cudaSuccess) return e;
             e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPanelDynSmem);
@@ -480,23 +557,34 @@ cudaError_t launch_panel(float *AF, int64_t ldf, int n, int j, int nbp, int32_t 
     }
     int M = n - j;
     int C = (M + RPC - 1) / RPC;
-    if (C > kPanelMaxCluster) return cudaErrorInvalidValue;
+    const int has_trailing = (j + NB < n) ? 1 : 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(C, 1, 1);
     cfg.blockDim = dim3(T, 1, 1);
     cfg.dynamicSmemBytes = kPanelDynSmem;
     cfg.stream = s;
     cudaLaunchAttribute attr[2];
+    cfg.attrs = attr;
+    if (C > kPanelMaxCluster) {
+        // taller than one cluster holds: one cooperative launch, every CTA resident
+        if (!grec || !gcnt || C > kPanelMaxGrid) return cudaErrorInvalidValue;
+        cudaError_t e = cudaMemsetAsync(gcnt, 0, kPanelGridCounters * sizeof(unsigned), s);
+        if (e != cudaSuccess) return e;
+        attr[0].id = cudaLaunchAttributeCooperative;
+        attr[0].val.cooperative = 1;
+        cfg.numAttrs = 1;
+        count_launch();
+        return cudaLaunchKernelEx(&cfg, k_panel<kModeGrid>, AF, ldf, n, j, nbp, ipiv, perm, swap_list, dev, tf, Aop,
+                                  has_trailing, grec, gcnt);
+    }
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = C;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    cfg.attrs = attr;
     cfg.numAttrs = 1 + set_pdl(&attr[1]);
-    int has_trailing = (j + NB < n) ? 1 : 0;
     count_launch();
-    return cudaLaunchKernelEx(&cfg, C == 1 ? k_panel<true> : k_panel<false>, AF, ldf, n, j, nbp, ipiv, perm,
-                              swap_list, dev, tf, Aop, has_trailing);
+    return cudaLaunchKernelEx(&cfg, C == 1 ? k_panel<kModeSingle> : k_panel<kModeCluster>, AF, ldf, n, j, nbp, ipiv,
+                              perm, swap_list, dev, tf, Aop, has_trailing, (float *)nullptr, (unsigned *)nullptr);
 }
 
 cudaError_t launch_laswp(float *AF, int64_t ldf, int c0a, int c1a, int c0b, int c1b, const int32_t *swap_list,

@@ -142,9 +142,12 @@ def test_ir_edge_sizes_and_zero_rhs(ctx):
 
 def test_invalid_arguments_and_limits(ctx):
     from paper_2311_14616_gb300.ir import IRError
+    n = 77825                   # one row more than the tallest panel (152 CTAs x 512 rows)
+    big = torch.empty((n, n), dtype=torch.float32, device="cuda")    # 24 GB, never read
     with pytest.raises(IRError) as e:
-        ctx.factor(torch.zeros((8193, 8193), dtype=torch.float32, device="cuda"), tf="f32")
+        ctx.factor(big.t(), tf="f32")
     assert e.value.code == 7
+    del big
     with pytest.raises(IRError) as e:
         ctx.factor(dev_colmajor(np.eye(4)), tf=9)
     assert e.value.code == 1
