@@ -374,12 +374,15 @@ __global__ void __launch_bounds__(256) k_pack_slots(const float *AF, int64_t ldf
 //              tile (64 x 64) of slot a into one stage; before the first pair
 //              that needs U_a it waits until the epilogue has published U_a
 //   warp 1     TMEM (8 accumulators x 64 columns); MMAs, one accumulator per pair
-//   warps 2-5  one far column per thread: C_c into registers, the pairs'
-//              accumulators subtracted in order, the triangular solve, stores
+//   warps 2-5 and 6-9  two epilogue groups taking the block rows in turn
+//              (c even, c odd), one far column per thread: C_c into registers,
+//              the pairs' accumulators subtracted in order, the triangular
+//              solve, stores; while one group solves block c, the other
+//              already subtracts block c + 1's products with U_0 .. U_{c-1}
 // One CTA per 128 far columns.  Every wait is bounded; after a timeout the
 // epilogue still runs its loops (no barrier is skipped) without waiting.
 constexpr int kU12Acc = 8;                 // accumulators of 64 TMEM columns
-constexpr int kU12Threads = 192;
+constexpr int kU12Threads = 320;
 constexpr int kLAtomBytes = 64 * 128;      // one 64-row x 128-byte swizzle tile = 8 KB
 constexpr int kLtLd = K + 4;               // row stride of the staged diagonal block
 
@@ -408,8 +411,8 @@ __global__ void __launch_bounds__(kU12Threads, 1)
     unsigned char *gbase = smem_raw + (sbase - smem_u32(smem_raw));
     const unsigned sU = sbase;                                   // STAGES x KATOMS x 16 KB
     const unsigned sL = sbase + STAGES * KATOMS * kAtomBytes;    // STAGES x KATOMS x 8 KB
-    float *Lt = reinterpret_cast<float *>(gbase + STAGES * KATOMS * (kAtomBytes + kLAtomBytes));  // [K][kLtLd]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(Lt + K * kLtLd);
+    float *Lt = reinterpret_cast<float *>(gbase + STAGES * KATOMS * (kAtomBytes + kLAtomBytes));  // [2][K][kLtLd]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(Lt + 2 * K * kLtLd);
     const unsigned bar0 = smem_u32(bars);
     auto full_bar = [&](int s) { return bar0 + 8u * s; };
     auto empty_bar = [&](int s) { return bar0 + 8u * (STAGES + s); };
@@ -510,29 +513,33 @@ __global__ void __launch_bounds__(kU12Threads, 1)
             }
         }
     } else {
-        // warps 2..5: TMEM lane quarter warp % 4; thread = far column x of the CTA
+        // warps 2..9: group eg = (warp - 2) / 4 takes the block rows c = eg, eg + 2, ...;
+        // TMEM lane quarter warp % 4; thread = far column x of the CTA
+        const int eg = (warp - 2) >> 2;
         const int quarter = warp & 3;
         const int x = quarter * 32 + lane;
-        const int ep = threadIdx.x - 64;                    // 0 .. 127
+        const int ep = (threadIdx.x - 64) & 127;            // 0 .. 127 within the group
         const int col = p.cb + blockIdx.x * BM + x;
         const bool on = col < p.ce;
         const int esz = (p.tf == IR_TF32) ? 4 : 2;
-        unsigned qa = 0;
-        for (int c = 0; c < p.G; ++c) {
+        float *Ltg = Lt + eg * K * kLtLd;
+        const unsigned gbar = 1u + (unsigned)eg;            // the group's named barrier
+        for (int c = eg; c < p.G; c += 2) {
+            unsigned qa = (unsigned)(c * (c - 1) / 2);      // pairs of the blocks before c
             const int rc = p.c0 + K * c;
             float u[K];
 #pragma unroll
             for (int i = 0; i < K; ++i) u[i] = on ? p.AF[(int64_t)(rc + i) * p.ldf + col] : 0.f;
-            asm volatile("bar.sync 1, 128;" ::: "memory");   // the previous block's solve is done with Lt
+            asm volatile("bar.sync %0, 128;" ::"r"(gbar) : "memory");   // the group's previous solve is done with Lt
             // Lt[m][k] = l_km of the diagonal block (binary32)
 #pragma unroll
             for (int i = 0; i < K * K / 4 / 128; ++i) {
                 const int e = ep + 128 * i, k = e % K, m4 = e / K;
                 const float4 v = *reinterpret_cast<const float4 *>(p.AF + (int64_t)(rc + k) * p.ldf + rc + 4 * m4);
-                Lt[(4 * m4 + 0) * kLtLd + k] = v.x;
-                Lt[(4 * m4 + 1) * kLtLd + k] = v.y;
-                Lt[(4 * m4 + 2) * kLtLd + k] = v.z;
-                Lt[(4 * m4 + 3) * kLtLd + k] = v.w;
+                Ltg[(4 * m4 + 0) * kLtLd + k] = v.x;
+                Ltg[(4 * m4 + 1) * kLtLd + k] = v.y;
+                Ltg[(4 * m4 + 2) * kLtLd + k] = v.z;
+                Ltg[(4 * m4 + 3) * kLtLd + k] = v.w;
             }
             for (int a = 0; a < c; ++a, ++qa) {
                 const int ab = (int)(qa % kU12Acc);
@@ -550,11 +557,11 @@ __global__ void __launch_bounds__(kU12Threads, 1)
                     u[32 + q] -= v1[q];
                 }
             }
-            asm volatile("bar.sync 1, 128;" ::: "memory");   // Lt is complete
+            asm volatile("bar.sync %0, 128;" ::"r"(gbar) : "memory");   // Lt is complete
 #pragma unroll
             for (int m = 0; m < K - 1; ++m) {
                 const float um = u[m];
-                const float4 *l4 = reinterpret_cast<const float4 *>(Lt + m * kLtLd);
+                const float4 *l4 = reinterpret_cast<const float4 *>(Ltg + m * kLtLd);
 #pragma unroll
                 for (int k4 = (m + 1) / 4; k4 < K / 4; ++k4) {
                     const float4 l = l4[k4];
@@ -662,7 +669,7 @@ static_assert(smem_bytes<2, 3, 2>() <= 232448, "TF32 configuration exceeds share
 
 template <int KATOMS, int STAGES>
 constexpr size_t u12_smem_bytes() {
-    return 1024 + (size_t)STAGES * KATOMS * (kAtomBytes + kLAtomBytes) + (size_t)K * kLtLd * 4 +
+    return 1024 + (size_t)STAGES * KATOMS * (kAtomBytes + kLAtomBytes) + (size_t)2 * K * kLtLd * 4 +
            8 * (2 * STAGES + 2 * kU12Acc + 2) + 16;
 }
 static_assert(u12_smem_bytes<1, 4>() <= 232448 && u12_smem_bytes<2, 3>() <= 232448,
