@@ -2,9 +2,11 @@
 stay in place and carry position labels, every row holds a window of the
 panel that shifts left by one column per step, the pivot row travels as a
 record, and the rank-1 update stops at the first 16-column chunk past the
-live width, so window entries past it go stale.  The model checks the
-invariants the kernel relies on: the stale entries are never read, and the
-labels give LAPACK's interchanges.  fmaf is emulated in binary64 (the product
+live width, so window entries past it go stale; the record carries only the
+header and the live part of the row (16-byte chunks: 17 at the first column,
+one fewer every four), so the receivers see stale values past it.  The model
+checks the invariants the kernel relies on: the stale entries are never read,
+and the labels give LAPACK's interchanges.  fmaf is emulated in binary64 (the product
 of two binary32 values is exact there); the same emulation serves every
 variant, so variants are compared bit for bit and the model is compared with
 the oracle's binary32 LU through its pivots and to a tight tolerance."""
@@ -21,9 +23,11 @@ def _fmaf(a, b, c):
     return (a.astype(np.float64) * b.astype(np.float64) + c.astype(np.float64)).astype(np.float32)
 
 
-def panel_model(P, chunked):
+def panel_model(P, chunked, live_records=False):
     """Factor the M x nbp panel P (binary32); returns (factors in final row
-    order, ipiv) as the kernel writes them."""
+    order, ipiv) as the kernel writes them.  live_records: the pivot record
+    keeps only its first (70 - k) // 4 chunks of 4 (header: |a|, position,
+    1/a; then a[0], a[1], ...), everything past them arrives as NaN."""
     M, nbp = P.shape
     a = np.zeros((M, NB), np.float32)
     a[:, :nbp] = P
@@ -39,6 +43,9 @@ def panel_model(P, chunked):
         w = best[np.argmin(pos[best])]                   # ties: lowest current position
         ppos = pos[w]
         u = a[w].copy()                                  # the pivot row's record
+        if live_records:
+            nch = (70 - k) // 4                          # chunks sent at step k
+            u[4 * nch - 3:] = np.nan                     # record float 3 + i holds a[i]
         ipiv[k] = ppos
         piv = u[0]
         r = np.float32(1.0) / piv
@@ -70,6 +77,18 @@ def test_chunked_update_reads_no_stale_entry(M, nbp, seed):
     chunk, piv_chunk = panel_model(P, chunked=True)
     assert np.array_equal(piv_full, piv_chunk)
     assert np.array_equal(full.view(np.uint32), chunk.view(np.uint32))
+
+
+@pytest.mark.parametrize("M,nbp,seed", [(64, 64, 6), (300, 64, 7), (97, 44, 8), (70, 1, 9), (513, 64, 10)])
+def test_live_records_carry_every_value_that_is_read(M, nbp, seed):
+    """Sending only the live part of the pivot row (the rest arrives as NaN)
+    gives the same factors and pivots, bit for bit."""
+    P = np.random.default_rng(seed).standard_normal((M, nbp)).astype(np.float32)
+    full, piv_full = panel_model(P, chunked=True)
+    live, piv_live = panel_model(P, chunked=True, live_records=True)
+    assert np.array_equal(piv_full, piv_live)
+    assert not np.isnan(live).any()
+    assert np.array_equal(full.view(np.uint32), live.view(np.uint32))
 
 
 @pytest.mark.parametrize("n", [40, 64, 100])
