@@ -66,8 +66,9 @@ def test_single_rank_needs_no_process_group():
 
 
 def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
-    """bench.py --impl reference launched like the driver launches N > 1: rank 0
-    times the oracle and prints the one JSON line, the other rank exits 0."""
+    """bench.py --impl reference launched as a two-process torchrun job (the
+    launch used for N > 1): rank 0 times the oracle and prints the one JSON
+    line, the other rank exits 0."""
     port = _free_port()
     cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),

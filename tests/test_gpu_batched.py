@@ -59,7 +59,7 @@ def _run(ctx, As, bs, tf, dtype=np.float64, term=None):
 LITMAX_LP = 20
 
 
-def _judge(A, b, x, r, tf, litmax=LITMAX_LP):
+def _classify_member(A, b, x, r, tf, litmax=LITMAX_LP):
     """Compare one batch member with the oracle's IR on the same system; returns
     the oracle's class and whether x and the status were compared."""
     o = O.ir_solve(A, b, TF[tf], O.Term(litmax=litmax), nb=64)
@@ -122,7 +122,7 @@ def test_batch_low_precision_vs_oracle(ctx, tf):
         if r["status"] == "converged":
             # the residual test itself must hold
             assert r["rnorm"] <= 2.0 ** -52 * np.max(np.abs(b))
-        cls, st = _judge(A, b, x, r, tf)
+        cls, st = _classify_member(A, b, x, r, tf)
         compared += cls == "conv"
         status_cmp += st
     # most members are away from the boundary of their TF: most compare
@@ -152,7 +152,7 @@ def test_batch_failures_are_per_system(ctx):
     for i in (0,):
         assert res[i]["status"] != "failed"
         assert _same(res[i]["rnorm"], _rnorm_of(As[i], bs[i], xs[i]))
-        assert _judge(As[i], bs[i], xs[i], res[i], "f16") == ("conv", True)
+        assert _classify_member(As[i], bs[i], xs[i], res[i], "f16") == ("conv", True)
     assert res[1]["status"] == "failed" and res[1]["info"] == 1 and not res[1]["nonfinite"]
     assert res[2]["status"] == "failed" and res[2]["nonfinite"]
     assert res[3]["status"] == "failed" and res[3]["nonfinite"]
@@ -216,7 +216,7 @@ def test_full_batch_2000_systems(ctx, full_batch, tf):
     sample = g.choice(len(ns), size=40, replace=False)
     compared = status_cmp = 0
     for i in sample:
-        cls, st = _judge(As[i], bs[i], xs[i], res[i], tf)
+        cls, st = _classify_member(As[i], bs[i], xs[i], res[i], tf)
         compared += cls == "conv"
         status_cmp += st
     # a quarter of these systems have alpha close to a singular mode (kappa up to
@@ -264,7 +264,7 @@ def test_batch_autotune_picks_a_candidate_and_keeps_parity(ctx):
     res = plan.results()
     compared = 0
     for A, b, x, r in zip(As, bs, plan.xs, res):
-        cls, _ = _judge(A, b, x.cpu().numpy(), r, "f16")
+        cls, _ = _classify_member(A, b, x.cpu().numpy(), r, "f16")
         compared += cls == "conv"
     assert compared >= 0.8 * len(As), compared
     untuned = ctx.batch([dev_colmajor(A) for A in As], [dev_vec(b) for b in bs], tf="f16")
