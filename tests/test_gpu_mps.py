@@ -131,3 +131,25 @@ def test_mps_host_entry_point_and_many_rhs(ctx):
     X = X.cpu().numpy()
     assert reps[2].status == "converged" and reps[2].iters == 0
     assert O.rel_err_inf(X[:, 0], xh.numpy()) <= 1e-14
+
+
+@pytest.mark.parametrize("name,make,tf", [
+    ("green_a100_N700_f16", lambda: irgen.case_green(700, 100.0), O.F16),
+    ("gauss_N700_bf16", lambda: irgen.case_gaussian(700, 19), O.BF16),
+], ids=["green_a100_N700_f16", "gauss_N700_bf16"])
+def test_mps_on_factors_kept_in_two_bytes(ctx, name, make, tf):
+    """Mixed precision solves on factors kept in TF (store_tf): the oracle rounds
+    its factors to TF once and promotes them in its binary64 solves; the GPU's
+    status, steps (within one) and x agree with it."""
+    A, b = make()
+    f = ctx.factor(dev_colmajor(A), tf=O.DTYPE_NAMES[tf], onthefly=True, store_tf=True)
+    x, rep = f.solve(dev_vec(b))
+    x = x.cpu().numpy()
+    ref = O.ir_solve(A, b, tf, nb=64, solve="mps", store_tf=True)
+    xr = O.reference_solution(A, b)
+    tol = P.bar(O.cond_inf(A))
+    assert rep.status == O.STATUS_NAMES[ref.status], (rep.rhist, ref.rhist)
+    assert abs(rep.iters - ref.iters) <= 1
+    assert O.rel_err_inf(ref.x, xr) <= tol
+    assert O.rel_err_inf(x, ref.x) <= tol, O.rel_err_inf(x, ref.x)
+    assert O.rel_err_inf(x, xr) <= tol, O.rel_err_inf(x, xr)
