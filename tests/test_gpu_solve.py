@@ -277,19 +277,21 @@ def test_solve_many_columns_equal_single_solves(ctx):
     assert O.rel_err_inf(X[:, 0], xr) <= O.parity_tol(O.cond_inf(A), O.F64)
 
 
-@pytest.mark.parametrize("n,tf,store", [(700, "f32", False), (5000, "f32", False), (1500, "f16", True),
-                                         (300, "bf16", False)])
-def test_solve_many_blocked_equals_single_solves(ctx, n, tf, store):
+@pytest.mark.parametrize("n,tf,store,tw", [(700, "f32", False, np.float64), (5000, "f32", False, np.float64),
+                                            (1500, "f16", True, np.float64), (300, "bf16", False, np.float64),
+                                            (600, "f16", False, np.float32)])
+def test_solve_many_blocked_equals_single_solves(ctx, n, tf, store, tw):
     """ir_solve_many refines up to 4 columns together: each factor tile of the
     correction solve is applied to all of them and each residual reads A once,
     with every column's own scaling, history and termination.  Per column the
     arithmetic is that of the single-column path, in the same order, so x and
     the histories are bitwise the single solves' -- for blocks of 4, a ragged
     last block, a zero column, a non-finite column, the sync-free solve pair
-    (n > 4096), 2-byte factors, and the backward-error test."""
+    (n > 4096), 2-byte factors, the backward-error test, and TW = binary32."""
     A, _ = irgen.case_gaussian(n, 5000 + n)
+    A = np.asfortranarray(A.astype(tw))
     g = np.random.Generator(np.random.PCG64(n))
-    B = g.standard_normal((n, 9))
+    B = g.standard_normal((n, 9)).astype(tw)
     B[:, 5] = 0.0
     B[:, 2] *= 1e-3
     f = ctx.factor(dev_colmajor(A), tf=tf, store_tf=store)
